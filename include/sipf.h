@@ -1,0 +1,189 @@
+/*
+ * sipf.h -- C ABI of the GB300 SIPF-W step library (libsipf.so).
+ *
+ * The library advances the 3D u/v/m/w haptotaxis system
+ *     u_t + chi div(u grad v) = Du lap u - u + rho(w) u
+ *     v_t = -alpha m v
+ *     m_t = Dm lap m - beta m + u
+ *     w_t = Dw lap w - eta(u) w + gamma v - w,   rho(w) = 2w/(1+w), eta(u) = 2u/(1+u)
+ * (paper Eq. haptotaxis-system) with the stochastic interacting
+ * particle-field scheme with weighted particles, SIPF-W (paper Alg. 3):
+ * u is an empirical measure of P weighted particles, v, m, w live on an
+ * H^3 periodic grid (equivalently H^3 Fourier modes, Eq. vmw_hat), and each
+ * step does particle-to-grid deposit (Alg. 1), grid-to-particle gather
+ * (Alg. 2), the Euler-Maruyama push and mass update (Eq. u_hat_update), the
+ * explicit reaction and the spectral diffusion solve (Eq. g_hat_phy,
+ * k_q_update).  All arithmetic runs in CUDA kernels on the device the
+ * context was created on; there is no CPU fallback.
+ *
+ * Conventions shared by every call
+ *   - Return value: SIPF_OK (0) or a negative SIPF_E* code; the context's
+ *     last error message (sipf_last_error) says more.
+ *   - `where` selects the memory space of a caller buffer: SIPF_HOST
+ *     (pageable or pinned host memory) or SIPF_DEVICE (device memory on the
+ *     context's GPU).  Caller buffers are only read/written during the call
+ *     (plus the copy it enqueues, completed before the call returns); the
+ *     library never keeps a pointer to them.
+ *   - Positions cross the ABI as physical coordinates in the box
+ *     [origin, origin + L)^3, structure of arrays: x[0..N) then y[0..N) then
+ *     z[0..N) (3*N floats).  Fields cross as H^3 float32 arrays indexed
+ *     [z][y][x] (x fastest), node (i, j, k) at origin + (i, j, k) h, h = L/H.
+ *   - Work is enqueued on the CUDA stream given at creation; calls that
+ *     return data synchronise that stream.  A context must be used from one
+ *     host thread at a time; distinct contexts are independent.
+ *   - Noise: the Brownian increment of particle `id` in step n (n = 1, 2, ...)
+ *     is sqrt(2 Du dt) z with z from Box-Muller on the Philox4x32-10 words of
+ *     counter (n, 0, id, 0) and key (seed mod 2^32, seed >> 32).  Results
+ *     therefore depend only on (initial state, parameters, seed, dt
+ *     sequence), not on launch configuration.
+ */
+#ifndef SIPF_H
+#define SIPF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SIPF_OK            0
+#define SIPF_EINVAL       -1   /* invalid argument (value, size, pointer, order of calls) */
+#define SIPF_ENOMEM       -2   /* device or host allocation failed                       */
+#define SIPF_ECUDA        -3   /* a CUDA runtime call or kernel launch failed            */
+#define SIPF_EUNSUPPORTED -4   /* valid request this build does not implement            */
+#define SIPF_ENONFINITE   -6   /* a particle position became non-finite (reset to 0)      */
+#define SIPF_EINTERNAL    -7   /* a device-side consistency check failed                 */
+
+#define SIPF_HOST   0
+#define SIPF_DEVICE 1
+
+/* field selection bits for sipf_fields; fields are written in this order */
+#define SIPF_FIELD_U  1u    /* deposited density u_bar of the current particles (Alg. 1) */
+#define SIPF_FIELD_V  2u
+#define SIPF_FIELD_M  4u
+#define SIPF_FIELD_W  8u
+#define SIPF_FIELD_GX 16u   /* spectral d v / dx on the nodes (Eq. gradv) */
+#define SIPF_FIELD_GY 32u
+#define SIPF_FIELD_GZ 64u
+
+#define SIPF_DIFFUSION_IMPLICIT 0  /* 1/(1 + tau R + tau D|k|^2), convergence analysis Sec. 4 */
+#define SIPF_DIFFUSION_EXP      1  /* exp(-tau D|k|^2 - tau R), Eq. k_q_update              */
+#define SIPF_V_IMPLICIT 0          /* v/(1 + alpha tau m), Sec. 2.3.3                         */
+#define SIPF_V_EXPLICIT 1          /* v (1 - alpha tau m), source S of Eq. g_t                */
+
+typedef struct sipf_ctx sipf_ctx;
+
+/* Periodic box [origin, origin + L)^3 with H nodes per axis (paper Sec. 2.1;
+ * Omega = [-L/2, L/2]^3 there, origin = -L/2).  H must be a power of two
+ * with 16 <= H <= 128 in this build (256 returns SIPF_EUNSUPPORTED). */
+typedef struct {
+    int32_t H;
+    double L;
+    double origin[3];
+} sipf_grid;
+
+/* Model and scheme parameters (paper Eq. haptotaxis-system; all >= 0 and
+ * finite).  H0: low-pass cut-off exp(-2 pi^2 |q|^2 / H0^2) of Alg. 3 applied
+ * to the m, w spectra and to the v spectrum used for grad v; 0 or >= H is
+ * off (the paper's experiments run with it off). */
+typedef struct {
+    double chi, Du, Dm, Dw, alpha, beta, gamma;
+    int32_t diffusion;   /* SIPF_DIFFUSION_*  */
+    int32_t v_update;    /* SIPF_V_*          */
+    double H0;
+    uint64_t seed;       /* Philox key        */
+} sipf_params;
+
+/* FP64 diagnostics of the current state (Lemma mass, Corollary mass and the
+ * positivity lemma of the paper): total particle mass sum a_p, grid mass
+ * h^3 sum u_bar, minima of u_bar, v, m, w, and the count of non-finite
+ * values in v, m, w and the positions. */
+typedef struct {
+    double mass_particles, mass_grid, min_u, min_v, min_m, min_w;
+    int64_t step;
+    double time;
+    int64_t nonfinite;
+} sipf_diag;
+
+/* Create a context on the current CUDA device for N particles on `grid`.
+ * `stream` is a cudaStream_t (NULL = legacy default stream) on which all
+ * later work of the context is enqueued.  Allocates all device state
+ * (about 56 N + 90 H^3 bytes).  Errors: SIPF_EINVAL (N < 1 or N >= 2^31,
+ * H not supported, L <= 0, a parameter negative or non-finite, diffusion or
+ * v_update unknown), SIPF_EUNSUPPORTED (H = 256), SIPF_ENOMEM. */
+int sipf_create(const sipf_grid* grid, int64_t N, const sipf_params* params,
+                void* stream, sipf_ctx** out);
+
+/* Set the state at t = 0 (paper Alg. 3, initialisation): particle
+ * positions x (3*N physical coordinates, SoA; wrapped into the box),
+ * masses `mass` (N doubles, > 0, or 0 for a massless tracer), persistent
+ * ids `id` (N uint32; NULL means 0..N-1) and the node values of v, m, w
+ * (H^3 floats each).  grad v is computed from v by the spectral derivative
+ * (Eq. gradv) and the particles are binned by cell.  Resets the step counter
+ * and the time to 0.  Errors: SIPF_EINVAL (NULL pointer, bad `where`, a
+ * negative or non-finite mass), SIPF_ECUDA. */
+int sipf_set_state(sipf_ctx* ctx, const float* x, const double* mass, const uint32_t* id,
+                   const float* v, const float* m, const float* w, int where);
+
+/* Enqueue k steps of size dt (paper Alg. 3 loop body, Jacobi ordering:
+ * deposit, gather, push and field update all read the state at step n-1).
+ * Asynchronous: returns after enqueueing; device-side failures are reported
+ * by the next synchronising call.  Errors: SIPF_EINVAL (state not set,
+ * dt <= 0, dt > 0.5 -- the positivity lemma's bound -- or k < 0),
+ * SIPF_ECUDA. */
+int sipf_step(sipf_ctx* ctx, double dt, int64_t k);
+
+/* Copy the fields selected by `mask` (SIPF_FIELD_* bits) into dst, one H^3
+ * float array after another in bit order.  SIPF_FIELD_U deposits the
+ * current particles (Alg. 1).  Synchronises the context stream and reports
+ * any deferred device error.  Errors: SIPF_EINVAL, SIPF_ECUDA, deferred
+ * codes. */
+int sipf_fields(sipf_ctx* ctx, uint32_t mask, float* dst, int where);
+
+/* Copy the particles in the library's storage order (bucketed by cell):
+ * physical positions x (3*N floats, SoA; may be NULL), masses a = exp(log a)
+ * (N doubles; may be NULL) and ids (N uint32; may be NULL).  Synchronises. */
+int sipf_particles(sipf_ctx* ctx, float* x, double* mass, uint32_t* id, int where);
+
+/* Raw particle state in storage order: positions in grid units
+ * s = (x - origin)/h in [0, H) (3*N floats, SoA), log-masses (N doubles) and
+ * ids; any pointer may be NULL.  Synchronises. */
+int sipf_particle_state(sipf_ctx* ctx, float* s, double* loga, uint32_t* id, int where);
+
+/* Offsets of each cell's run of particles in storage order (H^3 + 1 int32).
+ * Cells are numbered tile-major: key = tile * 512 + local, tiles of 8^3
+ * cells, tile = ((cz/8) T + cy/8) T + cx/8 with T = H/8, local =
+ * ((cz%8) 8 + cy%8) 8 + cx%8, cell (cx, cy, cz) = floor(s).  Within a cell
+ * the storage order is unspecified.  Synchronises. */
+int sipf_cell_start(sipf_ctx* ctx, int32_t* cell_start, int where);
+
+/* FP64 diagnostics of the current state; synchronises. */
+int sipf_diagnostics(sipf_ctx* ctx, sipf_diag* out);
+
+/* Wait for the context's stream and return any deferred device error. */
+int sipf_sync(sipf_ctx* ctx);
+
+/* Free all device state of the context (synchronising first); NULL is a
+ * no-op. */
+void sipf_destroy(sipf_ctx* ctx);
+
+/* Static description of a return code. */
+const char* sipf_strerror(int code);
+
+/* Message of the last failed call on the context ("" if none). */
+const char* sipf_last_error(const sipf_ctx* ctx);
+
+/* Brownian normals used by the push, for checking the generator: for each
+ * i < N, z[i], z[N+i], z[2N+i] are the three standard normals of particle
+ * ids[i] in step n with key `seed` (Box-Muller on Philox4x32-10, counter
+ * (n, 0, id, 0)); `bits` (4*N uint32, SoA, may be NULL) receives the raw
+ * Philox words.  ids, z and bits are device pointers; runs on `stream` and
+ * synchronises it.  Errors: SIPF_EINVAL, SIPF_ECUDA. */
+int sipf_brownian_normals(const uint32_t* ids, int64_t N, uint32_t n, uint64_t seed,
+                          float* z, uint32_t* bits, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIPF_H */

@@ -1,0 +1,543 @@
+// C ABI of the SIPF-W library: argument checking, device memory of a
+// context, and the order of kernel launches of a step (paper Alg. 3).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sipf_internal.cuh"
+
+namespace sipf {
+cudaError_t launch_iota(sipf_ctx* c, int buf);
+size_t diag_scratch_doubles();
+size_t diag_scratch_ll();
+int scan_tiles(int n);
+}  // namespace sipf
+
+namespace {
+
+using namespace sipf;
+
+int fail(sipf_ctx* c, int code, const std::string& msg) {
+    if (c) c->last_error = msg;
+    return code;
+}
+
+int cuda_fail(sipf_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, SIPF_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define SIPF_CUDA(ctx, call)                                         \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);   \
+    } while (0)
+
+bool supported_H(int H) { return H == 16 || H == 32 || H == 64 || H == 128; }
+
+bool finite_nonneg(double x) { return isfinite(x) && x >= 0.0; }
+
+int check_params(const sipf_params* p, std::string* why) {
+    const double v[] = {p->chi, p->Du, p->Dm, p->Dw, p->alpha, p->beta, p->gamma, p->H0};
+    const char* n[] = {"chi", "Du", "Dm", "Dw", "alpha", "beta", "gamma", "H0"};
+    for (int i = 0; i < 8; ++i)
+        if (!finite_nonneg(v[i])) {
+            *why = std::string("parameter ") + n[i] + " must be finite and >= 0";
+            return SIPF_EINVAL;
+        }
+    if (p->diffusion != SIPF_DIFFUSION_IMPLICIT && p->diffusion != SIPF_DIFFUSION_EXP) {
+        *why = "unknown diffusion mode";
+        return SIPF_EINVAL;
+    }
+    if (p->v_update != SIPF_V_IMPLICIT && p->v_update != SIPF_V_EXPLICIT) {
+        *why = "unknown v_update mode";
+        return SIPF_EINVAL;
+    }
+    return SIPF_OK;
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t n) {
+    return cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
+}
+
+void free_all(sipf_ctx* c) {
+    void* ptrs[] = {c->sx[0], c->sx[1], c->sy[0], c->sy[1], c->sz[0], c->sz[1], c->loga[0],
+                    c->loga[1], c->id[0], c->id[1], c->count, c->cell_start, c->scan_tmp, c->acc,
+                    c->v, c->m, c->w, c->gx, c->gy, c->gz, c->specM, c->specW, c->specV,
+                    c->specB, c->specA, c->twiddle, c->status, c->diag_tmp, c->diag_out,
+                    c->diag_ll, c->voff};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+}
+
+int copy_in(sipf_ctx* c, void* dst, const void* src, size_t bytes, int where) {
+    const cudaMemcpyKind k = where == SIPF_DEVICE ? cudaMemcpyDeviceToDevice
+                                                  : cudaMemcpyHostToDevice;
+    SIPF_CUDA(c, cudaMemcpyAsync(dst, src, bytes, k, c->stream));
+    return SIPF_OK;
+}
+
+int copy_out(sipf_ctx* c, void* dst, const void* src, size_t bytes, int where) {
+    const cudaMemcpyKind k = where == SIPF_DEVICE ? cudaMemcpyDeviceToDevice
+                                                  : cudaMemcpyDeviceToHost;
+    SIPF_CUDA(c, cudaMemcpyAsync(dst, src, bytes, k, c->stream));
+    return SIPF_OK;
+}
+
+int check_status(sipf_ctx* c) {
+    int st = 0;
+    SIPF_CUDA(c, cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    SIPF_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (st) {
+        SIPF_CUDA(c, cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+        if (st & kStatusNonfinite)
+            return fail(c, SIPF_ENONFINITE, "a particle position became non-finite and was reset");
+        return fail(c, SIPF_EINTERNAL,
+                    std::string("device consistency check failed (status ") +
+                        std::to_string(st) + ")");
+    }
+    return SIPF_OK;
+}
+
+// Fixed-point scale 2^S of the deposit: the total contribution of all
+// particles, sum exp(loga - logref) <= N e^t (Corollary mass: M <= M0 e^t),
+// stays below 2^61 after scaling.
+int deposit_shift(const sipf_ctx* c) {
+    const double bound = log2(static_cast<double>(c->N)) + c->time * 1.4426950408889634 + 2.0;
+    int S = static_cast<int>(floor(61.0 - bound));
+    if (S > 60) S = 60;
+    if (S < 0) S = 0;
+    return S;
+}
+
+DepositArgs deposit_args(const sipf_ctx* c) {
+    DepositArgs d;
+    d.logref = c->logref;
+    d.scale = ldexpf(1.0f, deposit_shift(c));
+    return d;
+}
+
+// Converts the integer accumulator to u_bar = a R_h summed: 2^-S e^logref / h^3.
+float acc_to_u(const sipf_ctx* c) {
+    return static_cast<float>(ldexp(exp(c->logref), -deposit_shift(c)) / (c->h * c->h * c->h));
+}
+
+PushArgs push_args(const sipf_ctx* c, double dt, uint32_t n, int push) {
+    PushArgs a;
+    a.H = c->H;
+    a.drift = static_cast<float>(c->p.chi * dt / c->h);
+    a.noise = static_cast<float>(sqrt(2.0 * c->p.Du * dt) / c->h);
+    a.tau = static_cast<float>(dt);
+    a.n = n;
+    a.k0 = static_cast<uint32_t>(c->p.seed);
+    a.k1 = static_cast<uint32_t>(c->p.seed >> 32);
+    a.push = push;
+    return a;
+}
+
+SpectralArgs spectral_args(const sipf_ctx* c, double dt, float react_scale, int full) {
+    SpectralArgs s;
+    s.tau = static_cast<float>(dt);
+    s.react_scale = react_scale;
+    s.gamma = static_cast<float>(c->p.gamma);
+    s.alpha = static_cast<float>(c->p.alpha);
+    s.v_update = c->p.v_update;
+    s.diffusion = c->p.diffusion;
+    s.two_pi_over_L = static_cast<float>(2.0 * M_PI / c->L);
+    const double k1 = (2.0 * M_PI / c->L) * (2.0 * M_PI / c->L);
+    const double R[2] = {c->p.beta, 1.0}, D[2] = {c->p.Dm, c->p.Dw};
+    float* hi[2] = {&s.m_r0_hi, &s.w_r0_hi};
+    float* lo[2] = {&s.m_r0_lo, &s.w_r0_lo};
+    float* cc[2] = {&s.m_c, &s.w_c};
+    for (int f = 0; f < 2; ++f) {
+        const bool impl = c->p.diffusion == SIPF_DIFFUSION_IMPLICIT;
+        const double r0 = impl ? 1.0 / (1.0 + dt * R[f]) : exp(-dt * R[f]);
+        *hi[f] = static_cast<float>(r0);
+        *lo[f] = static_cast<float>(r0 - static_cast<double>(*hi[f]));
+        *cc[f] = static_cast<float>(impl ? dt * D[f] * k1 * r0 : dt * D[f] * k1);
+    }
+    s.filter = (c->p.H0 > 0.0 && c->p.H0 < c->H) ? 1 : 0;
+    s.inv_H0sq_2pi2 = s.filter ? static_cast<float>(2.0 * M_PI * M_PI / (c->p.H0 * c->p.H0)) : 0.f;
+    s.out_scale = static_cast<float>(1.0 / (static_cast<double>(c->H) * c->H * c->H));
+    // without the filter the v spectrum used for dv/dx, dv/dy is never
+    // transformed along z, so its inverse carries H^2 instead of H^3
+    s.out_scale_xy = s.filter ? s.out_scale
+                              : static_cast<float>(1.0 / (static_cast<double>(c->H) * c->H));
+    s.write_v = full;
+    s.do_mw = full;
+    return s;
+}
+
+// Bin the store in buffer 1 into buffer 0 (positions unchanged).
+int bin_initial(sipf_ctx* c) {
+    c->cur = 1;
+    const PushArgs a = push_args(c, 0.0, 0, 0);
+    SIPF_CUDA(c, launch_count(c, a));
+    SIPF_CUDA(c, launch_scan(c));
+    SIPF_CUDA(c, launch_scatter(c, a, deposit_args(c), 0, 1));
+    c->cur = 0;
+    return SIPF_OK;
+}
+
+// Deposit the current particles into the accumulator (Alg. 1).
+int deposit_current(sipf_ctx* c) {
+    const PushArgs a = push_args(c, 0.0, 0, 0);
+    SIPF_CUDA(c, launch_scatter(c, a, deposit_args(c), 1, 0));
+    return SIPF_OK;
+}
+
+int enqueue_step(sipf_ctx* c, double dt) {
+    const uint32_t n = static_cast<uint32_t>(c->step + 1);
+    const PushArgs a = push_args(c, dt, n, 1);
+    const DepositArgs d = deposit_args(c);
+    const float u_scale = acc_to_u(c);
+    SIPF_CUDA(c, launch_count(c, a));
+    SIPF_CUDA(c, launch_scan(c));
+    SIPF_CUDA(c, launch_scatter(c, a, d, 1, 1));
+    SIPF_CUDA(c, launch_spectral_step(c, spectral_args(c, dt, u_scale, 1)));
+    c->cur ^= 1;
+    c->step += 1;
+    c->time += dt;
+    return SIPF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sipf_strerror(int code) {
+    switch (code) {
+        case SIPF_OK: return "success";
+        case SIPF_EINVAL: return "invalid argument";
+        case SIPF_ENOMEM: return "out of memory";
+        case SIPF_ECUDA: return "CUDA error";
+        case SIPF_EUNSUPPORTED: return "unsupported configuration";
+        case SIPF_ENONFINITE: return "non-finite particle position";
+        case SIPF_EINTERNAL: return "device consistency check failed";
+        default: return "unknown error";
+    }
+}
+
+const char* sipf_last_error(const sipf_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+int sipf_create(const sipf_grid* grid, int64_t N, const sipf_params* params, void* stream,
+                sipf_ctx** out) {
+    if (!out || !grid || !params) return SIPF_EINVAL;
+    *out = nullptr;
+    std::string why;
+    if (N < 1 || N >= (int64_t{1} << 31)) return SIPF_EINVAL;
+    if (!(isfinite(grid->L) && grid->L > 0.0)) return SIPF_EINVAL;
+    for (int k = 0; k < 3; ++k)
+        if (!isfinite(grid->origin[k])) return SIPF_EINVAL;
+    if (grid->H == 256) return SIPF_EUNSUPPORTED;
+    if (!supported_H(grid->H)) return SIPF_EINVAL;
+    if (check_params(params, &why) != SIPF_OK) return SIPF_EINVAL;
+
+    sipf_ctx* c = new (std::nothrow) sipf_ctx();
+    if (!c) return SIPF_ENOMEM;
+    c->H = grid->H;
+    c->L = grid->L;
+    c->h = grid->L / grid->H;
+    for (int k = 0; k < 3; ++k) c->origin[k] = grid->origin[k];
+    c->N = N;
+    c->p = *params;
+    c->stream = static_cast<cudaStream_t>(stream);
+    cudaGetDevice(&c->device);
+    const size_t H3 = static_cast<size_t>(c->H) * c->H * c->H;
+    c->kxp = c->H / 2 + 2;
+    const size_t spec = static_cast<size_t>(c->H) * c->H * c->kxp;
+    bool ok = true;
+    for (int b = 0; b < 2; ++b) {
+        ok = ok && dalloc(&c->sx[b], N) == cudaSuccess && dalloc(&c->sy[b], N) == cudaSuccess &&
+             dalloc(&c->sz[b], N) == cudaSuccess && dalloc(&c->loga[b], N) == cudaSuccess &&
+             dalloc(&c->id[b], N) == cudaSuccess;
+    }
+    ok = ok && dalloc(&c->count, H3) == cudaSuccess && dalloc(&c->cell_start, H3 + 1) == cudaSuccess &&
+         dalloc(&c->scan_tmp, static_cast<size_t>(scan_tiles(static_cast<int>(H3))) + 1) == cudaSuccess &&
+         dalloc(&c->acc, H3) == cudaSuccess && dalloc(&c->v, H3) == cudaSuccess &&
+         dalloc(&c->m, H3) == cudaSuccess && dalloc(&c->w, H3) == cudaSuccess &&
+         dalloc(&c->gx, H3) == cudaSuccess && dalloc(&c->gy, H3) == cudaSuccess &&
+         dalloc(&c->gz, H3) == cudaSuccess && dalloc(&c->specM, spec) == cudaSuccess &&
+         dalloc(&c->specW, spec) == cudaSuccess && dalloc(&c->specV, spec) == cudaSuccess &&
+         dalloc(&c->specB, spec) == cudaSuccess && dalloc(&c->twiddle, c->H) == cudaSuccess &&
+         dalloc(&c->status, 1) == cudaSuccess && dalloc(&c->voff, 1) == cudaSuccess &&
+         dalloc(&c->diag_tmp, diag_scratch_doubles()) == cudaSuccess &&
+         dalloc(&c->diag_ll, diag_scratch_ll()) == cudaSuccess &&
+         dalloc(&c->diag_out, 8) == cudaSuccess;
+    const bool filter = params->H0 > 0.0 && params->H0 < grid->H;
+    if (ok && filter) ok = dalloc(&c->specA, spec) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return SIPF_ENOMEM;
+    }
+    std::vector<float2> tw(c->H);
+    fill_twiddles(c->H, tw.data());
+    cudaError_t e = cudaMemcpy(c->twiddle, tw.data(), c->H * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->count, 0, H3 * sizeof(int32_t), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, H3 * sizeof(long long), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return SIPF_ECUDA;
+    }
+    *out = c;
+    return SIPF_OK;
+}
+
+int sipf_set_state(sipf_ctx* c, const float* x, const double* mass, const uint32_t* id,
+                   const float* v, const float* m, const float* w, int where) {
+    if (!c) return SIPF_EINVAL;
+    if (!x || !mass || !v || !m || !w) return fail(c, SIPF_EINVAL, "NULL input pointer");
+    if (where != SIPF_HOST && where != SIPF_DEVICE) return fail(c, SIPF_EINVAL, "bad where");
+    const size_t N = static_cast<size_t>(c->N);
+    const size_t H3 = static_cast<size_t>(c->H) * c->H * c->H;
+    // reference log-mass logref = log(M0 / N) from the masses (host FP64 sum)
+    std::vector<double> hm;
+    const double* mp = mass;
+    if (where == SIPF_DEVICE) {
+        hm.resize(N);
+        SIPF_CUDA(c, cudaMemcpyAsync(hm.data(), mass, N * sizeof(double), cudaMemcpyDeviceToHost,
+                                     c->stream));
+        SIPF_CUDA(c, cudaStreamSynchronize(c->stream));
+        mp = hm.data();
+    }
+    double M0 = 0.0;
+    for (size_t i = 0; i < N; ++i) {
+        if (!(isfinite(mp[i]) && mp[i] >= 0.0))
+            return fail(c, SIPF_EINVAL, "masses must be finite and >= 0");
+        M0 += mp[i];
+    }
+    c->logref = M0 > 0.0 ? log(M0 / static_cast<double>(N)) : 0.0;
+    c->step = 0;
+    c->time = 0.0;
+    // upload into buffer 1 (unordered), then bin into buffer 0
+    float* xin = nullptr;
+    double* min_ = nullptr;
+    if (where == SIPF_HOST) {
+        SIPF_CUDA(c, dalloc(&xin, 3 * N));
+        SIPF_CUDA(c, dalloc(&min_, N));
+        int r = copy_in(c, xin, x, 3 * N * sizeof(float), SIPF_HOST);
+        if (r == SIPF_OK) r = copy_in(c, min_, mass, N * sizeof(double), SIPF_HOST);
+        if (r != SIPF_OK) {
+            cudaFree(xin);
+            cudaFree(min_);
+            return r;
+        }
+    }
+    int r = SIPF_OK;
+    cudaError_t e = launch_wrap_positions(c, where == SIPF_HOST ? xin : x, 1);
+    if (e == cudaSuccess) e = launch_log_mass(c, where == SIPF_HOST ? min_ : mass, 1);
+    if (e == cudaSuccess) {
+        if (id) {
+            r = copy_in(c, c->id[1], id, N * sizeof(uint32_t), where);
+        } else {
+            e = launch_iota(c, 1);
+        }
+    }
+    if (e == cudaSuccess && r == SIPF_OK) {
+        // offset for the v transform: the mean of v^(0) (only derivatives of
+        // the v spectrum are used, so any constant may be removed first)
+        std::vector<float> hv;
+        const float* vp = v;
+        if (where == SIPF_DEVICE) {
+            hv.resize(H3);
+            e = cudaMemcpyAsync(hv.data(), v, H3 * sizeof(float), cudaMemcpyDeviceToHost,
+                                c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            vp = hv.data();
+        }
+        double vs = 0.0;
+        for (size_t i = 0; e == cudaSuccess && i < H3; ++i) vs += vp[i];
+        c->voff_host = static_cast<float>(vs / static_cast<double>(H3));
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->voff, &c->voff_host, sizeof(float), cudaMemcpyHostToDevice,
+                                c->stream);
+    }
+    if (e == cudaSuccess && r == SIPF_OK) {
+        r = copy_in(c, c->v, v, H3 * sizeof(float), where);
+        if (r == SIPF_OK) r = copy_in(c, c->m, m, H3 * sizeof(float), where);
+        if (r == SIPF_OK) r = copy_in(c, c->w, w, H3 * sizeof(float), where);
+    }
+    if (e == cudaSuccess && r == SIPF_OK) r = bin_initial(c);
+    if (e == cudaSuccess && r == SIPF_OK) {
+        // grad v^(0) from the DFT of v^(0) (tau = 0: no reaction, v unchanged)
+        e = launch_spectral_step(c, spectral_args(c, 0.0, 0.0f, 0));
+    }
+    if (e == cudaSuccess && r == SIPF_OK) e = cudaStreamSynchronize(c->stream);
+    if (xin) cudaFree(xin);
+    if (min_) cudaFree(min_);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sipf_set_state");
+    if (r != SIPF_OK) return r;
+    r = check_status(c);
+    if (r != SIPF_OK) return r;
+    c->state_set = true;
+    return SIPF_OK;
+}
+
+int sipf_step(sipf_ctx* c, double dt, int64_t k) {
+    if (!c) return SIPF_EINVAL;
+    if (!c->state_set) return fail(c, SIPF_EINVAL, "sipf_set_state has not been called");
+    if (!(isfinite(dt) && dt > 0.0 && dt <= 0.5))
+        return fail(c, SIPF_EINVAL, "dt must satisfy 0 < dt <= 0.5");
+    if (k < 0) return fail(c, SIPF_EINVAL, "k must be >= 0");
+    for (int64_t i = 0; i < k; ++i) {
+        const int r = enqueue_step(c, dt);
+        if (r != SIPF_OK) return r;
+    }
+    return SIPF_OK;
+}
+
+int sipf_fields(sipf_ctx* c, uint32_t mask, float* dst, int where) {
+    if (!c) return SIPF_EINVAL;
+    if (!dst || (mask & ~127u)) return fail(c, SIPF_EINVAL, "bad dst or mask");
+    if (where != SIPF_HOST && where != SIPF_DEVICE) return fail(c, SIPF_EINVAL, "bad where");
+    if (!c->state_set) return fail(c, SIPF_EINVAL, "sipf_set_state has not been called");
+    const size_t H3 = static_cast<size_t>(c->H) * c->H * c->H;
+    const float* src[7] = {nullptr, c->v, c->m, c->w, c->gx, c->gy, c->gz};
+    float* tmp = nullptr;
+    size_t off = 0;
+    for (int b = 0; b < 7; ++b) {
+        if (!(mask & (1u << b))) continue;
+        if (b == 0) {
+            int r = deposit_current(c);
+            if (r != SIPF_OK) return r;
+            if (where == SIPF_DEVICE) {
+                SIPF_CUDA(c, launch_acc_to_float(c, dst + off, acc_to_u(c)));
+            } else {
+                SIPF_CUDA(c, dalloc(&tmp, H3));
+                cudaError_t e = launch_acc_to_float(c, tmp, acc_to_u(c));
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(dst + off, tmp, H3 * sizeof(float), cudaMemcpyDeviceToHost,
+                                        c->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+                cudaFree(tmp);
+                if (e != cudaSuccess) return cuda_fail(c, e, "sipf_fields(U)");
+            }
+        } else {
+            int r = copy_out(c, dst + off, src[b], H3 * sizeof(float), where);
+            if (r != SIPF_OK) return r;
+        }
+        off += H3;
+    }
+    return check_status(c);
+}
+
+int sipf_particle_state(sipf_ctx* c, float* s, double* loga, uint32_t* id, int where) {
+    if (!c) return SIPF_EINVAL;
+    if (where != SIPF_HOST && where != SIPF_DEVICE) return fail(c, SIPF_EINVAL, "bad where");
+    const size_t N = static_cast<size_t>(c->N);
+    const int b = c->cur;
+    int r = SIPF_OK;
+    if (s) {
+        r = copy_out(c, s, c->sx[b], N * sizeof(float), where);
+        if (r == SIPF_OK) r = copy_out(c, s + N, c->sy[b], N * sizeof(float), where);
+        if (r == SIPF_OK) r = copy_out(c, s + 2 * N, c->sz[b], N * sizeof(float), where);
+    }
+    if (r == SIPF_OK && loga) r = copy_out(c, loga, c->loga[b], N * sizeof(double), where);
+    if (r == SIPF_OK && id) r = copy_out(c, id, c->id[b], N * sizeof(uint32_t), where);
+    if (r != SIPF_OK) return r;
+    return check_status(c);
+}
+
+int sipf_particles(sipf_ctx* c, float* x, double* mass, uint32_t* id, int where) {
+    if (!c) return SIPF_EINVAL;
+    if (where != SIPF_HOST && where != SIPF_DEVICE) return fail(c, SIPF_EINVAL, "bad where");
+    const size_t N = static_cast<size_t>(c->N);
+    float* tx = nullptr;
+    double* tm = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (x) {
+        float* dx = x;
+        if (where == SIPF_HOST) {
+            e = dalloc(&tx, 3 * N);
+            dx = tx;
+        }
+        if (e == cudaSuccess) e = launch_export_positions(c, dx);
+        if (e == cudaSuccess && where == SIPF_HOST)
+            e = cudaMemcpyAsync(x, tx, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+    }
+    if (e == cudaSuccess && mass) {
+        double* dm = mass;
+        if (where == SIPF_HOST) {
+            e = dalloc(&tm, N);
+            dm = tm;
+        }
+        if (e == cudaSuccess) e = launch_export_mass(c, dm);
+        if (e == cudaSuccess && where == SIPF_HOST)
+            e = cudaMemcpyAsync(mass, tm, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    }
+    if (e == cudaSuccess && id)
+        e = cudaMemcpyAsync(id, c->id[c->cur], N * sizeof(uint32_t),
+                            where == SIPF_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                            c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (tx) cudaFree(tx);
+    if (tm) cudaFree(tm);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sipf_particles");
+    return check_status(c);
+}
+
+int sipf_cell_start(sipf_ctx* c, int32_t* cell_start, int where) {
+    if (!c || !cell_start) return SIPF_EINVAL;
+    if (where != SIPF_HOST && where != SIPF_DEVICE) return fail(c, SIPF_EINVAL, "bad where");
+    const size_t H3 = static_cast<size_t>(c->H) * c->H * c->H;
+    int r = copy_out(c, cell_start, c->cell_start, (H3 + 1) * sizeof(int32_t), where);
+    if (r != SIPF_OK) return r;
+    return check_status(c);
+}
+
+int sipf_diagnostics(sipf_ctx* c, sipf_diag* out) {
+    if (!c || !out) return SIPF_EINVAL;
+    if (!c->state_set) return fail(c, SIPF_EINVAL, "sipf_set_state has not been called");
+    int r = deposit_current(c);
+    if (r != SIPF_OK) return r;
+    SIPF_CUDA(c, launch_diagnostics(c, acc_to_u(c)));
+    const size_t H3 = static_cast<size_t>(c->H) * c->H * c->H;
+    SIPF_CUDA(c, cudaMemsetAsync(c->acc, 0, H3 * sizeof(long long), c->stream));
+    double h[8];
+    SIPF_CUDA(c, cudaMemcpyAsync(h, c->diag_out, 7 * sizeof(double), cudaMemcpyDeviceToHost,
+                                 c->stream));
+    SIPF_CUDA(c, cudaStreamSynchronize(c->stream));
+    out->mass_particles = h[0];
+    out->mass_grid = h[1] * c->h * c->h * c->h;
+    out->min_u = h[2];
+    out->min_v = h[3];
+    out->min_m = h[4];
+    out->min_w = h[5];
+    out->nonfinite = static_cast<int64_t>(h[6]);
+    out->step = c->step;
+    out->time = c->time;
+    return check_status(c);
+}
+
+int sipf_sync(sipf_ctx* c) {
+    if (!c) return SIPF_EINVAL;
+    return check_status(c);
+}
+
+void sipf_destroy(sipf_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+int sipf_brownian_normals(const uint32_t* ids, int64_t N, uint32_t n, uint64_t seed, float* z,
+                          uint32_t* bits, void* stream) {
+    if (!ids || !z || N < 1 || N >= (int64_t{1} << 31)) return SIPF_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (launch_normals(ids, N, n, seed, z, bits, s) != cudaSuccess) return SIPF_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SIPF_ECUDA;
+    return SIPF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,271 @@
+"""ctypes binding of libsipf.so (the C ABI declared in include/sipf.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Functions keep the C names; buffers are passed as raw
+pointers (``int`` addresses, e.g. ``tensor.data_ptr()`` of a CUDA tensor
+with ``where=SIPF_DEVICE``) or NumPy arrays (``where=SIPF_HOST``).  A missing
+library raises immediately: there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+SIPF_OK = 0
+SIPF_EINVAL = -1
+SIPF_ENOMEM = -2
+SIPF_ECUDA = -3
+SIPF_EUNSUPPORTED = -4
+SIPF_ENONFINITE = -6
+SIPF_EINTERNAL = -7
+
+SIPF_HOST = 0
+SIPF_DEVICE = 1
+
+FIELD_U, FIELD_V, FIELD_M, FIELD_W, FIELD_GX, FIELD_GY, FIELD_GZ = (1, 2, 4, 8, 16, 32, 64)
+FIELD_NAMES = ("u", "v", "m", "w", "gx", "gy", "gz")
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsipf.so")
+
+EXPORTED = (
+    "sipf_create", "sipf_set_state", "sipf_step", "sipf_fields", "sipf_particles",
+    "sipf_particle_state", "sipf_cell_start", "sipf_diagnostics", "sipf_sync",
+    "sipf_destroy", "sipf_strerror", "sipf_last_error", "sipf_brownian_normals",
+)
+
+
+class sipf_grid(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int32), ("L", ctypes.c_double), ("origin", ctypes.c_double * 3)]
+
+
+class sipf_params(ctypes.Structure):
+    _fields_ = [("chi", ctypes.c_double), ("Du", ctypes.c_double), ("Dm", ctypes.c_double),
+                ("Dw", ctypes.c_double), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("diffusion", ctypes.c_int32),
+                ("v_update", ctypes.c_int32), ("H0", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class sipf_diag(ctypes.Structure):
+    _fields_ = [("mass_particles", ctypes.c_double), ("mass_grid", ctypes.c_double),
+                ("min_u", ctypes.c_double), ("min_v", ctypes.c_double),
+                ("min_m", ctypes.c_double), ("min_w", ctypes.c_double),
+                ("step", ctypes.c_int64), ("time", ctypes.c_double),
+                ("nonfinite", ctypes.c_int64)]
+
+
+class SipfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libsipf.so from the package directory (raises if it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I64, I32, U32, U64 = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint32,
+                             ctypes.c_uint64)
+    sig = {
+        "sipf_create": ([ctypes.POINTER(sipf_grid), I64, ctypes.POINTER(sipf_params), P,
+                         ctypes.POINTER(P)], I32),
+        "sipf_set_state": ([P, P, P, P, P, P, P, I32], I32),
+        "sipf_step": ([P, ctypes.c_double, I64], I32),
+        "sipf_fields": ([P, U32, P, I32], I32),
+        "sipf_particles": ([P, P, P, P, I32], I32),
+        "sipf_particle_state": ([P, P, P, P, I32], I32),
+        "sipf_cell_start": ([P, P, I32], I32),
+        "sipf_diagnostics": ([P, ctypes.POINTER(sipf_diag)], I32),
+        "sipf_sync": ([P], I32),
+        "sipf_destroy": ([P], None),
+        "sipf_strerror": ([I32], ctypes.c_char_p),
+        "sipf_last_error": ([P], ctypes.c_char_p),
+        "sipf_brownian_normals": ([P, I64, U32, U64, P, P, P], I32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(buf):
+    """Address of a NumPy array, a CUDA tensor, or an int address."""
+    if buf is None:
+        return None
+    if isinstance(buf, int):
+        return buf
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("host buffers must be C-contiguous")
+        return buf.ctypes.data
+    if hasattr(buf, "data_ptr"):
+        if hasattr(buf, "is_contiguous") and not buf.is_contiguous():
+            raise ValueError("device buffers must be contiguous")
+        return buf.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(buf)}")
+
+
+def _check(code: int, ctx=None):
+    if code != SIPF_OK:
+        lib = load()
+        msg = lib.sipf_strerror(code).decode()
+        if ctx:
+            extra = lib.sipf_last_error(ctx).decode()
+            if extra:
+                msg = f"{msg}: {extra}"
+        raise SipfError(code, msg)
+
+
+# ---------------------------------------------------------------- C names
+
+def sipf_create(grid: sipf_grid, N: int, params: sipf_params, stream: int = 0) -> int:
+    out = ctypes.c_void_p()
+    _check(load().sipf_create(ctypes.byref(grid), int(N), ctypes.byref(params),
+                              ctypes.c_void_p(stream or None), ctypes.byref(out)))
+    return out.value
+
+
+def sipf_set_state(ctx, x, mass, id_, v, m, w, where=SIPF_HOST):
+    _check(load().sipf_set_state(ctx, _ptr(x), _ptr(mass), _ptr(id_), _ptr(v), _ptr(m), _ptr(w),
+                                 where), ctx)
+
+
+def sipf_step(ctx, dt: float, k: int = 1):
+    _check(load().sipf_step(ctx, float(dt), int(k)), ctx)
+
+
+def sipf_fields(ctx, mask: int, dst, where=SIPF_HOST):
+    _check(load().sipf_fields(ctx, mask, _ptr(dst), where), ctx)
+
+
+def sipf_particles(ctx, x=None, mass=None, id_=None, where=SIPF_HOST):
+    _check(load().sipf_particles(ctx, _ptr(x), _ptr(mass), _ptr(id_), where), ctx)
+
+
+def sipf_particle_state(ctx, s=None, loga=None, id_=None, where=SIPF_HOST):
+    _check(load().sipf_particle_state(ctx, _ptr(s), _ptr(loga), _ptr(id_), where), ctx)
+
+
+def sipf_cell_start(ctx, dst, where=SIPF_HOST):
+    _check(load().sipf_cell_start(ctx, _ptr(dst), where), ctx)
+
+
+def sipf_diagnostics(ctx) -> dict:
+    d = sipf_diag()
+    _check(load().sipf_diagnostics(ctx, ctypes.byref(d)), ctx)
+    return {k: getattr(d, k) for k, _ in sipf_diag._fields_}
+
+
+def sipf_sync(ctx):
+    _check(load().sipf_sync(ctx), ctx)
+
+
+def sipf_destroy(ctx):
+    if ctx:
+        load().sipf_destroy(ctx)
+
+
+def sipf_brownian_normals(ids_dev, N: int, n: int, seed: int, z_dev, bits_dev=None, stream=0):
+    _check(load().sipf_brownian_normals(_ptr(ids_dev), int(N), int(n), int(seed), _ptr(z_dev),
+                                        _ptr(bits_dev), ctypes.c_void_p(stream or None)))
+
+
+# ---------------------------------------------------------------- convenience
+
+def make_grid(H: int, L: float, origin=(0.0, 0.0, 0.0)) -> sipf_grid:
+    g = sipf_grid()
+    g.H = H
+    g.L = L
+    for k in range(3):
+        g.origin[k] = origin[k]
+    return g
+
+
+def make_params(p) -> sipf_params:
+    """From any object with chi, Du, Dm, Dw, alpha, beta, gamma (and optional
+    diffusion, v_update, H0, seed) attributes."""
+    q = sipf_params()
+    for name in ("chi", "Du", "Dm", "Dw", "alpha", "beta", "gamma"):
+        setattr(q, name, float(getattr(p, name)))
+    q.diffusion = int(getattr(p, "diffusion", 0))
+    q.v_update = int(getattr(p, "v_update", 0))
+    q.H0 = float(getattr(p, "H0", 0.0))
+    q.seed = int(getattr(p, "seed", 0))
+    return q
+
+
+class Simulation:
+    """Owns one context; host NumPy in and out (SoA conversions included)."""
+
+    def __init__(self, H, L, origin, N, params, stream: int = 0):
+        self.H, self.L, self.N = H, L, N
+        self.ctx = sipf_create(make_grid(H, L, origin), N, make_params(params), stream)
+
+    def close(self):
+        if self.ctx:
+            sipf_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_state(self, x, mass, ids, v, m, w):
+        xs = np.ascontiguousarray(np.asarray(x, dtype=np.float32).T)
+        sipf_set_state(self.ctx, xs, np.ascontiguousarray(mass, dtype=np.float64),
+                       None if ids is None else np.ascontiguousarray(ids, dtype=np.uint32),
+                       np.ascontiguousarray(v, dtype=np.float32),
+                       np.ascontiguousarray(m, dtype=np.float32),
+                       np.ascontiguousarray(w, dtype=np.float32), SIPF_HOST)
+
+    def step(self, dt, k=1):
+        sipf_step(self.ctx, dt, k)
+
+    def fields(self, mask=127) -> dict:
+        nsel = bin(mask).count("1")
+        H3 = self.H ** 3
+        buf = np.empty(nsel * H3, dtype=np.float32)
+        sipf_fields(self.ctx, mask, buf, SIPF_HOST)
+        out, off = {}, 0
+        for b, name in enumerate(FIELD_NAMES):
+            if mask & (1 << b):
+                out[name] = buf[off * H3:(off + 1) * H3].reshape(self.H, self.H, self.H)
+                off += 1
+        return out
+
+    def particles(self):
+        """(x (N, 3) float32 physical, mass (N,) float64, id (N,) uint32), storage order."""
+        x = np.empty(3 * self.N, dtype=np.float32)
+        mass = np.empty(self.N, dtype=np.float64)
+        ids = np.empty(self.N, dtype=np.uint32)
+        sipf_particles(self.ctx, x, mass, ids, SIPF_HOST)
+        return x.reshape(3, self.N).T.copy(), mass, ids
+
+    def particle_state(self):
+        """(s (N, 3) float32 grid units, loga (N,) float64, id (N,) uint32), storage order."""
+        s = np.empty(3 * self.N, dtype=np.float32)
+        loga = np.empty(self.N, dtype=np.float64)
+        ids = np.empty(self.N, dtype=np.uint32)
+        sipf_particle_state(self.ctx, s, loga, ids, SIPF_HOST)
+        return s.reshape(3, self.N).T.copy(), loga, ids
+
+    def cell_start(self):
+        cs = np.empty(self.H ** 3 + 1, dtype=np.int32)
+        sipf_cell_start(self.ctx, cs, SIPF_HOST)
+        return cs
+
+    def diagnostics(self) -> dict:
+        return sipf_diagnostics(self.ctx)

@@ -1,0 +1,103 @@
+"""CPU checks of the C ABI: the library builds, loads, exports every function
+declared in include/sipf.h, its structs have the layout gcc gives the header,
+and argument validation rejects bad input before any CUDA work."""
+
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_2605_20140_gb300 import sipf
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sipf.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(sipf.LIB_PATH):
+        from paper_2605_20140_gb300 import build
+        build.build()
+    return sipf.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sipf_\w+)\s*\(", text)))
+
+
+def test_every_declared_function_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 13
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert sorted(sipf.EXPORTED) == sorted(n for n in names if n in sipf.EXPORTED)
+
+
+def test_struct_layout_matches_the_header():
+    prog = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "sipf.h"
+int main(void) {
+  printf("%zu %zu %zu\n", sizeof(sipf_grid), sizeof(sipf_params), sizeof(sipf_diag));
+  printf("%zu %zu %zu\n", offsetof(sipf_grid, origin), offsetof(sipf_params, diffusion),
+         offsetof(sipf_params, H0));
+  printf("%zu %zu\n", offsetof(sipf_params, seed), offsetof(sipf_diag, nonfinite));
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "l.c")
+        exe = os.path.join(d, "l")
+        open(src, "w").write(prog)
+        subprocess.run(["gcc", "-I", os.path.dirname(HEADER), src, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    got = [int(x) for x in out]
+    want = [ctypes.sizeof(sipf.sipf_grid), ctypes.sizeof(sipf.sipf_params),
+            ctypes.sizeof(sipf.sipf_diag), sipf.sipf_grid.origin.offset,
+            sipf.sipf_params.diffusion.offset, sipf.sipf_params.H0.offset,
+            sipf.sipf_params.seed.offset, sipf.sipf_diag.nonfinite.offset]
+    assert got == want
+
+
+def _create(lib, H=32, L=1.0, N=100, **kw):
+    g = sipf.make_grid(H, L)
+    p = sipf.sipf_params()
+    p.chi, p.Du, p.Dm, p.Dw, p.alpha, p.beta, p.gamma = 0.01, 1e-3, 1e-3, 1e-2, 10, 0.1, 0.5
+    for k, v in kw.items():
+        setattr(p, k, v)
+    out = ctypes.c_void_p()
+    return lib.sipf_create(ctypes.byref(g), N, ctypes.byref(p), None, ctypes.byref(out)), out
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(N=0), sipf.SIPF_EINVAL),
+    (dict(N=1 << 31), sipf.SIPF_EINVAL),
+    (dict(H=48), sipf.SIPF_EINVAL),
+    (dict(H=12), sipf.SIPF_EINVAL),
+    (dict(H=256), sipf.SIPF_EUNSUPPORTED),
+    (dict(L=0.0), sipf.SIPF_EINVAL),
+    (dict(L=float("nan")), sipf.SIPF_EINVAL),
+    (dict(chi=-1.0), sipf.SIPF_EINVAL),
+    (dict(Du=float("inf")), sipf.SIPF_EINVAL),
+    (dict(diffusion=7), sipf.SIPF_EINVAL),
+    (dict(v_update=2), sipf.SIPF_EINVAL),
+])
+def test_create_rejects_bad_arguments_without_touching_the_gpu(lib, kw, code):
+    r, out = _create(lib, **kw)
+    assert r == code and out.value is None
+
+
+def test_null_arguments_and_strerror(lib):
+    assert lib.sipf_create(None, 10, None, None, None) == sipf.SIPF_EINVAL
+    assert lib.sipf_step(None, 1e-3, 1) == sipf.SIPF_EINVAL
+    assert lib.sipf_sync(None) == sipf.SIPF_EINVAL
+    lib.sipf_destroy(None)
+    for code in (0, -1, -2, -3, -4, -6, -7):
+        assert lib.sipf_strerror(code)
+    assert lib.sipf_last_error(None) == b""

@@ -1,0 +1,419 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (float32 path against float64 oracle):
+* integer work -- Philox words, cell keys, cell offsets, per-cell particle
+  sets -- bit-exact;
+* grid fields u_bar, v, m, w after up to 100 steps -- relative L2 <= 1e-5
+  (the target tolerance for the float32 path);
+* grad v -- the spectral derivative of v.  Each step rounds v^n to float32
+  (relative 2^-24 per rounding, two roundings per step), and these
+  independent errors accumulate like sqrt(n); differentiation multiplies
+  white noise by the rms wave number (2 pi / L) H / sqrt(12) per axis.  The
+  bound is 4x that estimate relative to the oracle's ||d_j v|| (and never
+  below 1e-5); see grad_tolerance();
+* particle positions -- periodic difference <= 1e-4 grid units (float32
+  rounding of s < H accumulates ~ulp(H) sqrt(steps));
+* log-masses -- absolute difference <= 1e-6 (float32 increments of size
+  tau |rho - 1| <= tau, summed in float64).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import sipf_oracle as O
+from paper_2605_20140_gb300 import sipf
+from sipf_inputs import Params, workload
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+FIELD_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import os
+    if not os.path.exists(sipf.LIB_PATH):
+        from paper_2605_20140_gb300 import build
+        build.build()
+    sipf.load()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def oracle_state(wl, x=None, mass=None, v=None, m=None, w=None, p=None):
+    return O.make_state(wl.H, wl.L, wl.origin, p or wl.params,
+                        wl.x if x is None else x, wl.mass if mass is None else mass, wl.ids,
+                        wl.v if v is None else v, wl.m if m is None else m,
+                        wl.w if w is None else w)
+
+
+def oracle_fields(st):
+    return {"u": O.density(st), "v": st.v, "m": st.m, "w": st.w,
+            "gx": st.grad_v[0], "gy": st.grad_v[1], "gz": st.grad_v[2]}
+
+
+def by_id(s, loga, ids):
+    order = np.argsort(ids, kind="stable")
+    return s[order], loga[order], ids[order]
+
+
+def periodic_diff(a, b, H):
+    d = np.asarray(a, np.float64) - b
+    return d - H * np.round(d / H)
+
+
+def run_gpu(wl, steps, p=None, x=None, mass=None, v=None, m=None, w=None, dt=None):
+    sim = sipf.Simulation(wl.H, wl.L, wl.origin, wl.N, p or wl.params)
+    sim.set_state(wl.x if x is None else x, wl.mass if mass is None else mass, wl.ids,
+                  wl.v if v is None else v, wl.m if m is None else m, wl.w if w is None else w)
+    if steps:
+        sim.step(dt or wl.dt, steps)
+    return sim
+
+
+# ---------------------------------------------------------------- noise
+
+def test_philox_words_bit_exact_and_normals_close():
+    N = 1 << 16
+    ids = torch.arange(N, dtype=torch.int32, device="cuda").mul_(7919)
+    z = torch.empty(3 * N, dtype=torch.float32, device="cuda")
+    bits = torch.empty(4 * N, dtype=torch.int32, device="cuda")
+    seed, n = 0x1234_5678_9ABC_DEF0, 17
+    sipf.sipf_brownian_normals(ids, N, n, seed, z, bits)
+    idh = ids.cpu().numpy().astype(np.uint32)
+    zero = np.zeros(N, np.uint32)
+    ref_bits = O.philox4x32_10(np.full(N, n, np.uint32), zero, idh, zero, seed & 0xFFFFFFFF,
+                               seed >> 32)
+    got_bits = bits.cpu().numpy().view(np.uint32).reshape(4, N)
+    for k in range(4):
+        np.testing.assert_array_equal(got_bits[k], ref_bits[k])
+    ref = O.brownian_normals(idh, n, seed)
+    got = z.cpu().numpy().reshape(3, N).T
+    np.testing.assert_allclose(got, ref, rtol=2e-6, atol=2e-6)
+
+
+# ---------------------------------------------------------------- binning
+
+def _edge_positions(H, L, n_random, seed):
+    rng = np.random.default_rng(seed)
+    x = (rng.random((n_random, 3)) * L).astype(np.float32)
+    h = L / H
+    special = np.array([[0, 0, 0], [h, 2 * h, 3 * h], [L - h, L - h, L - h],
+                        [np.nextafter(np.float32(L), np.float32(0))] * 3,
+                        [0.5 * L, 0.5 * L, 0.5 * L]], dtype=np.float32)
+    return np.concatenate([special, x])
+
+
+@pytest.mark.parametrize("H", [16, 32, 64, 128])
+def test_binning_cell_offsets_and_sets_bit_exact(H):
+    wl = workload("small", H=H, N=4096)
+    x = _edge_positions(H, wl.L, 4091, H)
+    wl.x = x
+    sim = run_gpu(wl, 0)
+    s, loga, ids = sim.particle_state()
+    cs = sim.cell_start()
+    sim.close()
+    st = oracle_state(wl, x=x)
+    keys = O.cell_keys(st.s, H)
+    np.testing.assert_array_equal(cs.astype(np.int64), O.cell_start(keys, H))
+    # positions are stored exactly (L = 1 and H a power of two)
+    s_id, _, _ = by_id(s, loga, ids)
+    np.testing.assert_array_equal(s_id.astype(np.float64), st.s)
+    # each cell's run holds exactly the oracle's particles of that cell
+    gkeys = O.cell_keys(s.astype(np.float64), H)
+    assert np.all(np.diff(gkeys) >= 0)
+    order = O.canonical_order(keys, st.ids)
+    ref_sorted = st.ids[order]
+    got_sorted = ids[np.lexsort((ids.astype(np.int64), gkeys))]
+    np.testing.assert_array_equal(got_sorted, ref_sorted)
+
+
+def test_binning_after_a_step_without_motion_is_bit_exact():
+    """chi = Du = 0: the push leaves positions unchanged, so the count and
+    scatter passes of a real step must rebuild exactly the oracle's cells."""
+    wl = workload("small", H=32, N=8192)
+    p = Params(chi=0.0, Du=0.0, seed=3)
+    sim = run_gpu(wl, 2, p=p)
+    s, loga, ids = sim.particle_state()
+    cs = sim.cell_start()
+    sim.close()
+    st = oracle_state(wl, p=p)
+    np.testing.assert_array_equal(cs.astype(np.int64), O.cell_start(O.cell_keys(st.s, 32), 32))
+    s_id, _, _ = by_id(s, loga, ids)
+    np.testing.assert_array_equal(s_id.astype(np.float64), st.s)
+
+
+# ---------------------------------------------------------------- deposit / gradient
+
+@pytest.mark.parametrize("name,H,N", [("small", 32, 1 << 15), ("headline", 64, 1 << 18)])
+def test_deposit_matches_oracle_and_conserves_mass(name, H, N):
+    wl = workload(name, H=H, N=N)
+    sim = run_gpu(wl, 0)
+    u = sim.fields(sipf.FIELD_U)["u"]
+    d = sim.diagnostics()
+    sim.close()
+    st = oracle_state(wl)
+    ref = O.density(st)
+    assert rel_l2(u, ref) <= 1e-6
+    assert np.max(np.abs(u - ref)) <= 2e-6 * ref.max()
+    assert u.min() >= 0.0
+    h3 = (wl.L / wl.H) ** 3
+    assert abs(u.astype(np.float64).sum() * h3 - wl.mass.sum()) <= 1e-6 * wl.mass.sum()
+    assert abs(d["mass_grid"] - wl.mass.sum()) <= 1e-9 * wl.mass.sum()
+    assert abs(d["mass_particles"] - wl.mass.sum()) <= 1e-12 * wl.mass.sum()
+
+
+@pytest.mark.parametrize("H", [16, 32, 64, 128])
+def test_initial_spectral_gradient(H):
+    wl = workload("small", H=H, N=1024)
+    sim = run_gpu(wl, 0)
+    f = sim.fields(sipf.FIELD_GX | sipf.FIELD_GY | sipf.FIELD_GZ)
+    sim.close()
+    g = O.spectral_gradient(wl.v.astype(np.float64), wl.L)
+    for k, name in enumerate(("gx", "gy", "gz")):
+        assert rel_l2(f[name], g[k]) <= FIELD_TOL, name
+
+
+def test_gradient_of_a_sine_mode_closed_form():
+    H, L = 64, 2.0
+    q = np.arange(H) * (L / H)
+    Z, Y, X = np.meshgrid(q, q, q, indexing="ij")
+    qv = np.array([3, -5, 7])
+    ph = 2 * np.pi * (qv[0] * X + qv[1] * Y + qv[2] * Z) / L
+    v = (1.0 + 0.3 * np.sin(ph)).astype(np.float32)
+    wl = workload("small", H=H, N=64)
+    wl.L = L
+    wl.x = (wl.x.astype(np.float64) * L).astype(np.float32)
+    sim = run_gpu(wl, 0, v=v)
+    f = sim.fields(sipf.FIELD_GX | sipf.FIELD_GY | sipf.FIELD_GZ)
+    sim.close()
+    for k, name in enumerate(("gx", "gy", "gz")):
+        ref = 0.3 * 2 * np.pi * qv[k] / L * np.cos(ph)
+        assert np.max(np.abs(f[name] - ref)) <= 1e-5 * np.abs(ref).max(), name
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_single_mode_decay(mode):
+    """Massless particles, gamma = alpha = 0: one step multiplies a Fourier
+    mode of m by 1/(1 + tau beta + tau Dm |k|^2) (or the exponential) and of
+    w by 1/(1 + tau + tau Dw |k|^2)."""
+    H, L, tau = 32, 1.0, 0.01
+    p = Params(chi=0.0, Du=0.0, Dm=0.03, Dw=0.07, alpha=0.0, beta=0.4, gamma=0.0, diffusion=mode)
+    q = np.arange(H) * (L / H)
+    Z, Y, X = np.meshgrid(q, q, q, indexing="ij")
+    qv = np.array([2, 1, -3])
+    mf = np.cos(2 * np.pi * (qv[0] * X + qv[1] * Y + qv[2] * Z) / L)
+    wl = workload("small", H=H, N=256)
+    sim = run_gpu(wl, 3, p=p, mass=np.zeros(256), m=(1.5 * mf).astype(np.float32),
+                  w=(0.25 * mf).astype(np.float32), v=np.ones((H, H, H), np.float32), dt=tau)
+    f = sim.fields(sipf.FIELD_M | sipf.FIELD_W | sipf.FIELD_V | sipf.FIELD_U)
+    sim.close()
+    k2 = (2 * np.pi / L) ** 2 * np.sum(qv ** 2)
+    if mode == 0:
+        fm, fw = 1 / (1 + tau * 0.4 + tau * 0.03 * k2), 1 / (1 + tau + tau * 0.07 * k2)
+    else:
+        fm, fw = math.exp(-tau * 0.03 * k2 - tau * 0.4), math.exp(-tau * 0.07 * k2 - tau)
+    assert np.max(np.abs(f["m"] - 1.5 * mf * fm ** 3)) <= 2e-6 * 1.5
+    assert np.max(np.abs(f["w"] - 0.25 * mf * fw ** 3)) <= 2e-6 * 0.25
+    np.testing.assert_array_equal(f["v"], 1.0)
+    np.testing.assert_array_equal(f["u"], 0.0)
+
+
+# ---------------------------------------------------------------- whole steps
+
+def grad_tolerance(st, axis, L):
+    """Expected relative L2 effect on d_axis v of float32 rounding of v^n over
+    st.n steps (4x margin), floored at FIELD_TOL."""
+    H = st.H
+    n = max(st.n, 1)
+    k_rms = 2 * np.pi / L * H / np.sqrt(12.0)
+    dv_rms = 2.0 ** -24 * np.sqrt(2.0 * n / 3.0) * np.sqrt(np.mean(st.v ** 2))
+    g_rms = np.sqrt(np.mean(st.grad_v[axis] ** 2))
+    return max(FIELD_TOL, 4.0 * k_rms * dv_rms / g_rms)
+
+
+def _compare(sim, st, wl, field_tol=FIELD_TOL, pos_tol=1e-4, loga_tol=1e-6):
+    f = sim.fields()
+    ref = oracle_fields(st)
+    errs = {k: rel_l2(f[k], ref[k]) for k in ref}
+    tols = {k: field_tol for k in ("u", "v", "m", "w")}
+    for axis, k in enumerate(("gx", "gy", "gz")):
+        tols[k] = grad_tolerance(st, axis, wl.L)
+    s, loga, ids = sim.particle_state()
+    s_id, l_id, i_id = by_id(s, loga, ids)
+    np.testing.assert_array_equal(i_id, st.ids)
+    dpos = np.abs(periodic_diff(s_id, st.s, wl.H))
+    dloga = np.max(np.abs(l_id - st.loga))
+    report = {"errs": errs, "tols": tols, "dpos": float(dpos.max()), "dloga": float(dloga)}
+    for k, e in errs.items():
+        assert e <= tols[k], (k, report)
+    assert dpos.max() <= pos_tol, report
+    assert dloga <= loga_tol, report
+    return errs
+
+
+@pytest.mark.parametrize("steps", [1, 10])
+def test_steps_match_oracle_small(steps):
+    wl = workload("small", H=32, N=1 << 15)
+    sim = run_gpu(wl, steps)
+    st = O.run(oracle_state(wl), wl.dt, steps)
+    _compare(sim, st, wl)
+    sim.close()
+
+
+def test_hundred_steps_match_oracle_small_workload():
+    """The 32^3 / 2^15-particle workload for 100 steps on identical Philox
+    noise: grid fields within relative L2 1e-5."""
+    wl = workload("small")
+    sim = run_gpu(wl, wl.steps)
+    st = O.run(oracle_state(wl), wl.dt, wl.steps)
+    errs = _compare(sim, st, wl)
+    d = sim.diagnostics()
+    sim.close()
+    assert d["step"] == 100 and abs(d["time"] - 0.1) < 1e-12
+    od = O.diagnostics(st)
+    # d log M / dt = <rho(w) - 1>: a w error dw moves log M by at most
+    # T max|rho'| dw = 0.1 * 2 * (1e-5 * max w) over the run.
+    tol_m = wl.dt * wl.steps * 2.0 * FIELD_TOL * float(np.abs(st.w).max())
+    assert abs(d["mass_particles"] - od["mass_particles"]) <= tol_m * od["mass_particles"]
+    print("rel-L2 after 100 steps:", {k: f"{v:.2e}" for k, v in errs.items()})
+
+
+def test_hundred_steps_match_oracle_64_grid():
+    wl = workload("headline", H=64, N=1 << 18)
+    wl.dt = 5e-4
+    sim = run_gpu(wl, 100)
+    st = O.run(oracle_state(wl), wl.dt, 100)
+    _compare(sim, st, wl)
+    sim.close()
+
+
+def test_headline_size_one_step():
+    """Full 128^3 / 2^22 workload, in the launch configuration the benchmark
+    times: one step against the oracle."""
+    wl = workload("headline")
+    sim = run_gpu(wl, 1)
+    st = O.run(oracle_state(wl), wl.dt, 1)
+    _compare(sim, st, wl)
+    sim.close()
+
+
+def test_mass_lemma_bounds_per_particle():
+    wl = workload("small", H=32, N=1 << 15)
+    sim = run_gpu(wl, 0)
+    _, l0, i0 = by_id(*sim.particle_state())
+    sim.step(wl.dt, 1)
+    _, l1, i1 = by_id(*sim.particle_state())
+    sim.step(wl.dt, 49)
+    d = sim.diagnostics()
+    sim.close()
+    tau = wl.dt
+    ratio = np.exp(l1 - l0)
+    assert np.all(ratio >= 1 - tau) and np.all(ratio <= 1 + tau)
+    M0 = wl.mass.sum()
+    assert M0 * math.exp(-d["time"]) <= d["mass_particles"] <= M0 * math.exp(d["time"])
+    assert d["min_u"] >= 0 and d["min_v"] > 0 and d["nonfinite"] == 0
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_single_particle():
+    wl = workload("small", H=16, N=1)
+    wl.x = np.array([[0.3, 0.6, 0.9]], dtype=np.float32)
+    wl.mass = np.array([0.7])
+    wl.ids = np.array([5], dtype=np.uint32)
+    sim = run_gpu(wl, 5)
+    st = O.run(oracle_state(wl), wl.dt, 5)
+    _compare(sim, st, wl)
+    sim.close()
+
+
+def test_all_particles_in_one_cell():
+    """Dense degenerate case: every particle in one cell (whole-warp deposit path)."""
+    wl = workload("small", H=32, N=5000)
+    rng = np.random.default_rng(2)
+    wl.x = ((7 + rng.random((5000, 3))) / 32).astype(np.float32)
+    sim = run_gpu(wl, 0)
+    u = sim.fields(sipf.FIELD_U)["u"]
+    cs = sim.cell_start()
+    sim.step(wl.dt, 3)
+    st0 = oracle_state(wl)
+    assert rel_l2(u, O.density(st0)) <= 1e-6
+    assert np.count_nonzero(np.diff(cs)) == 1
+    st = O.run(st0, wl.dt, 3)
+    _compare(sim, st, wl)
+    sim.close()
+
+
+def test_massless_particles_and_zero_mass_mix():
+    wl = workload("small", H=32, N=4096)
+    wl.mass = np.where(np.arange(4096) % 3 == 0, 0.0, 1.0 / 4096)
+    sim = run_gpu(wl, 4)
+    st = O.run(oracle_state(wl), wl.dt, 4)
+    f = sim.fields(sipf.FIELD_U | sipf.FIELD_M)
+    assert rel_l2(f["u"], O.density(st)) <= FIELD_TOL
+    assert rel_l2(f["m"], st.m) <= FIELD_TOL
+    sim.close()
+
+
+def test_invalid_step_arguments():
+    wl = workload("small", H=16, N=64)
+    sim = sipf.Simulation(wl.H, wl.L, wl.origin, wl.N, wl.params)
+    with pytest.raises(sipf.SipfError):
+        sim.step(1e-3, 1)              # state not set
+    sim.set_state(wl.x, wl.mass, wl.ids, wl.v, wl.m, wl.w)
+    for dt in (0.0, -1e-3, 0.6, float("nan")):
+        with pytest.raises(sipf.SipfError):
+            sim.step(dt, 1)
+    with pytest.raises(sipf.SipfError):
+        sim.step(1e-3, -1)
+    with pytest.raises(sipf.SipfError):
+        sim.set_state(wl.x, -wl.mass, wl.ids, wl.v, wl.m, wl.w)
+    sim.step(1e-3, 0)
+    sim.close()
+
+
+def test_runs_are_bit_reproducible_and_stream_independent():
+    wl = workload("small", H=32, N=1 << 15)
+    outs = []
+    for use_stream in (False, True):
+        stream = torch.cuda.Stream() if use_stream else None
+        sim = sipf.Simulation(wl.H, wl.L, wl.origin, wl.N, wl.params,
+                              stream=stream.cuda_stream if stream else 0)
+        sim.set_state(wl.x, wl.mass, wl.ids, wl.v, wl.m, wl.w)
+        sim.step(wl.dt, 10)
+        f = sim.fields()
+        s, l, i = by_id(*sim.particle_state())
+        outs.append((f, s, l))
+        sim.close()
+    for k in outs[0][0]:
+        np.testing.assert_array_equal(outs[0][0][k], outs[1][0][k])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    np.testing.assert_array_equal(outs[0][2], outs[1][2])
+
+
+def test_device_buffers_in_and_out():
+    wl = workload("small", H=32, N=4096)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    xs = dev(wl.x.T.copy())
+    ctx = sipf.sipf_create(sipf.make_grid(wl.H, wl.L), wl.N, sipf.make_params(wl.params))
+    try:
+        sipf.sipf_set_state(ctx, xs, dev(wl.mass), dev(wl.ids.view(np.int32)), dev(wl.v),
+                            dev(wl.m), dev(wl.w), sipf.SIPF_DEVICE)
+        sipf.sipf_step(ctx, wl.dt, 2)
+        out = torch.empty(2 * wl.H ** 3, dtype=torch.float32, device="cuda")
+        sipf.sipf_fields(ctx, sipf.FIELD_M | sipf.FIELD_W, out, sipf.SIPF_DEVICE)
+        torch.cuda.synchronize()
+    finally:
+        sipf.sipf_destroy(ctx)
+    st = O.run(oracle_state(wl), wl.dt, 2)
+    o = out.cpu().numpy().reshape(2, wl.H, wl.H, wl.H)
+    assert rel_l2(o[0], st.m) <= FIELD_TOL and rel_l2(o[1], st.w) <= FIELD_TOL
