@@ -1,0 +1,320 @@
+#!/usr/bin/env python
+"""Throughput of the SIPF-W step on the 128^3-grid / 2^22-particle workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sipf|reference]
+
+One step = one pass of the whole hot path (count, scan, scatter+deposit,
+three spectral passes) over the synthetic headline workload (three Gaussian
+tumour seeds at seeded centres, sigma 0.04, unit periodic cube, dt 5e-4).
+Prints one JSON line on rank 0.  Under torchrun (N > 1) every rank runs an
+independent replica on its own GPU (no data-path collective); the timed
+region is bracketed by a barrier and the slowest rank's time is used.
+
+--impl reference times the FP64 oracle on the host cores (the paper ships
+no code; the oracle is the reference arm), each step on a particle sample
+of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s at 128^3 grid, 4M particles"
+UNIT = "particle-steps/s"
+WORKLOAD = "headline: 128^3 grid, 2^22 particles, 3 Gaussian seeds (sigma 0.04), dt 5e-4"
+# Algorithmic bytes (what the method must move): per particle-step read X
+# (12 B) + log a (8 B), write X' (12 B) + log a' (8 B); per node-step the 15
+# float32 field touches of the reaction, solve, gather and deposit.
+ALGO_B_PER_PARTICLE = 40
+ALGO_B_PER_NODE = 60
+# share of the per-node bytes that belongs to the scatter/deposit kernel
+# (gather of dv/dx, dv/dy, dv/dz, w: 16 B; deposit of u: 4 B)
+SCATTER_B_PER_NODE = 20
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def _dist_init(n_gpus):
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def _cpu_baseline(wl_fn, n_sample_steps=1):
+    """The FP64 oracle as it stands on this host: one full step of the
+    workload (about 10-30 s of CPU work)."""
+    from oracle import sipf_oracle as O
+    wl = wl_fn()
+    st = O.make_state(wl.H, wl.L, wl.origin, wl.params, wl.x, wl.mass, wl.ids, wl.v, wl.m, wl.w)
+    t0 = time.perf_counter()
+    for _ in range(n_sample_steps):
+        st = O.step(st, wl.dt)
+    dt = time.perf_counter() - t0
+    return {"value": wl.N * n_sample_steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n_sample_steps} full step(s) of the 128^3 / 2^22 workload, "
+                      f"NumPy FP64, single thread, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from oracle import sipf_oracle as O
+    from sipf_inputs import workload
+    n_sample = 1 << 16
+    wl = workload("headline", N=n_sample)
+    st = O.make_state(wl.H, wl.L, wl.origin, wl.params, wl.x, wl.mass, wl.ids, wl.v, wl.m, wl.w)
+    for _ in range(args.warmup):
+        st = O.step(st, wl.dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st = O.step(st, wl.dt)
+    el = time.perf_counter() - t0
+    value = n_sample * args.steps / el
+    sample = (f"each step: one oracle step on the full 128^3 grid with a 2^16-particle sample "
+              f"of the workload ({el / args.steps:.2f} s/step)")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD + " (particle-sampled)", "H": wl.H, "N": n_sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_sipf(args, rank, world, local):
+    import torch
+    from paper_2605_20140_gb300 import sipf
+    from sipf_inputs import workload
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the SIPF-W path has no CPU fallback)")
+    torch.cuda.set_device(local)
+    if not os.path.exists(sipf.LIB_PATH):
+        from paper_2605_20140_gb300 import build
+        build.build()
+    sipf.load()
+    wl = workload("headline", seed=rank)
+    N, H, dt = wl.N, wl.H, wl.dt
+    stream = torch.cuda.Stream()
+    sim = sipf.Simulation(H, wl.L, wl.origin, N, wl.params, stream=stream.cuda_stream)
+    sim.set_state(wl.x, wl.mass, wl.ids, wl.v, wl.m, wl.w)
+
+    # ---- device-resident timed region
+    sim.step(dt, args.warmup)
+    sipf.sipf_sync(sim.ctx)
+    clocks = ClockSampler(local)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    _barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    sipf.sipf_profile(sim.ctx, True)
+    e0.record(stream)
+    sim.step(dt, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sipf.sipf_profile(sim.ctx, False)
+    _barrier(world)
+    clk = clocks.stop()
+    ms_total = _max_over_ranks(e0.elapsed_time(e1), world)
+    prof = sipf.sipf_profile_read(sim.ctx)
+    sipf.sipf_sync(sim.ctx)
+    ms_step = ms_total / args.steps
+    value = world * N * args.steps / (ms_total * 1e-3)
+
+    # ---- roofline of the dominant kernel group (CUDA events on the launching stream)
+    hbm, peak_kind = _peaks()
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_launches = prof[dom]
+    per_launch_s = dom_ms * 1e-3 / max(dom_launches, 1)
+    algo = {"scatter_deposit": ALGO_B_PER_PARTICLE * N + SCATTER_B_PER_NODE * H ** 3}
+    algo_bytes = algo.get(dom)
+    roofline = None
+    if algo_bytes is not None:
+        achieved = algo_bytes / per_launch_s / 1e9
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+                    "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
+                    "traffic": None, "algorithmic_bytes": algo_bytes}
+    step_bytes = ALGO_B_PER_PARTICLE * N + ALGO_B_PER_NODE * H ** 3
+    step_roofline = {"algorithmic_bytes": step_bytes,
+                     "achieved": step_bytes / (ms_step * 1e-3) / 1e9,
+                     "frac": step_bytes / (ms_step * 1e-3) / 1e9 / hbm, "unit": "GB/s"}
+    kernels = {k: {"ms_per_step": v[0] / max(args.steps, 1), "launches": v[1],
+                   "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-12)}
+               for k, v in prof.items()}
+    launches = sum(v[1] for v in prof.values())
+    sim.close()
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        hx = pin(wl.x.T)
+        hm, hid = pin(wl.mass), pin(wl.ids)
+        hv, hmm, hw = pin(wl.v), pin(wl.m), pin(wl.w)
+        out = torch.empty(4 * H ** 3, dtype=torch.float32).pin_memory().numpy()
+        sim2 = sipf.Simulation(H, wl.L, wl.origin, N, wl.params, stream=stream.cuda_stream)
+        sim2.set_state(hx.T, hm, hid, hv, hmm, hw)          # first call: device set-up
+        sim2.step(dt, 2)
+        sipf.sipf_sync(sim2.ctx)
+        _barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sipf.sipf_set_state(sim2.ctx, hx, hm, hid, hv, hmm, hw, sipf.SIPF_HOST)
+        sipf.sipf_step(sim2.ctx, dt, args.steps)
+        sipf.sipf_fields(sim2.ctx, sipf.FIELD_U | sipf.FIELD_V | sipf.FIELD_M | sipf.FIELD_W,
+                         out, sipf.SIPF_HOST)
+        el = _max_over_ranks(time.perf_counter() - t0, world)
+        sim2.close()
+        h2d = hx.nbytes + hm.nbytes + hid.nbytes + hv.nbytes + hmm.nbytes + hw.nbytes
+        d2h = out.nbytes
+        e2e = {"value": world * N * args.steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "job": f"set_state from pinned host + {args.steps} steps + u,v,m,w to host"}
+
+    if rank != 0:
+        return 0
+    cpu = None if args.no_cpu_baseline else _cpu_baseline(lambda: workload("headline"))
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 (f64 log-mass and reductions)", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "H": H, "N": N, "dt": dt,
+                      "parallelism": f"replicas x{world}",
+                      "l2": "no flush: the step's working set (~300 MB) exceeds the 129 MB L2"},
+           "roofline": roofline, "step_roofline": step_roofline, "kernels": kernels,
+           "gpu_launches": launches, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["sipf", "reference"], default="sipf")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local = _dist_init(args.gpus)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, rank, world)
+        return run_sipf(args, rank, world, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

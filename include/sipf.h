@@ -182,6 +182,19 @@ const char* sipf_last_error(const sipf_ctx* ctx);
 int sipf_brownian_normals(const uint32_t* ids, int64_t N, uint32_t n, uint64_t seed,
                           float* z, uint32_t* bits, void* stream);
 
+/* Tracing.  sipf_profile(ctx, 1) starts recording CUDA events (on the
+ * context's stream) between the kernel groups of each subsequent step, for
+ * at most 4096 steps; sipf_profile(ctx, 0) stops; enabling again clears the
+ * record.  Groups, in launch order: 0 count, 1 scan (3 launches),
+ * 2 scatter_deposit, 3 forward_xy, 4 z_multiply, 5 inverse_xy (names from
+ * sipf_profile_name).  sipf_profile_read synchronises the stream and writes,
+ * for k < n, the summed device time ms[k] (milliseconds) and the number of
+ * kernel launches launches[k] over the recorded steps.  Errors: SIPF_EINVAL,
+ * SIPF_ECUDA. */
+int sipf_profile(sipf_ctx* ctx, int enable);
+int sipf_profile_read(sipf_ctx* ctx, double* ms, int64_t* launches, int n);
+const char* sipf_profile_name(int k);
+
 #ifdef __cplusplus
 }
 #endif

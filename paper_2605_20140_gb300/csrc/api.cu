@@ -191,15 +191,41 @@ int deposit_current(sipf_ctx* c) {
     return SIPF_OK;
 }
 
+// Event k of the current step (tracing); nullptr when not recording.
+cudaEvent_t prof_event(sipf_ctx* c, int k) {
+    if (!c->prof_on || c->prof_steps >= kProfMaxSteps) return nullptr;
+    const size_t i = static_cast<size_t>(c->prof_steps) * (kProfGroups + 1) + k;
+    while (c->prof_events.size() <= i) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        c->prof_events.push_back(e);
+    }
+    return c->prof_events[i];
+}
+
+cudaError_t prof_mark(sipf_ctx* c, int k) {
+    cudaEvent_t e = prof_event(c, k);
+    return e ? cudaEventRecord(e, c->stream) : cudaSuccess;
+}
+
 int enqueue_step(sipf_ctx* c, double dt) {
     const uint32_t n = static_cast<uint32_t>(c->step + 1);
     const PushArgs a = push_args(c, dt, n, 1);
     const DepositArgs d = deposit_args(c);
     const float u_scale = acc_to_u(c);
+    const SpectralArgs sa = spectral_args(c, dt, u_scale, 1);
+    SIPF_CUDA(c, prof_mark(c, 0));
     SIPF_CUDA(c, launch_count(c, a));
+    SIPF_CUDA(c, prof_mark(c, 1));
     SIPF_CUDA(c, launch_scan(c));
+    SIPF_CUDA(c, prof_mark(c, 2));
     SIPF_CUDA(c, launch_scatter(c, a, d, 1, 1));
-    SIPF_CUDA(c, launch_spectral_step(c, spectral_args(c, dt, u_scale, 1)));
+    SIPF_CUDA(c, prof_mark(c, 3));
+    for (int pass = 0; pass < 3; ++pass) {
+        SIPF_CUDA(c, launch_spectral_pass(c, sa, pass));
+        SIPF_CUDA(c, prof_mark(c, 4 + pass));
+    }
+    if (c->prof_on && c->prof_steps < kProfMaxSteps) c->prof_steps += 1;
     c->cur ^= 1;
     c->step += 1;
     c->time += dt;
@@ -527,8 +553,42 @@ int sipf_sync(sipf_ctx* c) {
 void sipf_destroy(sipf_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
     free_all(c);
     delete c;
+}
+
+int sipf_profile(sipf_ctx* c, int enable) {
+    if (!c) return SIPF_EINVAL;
+    if (enable && !c->prof_on) c->prof_steps = 0;
+    c->prof_on = enable != 0;
+    return SIPF_OK;
+}
+
+int sipf_profile_read(sipf_ctx* c, double* ms, int64_t* launches, int n) {
+    if (!c || !ms || !launches || n < 1) return SIPF_EINVAL;
+    SIPF_CUDA(c, cudaStreamSynchronize(c->stream));
+    static const int per_step[kProfGroups] = {1, 3, 1, 1, 1, 1};
+    for (int k = 0; k < n; ++k) {
+        ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    for (int64_t s = 0; s < c->prof_steps; ++s) {
+        for (int k = 0; k < kProfGroups && k < n; ++k) {
+            const size_t i = static_cast<size_t>(s) * (kProfGroups + 1) + k;
+            float t = 0.f;
+            SIPF_CUDA(c, cudaEventElapsedTime(&t, c->prof_events[i], c->prof_events[i + 1]));
+            ms[k] += t;
+            launches[k] += per_step[k];
+        }
+    }
+    return SIPF_OK;
+}
+
+const char* sipf_profile_name(int k) {
+    static const char* names[kProfGroups] = {"count", "scan", "scatter_deposit", "forward_xy",
+                                             "z_multiply", "inverse_xy"};
+    return (k >= 0 && k < kProfGroups) ? names[k] : "";
 }
 
 int sipf_brownian_normals(const uint32_t* ids, int64_t N, uint32_t n, uint64_t seed, float* z,

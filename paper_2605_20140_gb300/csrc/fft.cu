@@ -109,7 +109,9 @@ __device__ __forceinline__ void dft(float2 (&v)[R]) {
 }
 
 // One Stockham stage of radix R after NS points have been combined.
-// Transform t, element j lives at buf[t * TS + j * ES].
+// Transform t, element j lives at buf[t * TS + j * ES].  Consecutive lanes
+// take consecutive transforms (same butterfly), so a warp's accesses are
+// contiguous when TS == 1 and spread over all banks when TS is odd.
 template <int L, int R, int NS, int NTRANS, int ES, int TS, int NT, int SIGN>
 __device__ __forceinline__ void stage(float2* buf, const float2* tw) {
     constexpr int NB = NTRANS * (L / R);
@@ -119,8 +121,8 @@ __device__ __forceinline__ void stage(float2* buf, const float2* tw) {
     for (int i = 0; i < BPT; ++i) {
         const int b = threadIdx.x + i * NT;
         if (b < NB) {
-            const int t = (ES == 1) ? b / (L / R) : b % NTRANS;
-            const int j = (ES == 1) ? b % (L / R) : b / NTRANS;
+            const int t = b % NTRANS;
+            const int j = b / NTRANS;
             const int k = j % NS;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -140,8 +142,8 @@ __device__ __forceinline__ void stage(float2* buf, const float2* tw) {
     for (int i = 0; i < BPT; ++i) {
         const int b = threadIdx.x + i * NT;
         if (b < NB) {
-            const int t = (ES == 1) ? b / (L / R) : b % NTRANS;
-            const int j = (ES == 1) ? b % (L / R) : b / NTRANS;
+            const int t = b % NTRANS;
+            const int j = b / NTRANS;
             const int k = j % NS;
             const int base = (j - k) * R + k;
 #pragma unroll
@@ -173,8 +175,34 @@ template <> struct Cfg<64> { static constexpr int NT = 512; };
 template <> struct Cfg<128> { static constexpr int NT = 512; };
 
 template <int H> constexpr int kxp() { return H / 2 + 2; }
+// shared-memory pitch (float2) of rows that are transformed along the row
+template <int H> constexpr int rowp() { return H + 1; }
 
 __device__ __forceinline__ int signed_mode(int k, int H) { return k < H / 2 ? k : k - H; }
+
+// ---------------------------------------------------------------- I/O helpers
+// int64 deposit accumulator -> float, via two exact 32-bit halves (the
+// single 64-bit conversion would run on the FP64 pipe).
+__device__ __forceinline__ float acc_to_float(unsigned long long q) {
+    const float hi = __uint2float_rn(static_cast<unsigned>(q >> 32));
+    const float lo = __uint2float_rn(static_cast<unsigned>(q));
+    return fmaf(hi, 4294967296.0f, lo);
+}
+
+// R_tau at one node: (m*, w*) and v^n.
+__device__ __forceinline__ void react(const SpectralArgs& a, float vv, float mm, float ww, float u,
+                                      float& ms, float& ws, float& vn) {
+    ms = mm;
+    ws = ww;
+    if (a.do_mw) {
+        // explicit Euler of S = (-alpha m v; u; gamma v - eta(u) w), eta(u) = 2u/(1+u)
+        const float eta = 2.0f * u / (1.0f + u);
+        ms = mm + a.tau * u;
+        ws = ww + a.tau * (a.gamma * vv - eta * ww);
+    }
+    vn = (a.v_update == SIPF_V_IMPLICIT) ? vv / (1.0f + a.alpha * a.tau * mm)
+                                         : vv * (1.0f - a.alpha * a.tau * mm);
+}
 
 // ---------------------------------------------------------------- pass 1
 template <int H>
@@ -184,38 +212,66 @@ __global__ void __launch_bounds__(Cfg<H>::NT)
                  float* v_out, float2* __restrict__ gM, float2* __restrict__ gW,
                  float2* __restrict__ gV, const float2* __restrict__ twg,
                  const float* __restrict__ voff) {
-    constexpr int NT = Cfg<H>::NT, KXP = kxp<H>(), HK = H / 2 + 1;
+    constexpr int NT = Cfg<H>::NT, KXP = kxp<H>(), HK = H / 2 + 1, RP = rowp<H>();
     extern __shared__ float2 sm[];
-    float2* Z = sm;               // [H][H]: m* + i w*
-    float2* Vb = Z + H * H;       // [H][KXP]: v^n as pairs of rows, then half rows
+    float2* Z = sm;               // [H][RP]: m* + i w*
+    float2* Vb = Z + H * RP;      // v^n: [H/2][RP] row pairs, then [H][KXP] half rows
     float2* tw = Vb + H * KXP;    // [H]
     const int z = blockIdx.x;
     for (int i = threadIdx.x; i < H; i += NT) tw[i] = twg[i];
     const size_t plane = static_cast<size_t>(z) * H * H;
     const float c0 = *voff;   // the v spectrum only feeds derivatives: remove a constant
-    for (int idx = threadIdx.x; idx < H * H; idx += NT) {
-        const int y = idx / H, x = idx % H;
-        const size_t node = plane + idx;
-        const float vv = v[node], mm = m[node], ww = w[node];
-        const long long q = static_cast<long long>(acc[node]);
-        acc[node] = 0ull;
-        const float u = __ll2float_rn(q) * a.react_scale;
-        float ms = mm, ws = ww;
-        if (a.do_mw) {
-            // R_tau: explicit Euler of S = (-alpha m v; u; gamma v - eta(u) w)
-            const float eta = 2.0f * u / (1.0f + u);
-            ms = mm + a.tau * u;
-            ws = ww + a.tau * (a.gamma * vv - eta * ww);
+    {
+        // groups of 4 consecutive x; all loads of a batch are issued first
+        constexpr int NG = H * H / 4, ITER = (NG + NT - 1) / NT, CH = ITER < 4 ? ITER : 4;
+        const float4* v4 = reinterpret_cast<const float4*>(v + plane);
+        const float4* m4 = reinterpret_cast<const float4*>(m + plane);
+        const float4* w4 = reinterpret_cast<const float4*>(w + plane);
+        ulonglong2* a2 = reinterpret_cast<ulonglong2*>(acc + plane);
+        float4* vo4 = reinterpret_cast<float4*>(v_out + plane);
+#pragma unroll
+        for (int i0 = 0; i0 < ITER; i0 += CH) {
+            float4 rv[CH], rm[CH], rw[CH];
+            ulonglong2 ra[CH], rb[CH];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int g = threadIdx.x + (i0 + c) * NT;
+                if (i0 + c < ITER && g < NG) {
+                    rv[c] = v4[g];
+                    rm[c] = m4[g];
+                    rw[c] = w4[g];
+                    ra[c] = a2[2 * g];
+                    rb[c] = a2[2 * g + 1];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int g = threadIdx.x + (i0 + c) * NT;
+                if (!(i0 + c < ITER && g < NG)) continue;
+                a2[2 * g] = make_ulonglong2(0ull, 0ull);
+                a2[2 * g + 1] = make_ulonglong2(0ull, 0ull);
+                const float vv[4] = {rv[c].x, rv[c].y, rv[c].z, rv[c].w};
+                const float mm[4] = {rm[c].x, rm[c].y, rm[c].z, rm[c].w};
+                const float ww[4] = {rw[c].x, rw[c].y, rw[c].z, rw[c].w};
+                const unsigned long long qq[4] = {ra[c].x, ra[c].y, rb[c].x, rb[c].y};
+                float vn[4];
+                const int y = (4 * g) / H, x0 = (4 * g) % H;
+                float* vrow = reinterpret_cast<float*>(Vb + (y >> 1) * RP);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    float ms, ws;
+                    react(a, vv[e], mm[e], ww[e], acc_to_float(qq[e]) * a.react_scale, ms, ws,
+                          vn[e]);
+                    Z[y * RP + x0 + e] = make_float2(ms, ws);
+                    vrow[2 * (x0 + e) + (y & 1)] = vn[e] - c0;
+                }
+                if (a.write_v) vo4[g] = make_float4(vn[0], vn[1], vn[2], vn[3]);
+            }
         }
-        const float vn = (a.v_update == SIPF_V_IMPLICIT) ? vv / (1.0f + a.alpha * a.tau * mm)
-                                                          : vv * (1.0f - a.alpha * a.tau * mm);
-        if (a.write_v) v_out[node] = vn;
-        Z[idx] = make_float2(ms, ws);
-        reinterpret_cast<float*>(Vb + (y >> 1) * 2 * KXP)[2 * x + (y & 1)] = vn - c0;
     }
     __syncthreads();
-    if (a.do_mw) fft_axis<H, H, 1, H, NT, -1>(Z, tw);
-    fft_axis<H, H / 2, 1, 2 * KXP, NT, -1>(Vb, tw);
+    if (a.do_mw) fft_axis<H, H, 1, RP, NT, -1>(Z, tw);
+    fft_axis<H, H / 2, 1, RP, NT, -1>(Vb, tw);
     {
         // split each transformed row pair z = x1 + i x2 into X1, X2 (kx <= H/2)
         constexpr int NS = (H / 2) * HK, SPT = (NS + NT - 1) / NT;
@@ -225,8 +281,8 @@ __global__ void __launch_bounds__(Cfg<H>::NT)
             const int idx = threadIdx.x + s * NT;
             if (idx < NS) {
                 const int p = idx / HK, k = idx % HK;
-                const float2 zp = Vb[p * 2 * KXP + k];
-                const float2 zm = Vb[p * 2 * KXP + ((H - k) & (H - 1))];
+                const float2 zp = Vb[p * RP + k];
+                const float2 zm = Vb[p * RP + ((H - k) & (H - 1))];
                 x1[s] = make_float2(0.5f * (zp.x + zm.x), 0.5f * (zp.y - zm.y));
                 x2[s] = make_float2(0.5f * (zp.y + zm.y), -0.5f * (zp.x - zm.x));
             }
@@ -243,19 +299,35 @@ __global__ void __launch_bounds__(Cfg<H>::NT)
         }
         __syncthreads();
     }
-    if (a.do_mw) fft_axis<H, H, H, 1, NT, -1>(Z, tw);
+    if (a.do_mw) fft_axis<H, H, RP, 1, NT, -1>(Z, tw);
     fft_axis<H, HK, KXP, 1, NT, -1>(Vb, tw);
-    // write half spectra; M, W separated from the 2D spectrum of m* + i w*
-    for (int idx = threadIdx.x; idx < H * HK; idx += NT) {
-        const int ky = idx / HK, kx = idx % HK;
-        const size_t o = (static_cast<size_t>(z) * H + ky) * KXP + kx;
-        if (a.do_mw) {
-            const float2 zk = Z[ky * H + kx];
-            const float2 zc = Z[((H - ky) & (H - 1)) * H + ((H - kx) & (H - 1))];
-            gM[o] = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y - zc.y));
-            gW[o] = make_float2(0.5f * (zk.y + zc.y), -0.5f * (zk.x - zc.x));
+    // half spectra as pairs (kx, kx+1), the row's last slot (kx = H/2 + 1) is zero;
+    // M, W separated from the 2D spectrum of m* + i w*
+    constexpr int NP = H * (KXP / 2);
+    float4* m4 = reinterpret_cast<float4*>(gM + static_cast<size_t>(z) * H * KXP);
+    float4* w4 = reinterpret_cast<float4*>(gW + static_cast<size_t>(z) * H * KXP);
+    float4* v4o = reinterpret_cast<float4*>(gV + static_cast<size_t>(z) * H * KXP);
+    for (int idx = threadIdx.x; idx < NP; idx += NT) {
+        const int ky = idx / (KXP / 2), kx = 2 * (idx % (KXP / 2));
+        float2 M[2], W[2], V[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int k = kx + e;
+            if (k < HK) {
+                const float2 zk = Z[ky * RP + k];
+                const float2 zc = Z[((H - ky) & (H - 1)) * RP + ((H - k) & (H - 1))];
+                M[e] = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y - zc.y));
+                W[e] = make_float2(0.5f * (zk.y + zc.y), -0.5f * (zk.x - zc.x));
+                V[e] = Vb[ky * KXP + k];
+            } else {
+                M[e] = W[e] = V[e] = make_float2(0.f, 0.f);
+            }
         }
-        gV[o] = Vb[ky * KXP + kx];
+        if (a.do_mw) {
+            m4[idx] = make_float4(M[0].x, M[0].y, M[1].x, M[1].y);
+            w4[idx] = make_float4(W[0].x, W[0].y, W[1].x, W[1].y);
+        }
+        v4o[idx] = make_float4(V[0].x, V[0].y, V[1].x, V[1].y);
     }
 }
 
@@ -267,20 +339,35 @@ __global__ void __launch_bounds__(Cfg<H>::NT)
                  const float2* __restrict__ twg, float* __restrict__ voff) {
     constexpr int NT = Cfg<H>::NT, KXP = kxp<H>(), HK = H / 2 + 1;
     extern __shared__ float2 sm[];
-    float2* buf = sm;             // [H (z)][HK (kx)]
-    float2* tw = buf + H * HK;
+    float2* buf = sm;             // [H (z)][KXP (kx)]
+    float2* tw = buf + H * KXP;
     const int ky = blockIdx.x, field = blockIdx.y;   // 0 m, 1 w, 2 v -> i k_z V, 3 v -> filtered V
     if (field < 2 && !a.do_mw) return;
     if (field == 3 && !a.filter) return;
     const float2* src = field == 0 ? gM : field == 1 ? gW : gV;
     float2* dst = field == 0 ? gM : field == 1 ? gW : field == 2 ? gB : gA;
     for (int i = threadIdx.x; i < H; i += NT) tw[i] = twg[i];
-    for (int idx = threadIdx.x; idx < H * HK; idx += NT) {
-        const int zz = idx / HK, kx = idx % HK;
-        buf[idx] = src[(static_cast<size_t>(zz) * H + ky) * KXP + kx];
+    // rows (z, ky) of KXP float2 = KXP/2 float4, all loads issued first
+    constexpr int NQ = H * (KXP / 2), ITER = (NQ + NT - 1) / NT;
+    {
+        float4 r[ITER];
+#pragma unroll
+        for (int i = 0; i < ITER; ++i) {
+            const int q = threadIdx.x + i * NT;
+            if (q < NQ) {
+                const int zz = q / (KXP / 2), j = q % (KXP / 2);
+                r[i] = reinterpret_cast<const float4*>(
+                    src + (static_cast<size_t>(zz) * H + ky) * KXP)[j];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < ITER; ++i) {
+            const int q = threadIdx.x + i * NT;
+            if (q < NQ) reinterpret_cast<float4*>(buf)[q] = r[i];
+        }
     }
     __syncthreads();
-    fft_axis<H, HK, HK, 1, NT, -1>(buf, tw);
+    fft_axis<H, HK, KXP, 1, NT, -1>(buf, tw);
     if (field == 2 && ky == 0 && threadIdx.x == 0) {
         // DC of (v^n - c0): move the offset to the mean of v^n for the next step
         *voff = *voff + buf[0].x * a.out_scale;
@@ -291,7 +378,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT)
         const int qz = signed_mode(kz, H);
         const float q2 = static_cast<float>(qx * qx + qy * qy + qz * qz);
         float f = 1.0f;
-        float2 val = buf[idx];
+        float2 val = buf[kz * KXP + qx];
         if (field == 2) {
             const float kz_phys = (qz == -H / 2) ? 0.0f : a.two_pi_over_L * static_cast<float>(qz);
             val = make_float2(-kz_phys * val.y, kz_phys * val.x);
@@ -307,13 +394,14 @@ __global__ void __launch_bounds__(Cfg<H>::NT)
             const float lo = field == 0 ? a.m_r0_lo : a.w_r0_lo;
             val = make_float2(fmaf(val.x, lo, val.x * hi), fmaf(val.y, lo, val.y * hi));
         }
-        buf[idx] = val;
+        buf[kz * KXP + qx] = val;
     }
     __syncthreads();
-    fft_axis<H, HK, HK, 1, NT, +1>(buf, tw);
-    for (int idx = threadIdx.x; idx < H * HK; idx += NT) {
-        const int zz = idx / HK, kx = idx % HK;
-        dst[(static_cast<size_t>(zz) * H + ky) * KXP + kx] = buf[idx];
+    fft_axis<H, HK, KXP, 1, NT, +1>(buf, tw);
+    for (int q = threadIdx.x; q < NQ; q += NT) {
+        const int zz = q / (KXP / 2), j = q % (KXP / 2);
+        reinterpret_cast<float4*>(dst + (static_cast<size_t>(zz) * H + ky) * KXP)[j] =
+            reinterpret_cast<const float4*>(buf)[q];
     }
 }
 
@@ -345,31 +433,56 @@ __global__ void __launch_bounds__(Cfg<H>::NT)
                  float* __restrict__ m_out, float* __restrict__ w_out, float* __restrict__ gx_out,
                  float* __restrict__ gy_out, float* __restrict__ gz_out,
                  const float2* __restrict__ twg) {
-    constexpr int NT = Cfg<H>::NT, KXP = kxp<H>(), HK = H / 2 + 1;
+    constexpr int NT = Cfg<H>::NT, KXP = kxp<H>(), HK = H / 2 + 1, RP = rowp<H>();
+    static_assert(H * RP <= 2 * H * KXP, "packed rows must fit in B0/B1");
     extern __shared__ float2 sm[];
     float2* B0 = sm;              // [H][KXP]
     float2* B1 = B0 + H * KXP;    // [H][KXP]
-    float2* Z = sm;               // [H][H] packed rows (aliases B0/B1)
+    float2* Z = sm;               // [H][RP] packed rows (aliases B0/B1)
     float2* tw = B1 + H * KXP;
     const int z = blockIdx.x, group = blockIdx.y;   // 0 (m, w), 1 (dv/dx, dv/dy), 2 dv/dz
     if (group == 0 && !a.do_mw) return;
     for (int i = threadIdx.x; i < H; i += NT) tw[i] = twg[i];
-    const size_t pbase = static_cast<size_t>(z) * H * KXP;
-    for (int idx = threadIdx.x; idx < H * HK; idx += NT) {
-        const int ky = idx / HK, kx = idx % HK;
-        const size_t o = pbase + static_cast<size_t>(ky) * KXP + kx;
-        if (group == 0) {
-            B0[ky * KXP + kx] = gM[o];
-            B1[ky * KXP + kx] = gW[o];
-        } else if (group == 1) {
-            const float2 val = gV[o];
-            const float kxp_ = (kx == H / 2) ? 0.0f : a.two_pi_over_L * static_cast<float>(kx);
-            const int qy = signed_mode(ky, H);
-            const float kyp = (qy == -H / 2) ? 0.0f : a.two_pi_over_L * static_cast<float>(qy);
-            B0[ky * KXP + kx] = make_float2(-kxp_ * val.y, kxp_ * val.x);
-            B1[ky * KXP + kx] = make_float2(-kyp * val.y, kyp * val.x);
-        } else {
-            B0[ky * KXP + kx] = gB[o];
+    {
+        // whole planes of KXP/2 float4 per row, all loads issued first
+        constexpr int NQ = H * (KXP / 2), ITER = (NQ + NT - 1) / NT;
+        const size_t pbase = static_cast<size_t>(z) * H * KXP;
+        const float4* s0 = reinterpret_cast<const float4*>((group == 0 ? gM : group == 1 ? gV : gB) +
+                                                           pbase);
+        const float4* s1 = reinterpret_cast<const float4*>(gW + pbase);
+        float4 r0[ITER], r1[ITER];
+#pragma unroll
+        for (int i = 0; i < ITER; ++i) {
+            const int q = threadIdx.x + i * NT;
+            if (q < NQ) {
+                r0[i] = s0[q];
+                if (group == 0) r1[i] = s1[q];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < ITER; ++i) {
+            const int q = threadIdx.x + i * NT;
+            if (q >= NQ) continue;
+            if (group == 1) {
+                // i k_x V and i k_y V (Nyquist derivatives zero)
+                const int ky = q / (KXP / 2), kx = 2 * (q % (KXP / 2));
+                const int qy = signed_mode(ky, H);
+                const float kyp = (qy == -H / 2) ? 0.0f : a.two_pi_over_L * static_cast<float>(qy);
+                float2 dx[2], dy[2];
+                const float2 val[2] = {make_float2(r0[i].x, r0[i].y), make_float2(r0[i].z, r0[i].w)};
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int k = kx + e;
+                    const float kxp_ = (k >= H / 2) ? 0.0f : a.two_pi_over_L * static_cast<float>(k);
+                    dx[e] = make_float2(-kxp_ * val[e].y, kxp_ * val[e].x);
+                    dy[e] = make_float2(-kyp * val[e].y, kyp * val[e].x);
+                }
+                reinterpret_cast<float4*>(B0)[q] = make_float4(dx[0].x, dx[0].y, dx[1].x, dx[1].y);
+                reinterpret_cast<float4*>(B1)[q] = make_float4(dy[0].x, dy[0].y, dy[1].x, dy[1].y);
+            } else {
+                reinterpret_cast<float4*>(B0)[q] = r0[i];
+                if (group == 0) reinterpret_cast<float4*>(B1)[q] = r1[i];
+            }
         }
     }
     __syncthreads();
@@ -390,18 +503,22 @@ __global__ void __launch_bounds__(Cfg<H>::NT)
 #pragma unroll
         for (int s = 0; s < EPT; ++s) {
             const int idx = threadIdx.x + s * NT;
-            if (idx < NE) Z[idx] = r[s];
+            if (idx < NE) Z[(idx / H) * RP + idx % H] = r[s];
         }
         __syncthreads();
-        fft_axis<H, H, 1, H, NT, +1>(Z, tw);
+        fft_axis<H, H, 1, RP, NT, +1>(Z, tw);
         float* o1 = group == 0 ? m_out : gx_out;
         float* o2 = group == 0 ? w_out : gy_out;
         const float sc = group == 0 ? a.out_scale : a.out_scale_xy;
         const size_t plane = static_cast<size_t>(z) * H * H;
-        for (int idx = threadIdx.x; idx < H * H; idx += NT) {
-            const float2 val = Z[idx];
-            o1[plane + idx] = val.x * sc;
-            o2[plane + idx] = val.y * sc;
+        float4* p1 = reinterpret_cast<float4*>(o1 + plane);
+        float4* p2 = reinterpret_cast<float4*>(o2 + plane);
+        for (int g = threadIdx.x; g < H * H / 4; g += NT) {
+            const int y = (4 * g) / H, x0 = (4 * g) % H;
+            const float2 e0 = Z[y * RP + x0], e1 = Z[y * RP + x0 + 1];
+            const float2 e2 = Z[y * RP + x0 + 2], e3 = Z[y * RP + x0 + 3];
+            p1[g] = make_float4(e0.x * sc, e1.x * sc, e2.x * sc, e3.x * sc);
+            p2[g] = make_float4(e0.y * sc, e1.y * sc, e2.y * sc, e3.y * sc);
         }
     } else {
         constexpr int NE = (H / 2) * H, EPT = (NE + NT - 1) / NT;
@@ -418,57 +535,73 @@ __global__ void __launch_bounds__(Cfg<H>::NT)
 #pragma unroll
         for (int s = 0; s < EPT; ++s) {
             const int idx = threadIdx.x + s * NT;
-            if (idx < NE) Z[idx] = r[s];
+            if (idx < NE) Z[(idx / H) * RP + idx % H] = r[s];
         }
         __syncthreads();
-        fft_axis<H, H / 2, 1, H, NT, +1>(Z, tw);
+        fft_axis<H, H / 2, 1, RP, NT, +1>(Z, tw);
         const size_t plane = static_cast<size_t>(z) * H * H;
-        for (int idx = threadIdx.x; idx < NE; idx += NT) {
-            const int p = idx / H, x = idx % H;
-            const float2 val = Z[idx];
-            gz_out[plane + (2 * p) * H + x] = val.x * a.out_scale;
-            gz_out[plane + (2 * p + 1) * H + x] = val.y * a.out_scale;
+        float4* g4 = reinterpret_cast<float4*>(gz_out + plane);
+        const float sc = a.out_scale;
+        for (int g = threadIdx.x; g < NE / 4; g += NT) {
+            const int p = (4 * g) / H, x0 = (4 * g) % H;
+            const float2 e0 = Z[p * RP + x0], e1 = Z[p * RP + x0 + 1];
+            const float2 e2 = Z[p * RP + x0 + 2], e3 = Z[p * RP + x0 + 3];
+            g4[(2 * p * H + x0) / 4] = make_float4(e0.x * sc, e1.x * sc, e2.x * sc, e3.x * sc);
+            g4[((2 * p + 1) * H + x0) / 4] = make_float4(e0.y * sc, e1.y * sc, e2.y * sc, e3.y * sc);
         }
     }
 }
 
 template <int H>
-cudaError_t spectral_step(sipf_ctx* c, const SpectralArgs& a) {
+cudaError_t spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass) {
     constexpr int NT = Cfg<H>::NT, KXP = kxp<H>(), HK = H / 2 + 1;
-    const size_t sm1 = (static_cast<size_t>(H) * H + H * KXP + H) * sizeof(float2);
-    const size_t sm2 = (static_cast<size_t>(H) * HK + H) * sizeof(float2);
+    const size_t sm1 = (static_cast<size_t>(H) * rowp<H>() + H * KXP + H) * sizeof(float2);
+    const size_t sm2 = (static_cast<size_t>(H) * KXP + H) * sizeof(float2);
     const size_t sm3 = (2 * static_cast<size_t>(H) * KXP + H) * sizeof(float2);
-    static bool configured = false;   // per process; attributes are per function
-    if (!configured) {
+    static int configured_device = -1;   // attributes are set once per process and device
+    if (configured_device != c->device) {
         cudaFuncSetAttribute(k_forward_xy<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(sm1));
         cudaFuncSetAttribute(k_z_multiply<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(sm2));
         cudaFuncSetAttribute(k_inverse_xy<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(sm3));
-        configured = true;
+        configured_device = c->device;
     }
-    k_forward_xy<H><<<H, NT, sm1, c->stream>>>(
-        a, c->v, c->m, c->w, reinterpret_cast<unsigned long long*>(c->acc), c->v, c->specM,
-        c->specW, c->specV, c->twiddle, c->voff);
-    k_z_multiply<H><<<dim3(H, 4), NT, sm2, c->stream>>>(a, c->specM, c->specW, c->specV,
-                                                         c->specB, c->specA, c->twiddle, c->voff);
-    k_inverse_xy<H><<<dim3(H, 3), NT, sm3, c->stream>>>(
-        a, c->specM, c->specW, a.filter ? c->specA : c->specV, c->specB, c->m, c->w, c->gx,
-        c->gy, c->gz, c->twiddle);
+    if (pass == 0) {
+        k_forward_xy<H><<<H, NT, sm1, c->stream>>>(
+            a, c->v, c->m, c->w, reinterpret_cast<unsigned long long*>(c->acc), c->v, c->specM,
+            c->specW, c->specV, c->twiddle, c->voff);
+    } else if (pass == 1) {
+        k_z_multiply<H><<<dim3(H, 4), NT, sm2, c->stream>>>(a, c->specM, c->specW, c->specV,
+                                                             c->specB, c->specA, c->twiddle,
+                                                             c->voff);
+    } else {
+        k_inverse_xy<H><<<dim3(H, 3), NT, sm3, c->stream>>>(
+            a, c->specM, c->specW, a.filter ? c->specA : c->specV, c->specB, c->m, c->w, c->gx,
+            c->gy, c->gz, c->twiddle);
+    }
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_spectral_step(sipf_ctx* c, const SpectralArgs& a) {
+cudaError_t launch_spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass) {
     switch (c->H) {
-        case 16: return spectral_step<16>(c, a);
-        case 32: return spectral_step<32>(c, a);
-        case 64: return spectral_step<64>(c, a);
-        case 128: return spectral_step<128>(c, a);
+        case 16: return spectral_pass<16>(c, a, pass);
+        case 32: return spectral_pass<32>(c, a, pass);
+        case 64: return spectral_pass<64>(c, a, pass);
+        case 128: return spectral_pass<128>(c, a, pass);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_spectral_step(sipf_ctx* c, const SpectralArgs& a) {
+    for (int pass = 0; pass < 3; ++pass) {
+        const cudaError_t e = launch_spectral_pass(c, a, pass);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 void fill_twiddles(int H, float2* out) {

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/sipf.h"
 
@@ -18,6 +19,10 @@ constexpr int kMaxH = 128;          // largest grid of this build
 constexpr int kStatusNonfinite = 1;   // a pushed position was NaN/inf (reset to 0)
 constexpr int kStatusSlot = 2;        // scatter slot outside its cell's run
 constexpr int kStatusTotal = 4;       // cell counts did not sum to N
+
+// Kernel groups of a step, in launch order (tracing).
+constexpr int kProfGroups = 6;
+constexpr int kProfMaxSteps = 4096;
 
 // Per-step scalars of the particle kernels.
 struct PushArgs {
@@ -106,6 +111,11 @@ struct sipf_ctx {
     double* diag_out = nullptr;      // 8 doubles
     long long* diag_ll = nullptr;    // fixed-point partial sums
 
+    // tracing: CUDA events between the kernel groups of each step
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_events;      // kProfGroups + 1 per recorded step
+    int64_t prof_steps = 0;
+
     int64_t step = 0;
     double time = 0;
     double logref = 0;               // log(M0 / N) of the initial state
@@ -132,6 +142,7 @@ cudaError_t launch_normals(const uint32_t* ids, int64_t N, uint32_t n, uint64_t 
                            uint32_t* bits, cudaStream_t s);
 // fft.cu
 cudaError_t launch_spectral_step(sipf_ctx* c, const SpectralArgs& a);
+cudaError_t launch_spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass);
 void fill_twiddles(int H, float2* host_out);
 
 }  // namespace sipf

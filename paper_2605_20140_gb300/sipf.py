@@ -34,7 +34,9 @@ EXPORTED = (
     "sipf_create", "sipf_set_state", "sipf_step", "sipf_fields", "sipf_particles",
     "sipf_particle_state", "sipf_cell_start", "sipf_diagnostics", "sipf_sync",
     "sipf_destroy", "sipf_strerror", "sipf_last_error", "sipf_brownian_normals",
+    "sipf_profile", "sipf_profile_read", "sipf_profile_name",
 )
+PROFILE_GROUPS = 6
 
 
 class sipf_grid(ctypes.Structure):
@@ -90,6 +92,9 @@ def load() -> ctypes.CDLL:
         "sipf_strerror": ([I32], ctypes.c_char_p),
         "sipf_last_error": ([P], ctypes.c_char_p),
         "sipf_brownian_normals": ([P, I64, U32, U64, P, P, P], I32),
+        "sipf_profile": ([P, I32], I32),
+        "sipf_profile_read": ([P, P, P, I32], I32),
+        "sipf_profile_name": ([I32], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -179,6 +184,19 @@ def sipf_destroy(ctx):
 def sipf_brownian_normals(ids_dev, N: int, n: int, seed: int, z_dev, bits_dev=None, stream=0):
     _check(load().sipf_brownian_normals(_ptr(ids_dev), int(N), int(n), int(seed), _ptr(z_dev),
                                         _ptr(bits_dev), ctypes.c_void_p(stream or None)))
+
+
+def sipf_profile(ctx, enable: bool):
+    _check(load().sipf_profile(ctx, int(bool(enable))), ctx)
+
+
+def sipf_profile_read(ctx) -> dict:
+    """{group name: (total ms, launches)} over the recorded steps."""
+    ms = np.zeros(PROFILE_GROUPS, dtype=np.float64)
+    n = np.zeros(PROFILE_GROUPS, dtype=np.int64)
+    _check(load().sipf_profile_read(ctx, ms.ctypes.data, n.ctypes.data, PROFILE_GROUPS), ctx)
+    return {load().sipf_profile_name(k).decode(): (float(ms[k]), int(n[k]))
+            for k in range(PROFILE_GROUPS)}
 
 
 # ---------------------------------------------------------------- convenience
