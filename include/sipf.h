@@ -108,7 +108,8 @@ typedef struct {
 /* Create a context on the current CUDA device for N particles on `grid`.
  * `stream` is a cudaStream_t (NULL = legacy default stream) on which all
  * later work of the context is enqueued.  Allocates all device state
- * (about 56 N + 90 H^3 bytes).  Errors: SIPF_EINVAL (N < 1 or N >= 2^31,
+ * (about 110 N + 110 H^3 bytes: two particle buffers with tile buckets and
+ * an overflow region of N slots each, fields, spectra).  Errors: SIPF_EINVAL (N < 1 or N >= 2^31,
  * H not supported, L <= 0, a parameter negative or non-finite, diffusion or
  * v_update unknown), SIPF_EUNSUPPORTED (H = 256), SIPF_ENOMEM. */
 int sipf_create(const sipf_grid* grid, int64_t N, const sipf_params* params,
@@ -140,7 +141,10 @@ int sipf_step(sipf_ctx* ctx, double dt, int64_t k);
  * codes. */
 int sipf_fields(sipf_ctx* ctx, uint32_t mask, float* dst, int where);
 
-/* Copy the particles in the library's storage order (bucketed by cell):
+/* Copy the particles in the library's storage order (bucketed by tile of
+ * 8^3 cells, tiles in tile-index order, order within a tile unspecified;
+ * particles that overflowed their tile's bucket in the last step follow at
+ * the end):
  * physical positions x (3*N floats, SoA; may be NULL), masses a = exp(log a)
  * (N doubles; may be NULL) and ids (N uint32; may be NULL).  Synchronises. */
 int sipf_particles(sipf_ctx* ctx, float* x, double* mass, uint32_t* id, int where);
@@ -150,11 +154,11 @@ int sipf_particles(sipf_ctx* ctx, float* x, double* mass, uint32_t* id, int wher
  * ids; any pointer may be NULL.  Synchronises. */
 int sipf_particle_state(sipf_ctx* ctx, float* s, double* loga, uint32_t* id, int where);
 
-/* Offsets of each cell's run of particles in storage order (H^3 + 1 int32).
+/* Exclusive prefix sum of the number of particles per cell (H^3 + 1 int32):
+ * the offsets of each cell's run if the particles were sorted by cell key.
  * Cells are numbered tile-major: key = tile * 512 + local, tiles of 8^3
  * cells, tile = ((cz/8) T + cy/8) T + cx/8 with T = H/8, local =
- * ((cz%8) 8 + cy%8) 8 + cx%8, cell (cx, cy, cz) = floor(s).  Within a cell
- * the storage order is unspecified.  Synchronises. */
+ * ((cz%8) 8 + cy%8) 8 + cx%8, cell (cx, cy, cz) = floor(s).  Synchronises. */
 int sipf_cell_start(sipf_ctx* ctx, int32_t* cell_start, int where);
 
 /* FP64 diagnostics of the current state; synchronises. */
@@ -182,12 +186,24 @@ const char* sipf_last_error(const sipf_ctx* ctx);
 int sipf_brownian_normals(const uint32_t* ids, int64_t N, uint32_t n, uint64_t seed,
                           float* z, uint32_t* bits, void* stream);
 
+/* Self-check of the integer-arithmetic float<->double conversions the step
+ * kernel uses instead of the FP64 pipe: for each i < n compares the
+ * conversion of f[i] to double and of d[i] to float (round to nearest even)
+ * with the hardware conversions, bit for bit; mismatches[0] and
+ * mismatches[1] (device int32) receive the two mismatch counts.  f, d and
+ * mismatches are device pointers; synchronises `stream`.  Errors:
+ * SIPF_EINVAL, SIPF_ECUDA.  (Not an operation of the paper: it checks this
+ * implementation.) */
+int sipf_check_conversions(const float* f, const double* d, int64_t n, int32_t* mismatches,
+                           void* stream);
+
 /* Tracing.  sipf_profile(ctx, 1) starts recording CUDA events (on the
  * context's stream) between the kernel groups of each subsequent step, for
  * at most 4096 steps; sipf_profile(ctx, 0) stops; enabling again clears the
- * record.  Groups, in launch order: 0 count, 1 scan (3 launches),
- * 2 scatter_deposit, 3 forward_xy, 4 z_multiply, 5 inverse_xy (names from
- * sipf_profile_name).  sipf_profile_read synchronises the stream and writes,
+ * record.  Groups, in launch order: 0 particle_step (deposit, gather, push,
+ * mass update and binning of all particles), 1 forward_xy, 2 z_multiply,
+ * 3 inverse_xy (names from sipf_profile_name); the plan of the next step's
+ * bucket layout runs concurrently on a second stream and is not timed.  sipf_profile_read synchronises the stream and writes,
  * for k < n, the summed device time ms[k] (milliseconds) and the number of
  * kernel launches launches[k] over the recorded steps.  Errors: SIPF_EINVAL,
  * SIPF_ECUDA. */

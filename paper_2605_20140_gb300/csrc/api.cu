@@ -11,13 +11,6 @@
 
 #include "sipf_internal.cuh"
 
-namespace sipf {
-cudaError_t launch_iota(sipf_ctx* c, int buf);
-size_t diag_scratch_doubles();
-size_t diag_scratch_ll();
-int scan_tiles(int n);
-}  // namespace sipf
-
 namespace {
 
 using namespace sipf;
@@ -66,11 +59,12 @@ cudaError_t dalloc(T** p, size_t n) {
 }
 
 void free_all(sipf_ctx* c) {
-    void* ptrs[] = {c->sx[0], c->sx[1], c->sy[0], c->sy[1], c->sz[0], c->sz[1], c->loga[0],
-                    c->loga[1], c->id[0], c->id[1], c->count, c->cell_start, c->scan_tmp, c->acc,
-                    c->v, c->m, c->w, c->gx, c->gy, c->gz, c->specM, c->specW, c->specV,
-                    c->specB, c->specA, c->twiddle, c->status, c->diag_tmp, c->diag_out,
-                    c->diag_ll, c->voff};
+    void* ptrs[] = {c->sx[0], c->sx[1], c->sy[0], c->sy[1], c->sz[0], c->sz[1], c->dl[0],
+                    c->dl[1], c->id[0], c->id[1], c->bstart[0], c->bstart[1], c->cap[0],
+                    c->cap[1], c->cnt[0], c->cnt[1], c->ovf[0], c->ovf[1], c->items, c->n_items,
+                    c->work, c->count, c->cell_start, c->scan_tmp, c->acc, c->v, c->m, c->w,
+                    c->G, c->specM, c->specW, c->specV, c->specB, c->specA, c->twiddle,
+                    c->status, c->diag_tmp, c->diag_out, c->diag_ll, c->voff};
     for (void* q : ptrs)
         if (q) cudaFree(q);
 }
@@ -104,21 +98,21 @@ int check_status(sipf_ctx* c) {
     return SIPF_OK;
 }
 
-// Fixed-point scale 2^S of the deposit: the total contribution of all
-// particles, sum exp(loga - logref) <= N e^t (Corollary mass: M <= M0 e^t),
-// stays below 2^61 after scaling.
+// Fixed-point scale 2^S of the deposit: one contribution is at most
+// max_p a_p / exp(logref) <= maxrel e^t (Lemma mass: a grows by at most
+// 1 + tau <= e^tau per step), and must stay below 2^31 after scaling; node
+// sums are accumulated in 64-bit integers.
 int deposit_shift(const sipf_ctx* c) {
-    const double bound = log2(static_cast<double>(c->N)) + c->time * 1.4426950408889634 + 2.0;
-    int S = static_cast<int>(floor(61.0 - bound));
-    if (S > 60) S = 60;
-    if (S < 0) S = 0;
+    const double bound = log2(c->maxrel) + c->time * 1.4426950408889634 + 0.5;
+    int S = static_cast<int>(floor(30.0 - bound));
+    if (S > 40) S = 40;
+    if (S < -60) S = -60;
     return S;
 }
 
 DepositArgs deposit_args(const sipf_ctx* c) {
     DepositArgs d;
-    d.logref = c->logref;
-    d.scale = ldexpf(1.0f, deposit_shift(c));
+    d.scale = static_cast<float>(ldexp(1.0, deposit_shift(c)));
     return d;
 }
 
@@ -173,21 +167,33 @@ SpectralArgs spectral_args(const sipf_ctx* c, double dt, float react_scale, int 
     return s;
 }
 
-// Bin the store in buffer 1 into buffer 0 (positions unchanged).
+// Bin the unbinned particles of buffer 1 into tile buckets of buffer 0, and
+// plan the items of buffer 0 and the layout of buffer 1.
 int bin_initial(sipf_ctx* c) {
+    SIPF_CUDA(c, cudaMemsetAsync(c->cnt[1], 0, sizeof(int) * c->ntiles, c->stream));
+    SIPF_CUDA(c, cudaMemsetAsync(c->ovf[1], 0, sizeof(int), c->stream));
+    SIPF_CUDA(c, launch_tile_count(c, 1, c->cnt[1]));
+    SIPF_CUDA(c, launch_plan(c, 1, 1, c->stream));   // layout of buffer 0 from the tile counts
+    SIPF_CUDA(c, launch_plan_flat(c));           // items: the raw input array
     c->cur = 1;
     const PushArgs a = push_args(c, 0.0, 0, 0);
-    SIPF_CUDA(c, launch_count(c, a));
-    SIPF_CUDA(c, launch_scan(c));
-    SIPF_CUDA(c, launch_scatter(c, a, deposit_args(c), 0, 1));
+    SIPF_CUDA(c, launch_step_kernel(c, a, deposit_args(c), 0, 1));
     c->cur = 0;
+    SIPF_CUDA(c, launch_plan(c, 0, 1, c->stream));
     return SIPF_OK;
 }
 
 // Deposit the current particles into the accumulator (Alg. 1).
 int deposit_current(sipf_ctx* c) {
     const PushArgs a = push_args(c, 0.0, 0, 0);
-    SIPF_CUDA(c, launch_scatter(c, a, deposit_args(c), 1, 0));
+    SIPF_CUDA(c, launch_step_kernel(c, a, deposit_args(c), 1, 0));
+    return SIPF_OK;
+}
+
+// Compact the live particles of the current buffer into the other buffer
+// (slots [0, N), item order), which is free between steps.
+int compact_current(sipf_ctx* c) {
+    SIPF_CUDA(c, launch_compact(c, c->cur, c->cur ^ 1));
     return SIPF_OK;
 }
 
@@ -215,16 +221,19 @@ int enqueue_step(sipf_ctx* c, double dt) {
     const float u_scale = acc_to_u(c);
     const SpectralArgs sa = spectral_args(c, dt, u_scale, 1);
     SIPF_CUDA(c, prof_mark(c, 0));
-    SIPF_CUDA(c, launch_count(c, a));
+    SIPF_CUDA(c, launch_step_kernel(c, a, d, 1, 1));
     SIPF_CUDA(c, prof_mark(c, 1));
-    SIPF_CUDA(c, launch_scan(c));
-    SIPF_CUDA(c, prof_mark(c, 2));
-    SIPF_CUDA(c, launch_scatter(c, a, d, 1, 1));
-    SIPF_CUDA(c, prof_mark(c, 3));
+    // the plan of the next step's items and layout needs only the counts: it
+    // runs on the side stream while the spectral passes run on the main one
+    SIPF_CUDA(c, cudaEventRecord(c->ev_fork, c->stream));
+    SIPF_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    SIPF_CUDA(c, launch_plan(c, c->cur ^ 1, 1, c->side));
+    SIPF_CUDA(c, cudaEventRecord(c->ev_join, c->side));
     for (int pass = 0; pass < 3; ++pass) {
         SIPF_CUDA(c, launch_spectral_pass(c, sa, pass));
-        SIPF_CUDA(c, prof_mark(c, 4 + pass));
+        SIPF_CUDA(c, prof_mark(c, 2 + pass));
     }
+    SIPF_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     if (c->prof_on && c->prof_steps < kProfMaxSteps) c->prof_steps += 1;
     c->cur ^= 1;
     c->step += 1;
@@ -277,18 +286,34 @@ int sipf_create(const sipf_grid* grid, int64_t N, const sipf_params* params, voi
     const size_t H3 = static_cast<size_t>(c->H) * c->H * c->H;
     c->kxp = c->H / 2 + 2;
     const size_t spec = static_cast<size_t>(c->H) * c->H * c->kxp;
+    const int T = c->H / 8;
+    c->ntiles = T * T * T;
+    const int64_t bucket_slots = N + N / 8 + 36 * static_cast<int64_t>(c->ntiles) + 64;
+    c->ovf_base = static_cast<int>((bucket_slots + 3) & ~int64_t{3});
+    c->buf_slots = c->ovf_base + N + 8;
+    if (c->buf_slots >= (int64_t{1} << 31)) {
+        delete c;
+        return SIPF_EINVAL;
+    }
+    const int K = item_size();
+    c->max_items = static_cast<int>(2 * ((N + K - 1) / K) + c->ntiles + 2);
+    const size_t S = static_cast<size_t>(c->buf_slots);
     bool ok = true;
     for (int b = 0; b < 2; ++b) {
-        ok = ok && dalloc(&c->sx[b], N) == cudaSuccess && dalloc(&c->sy[b], N) == cudaSuccess &&
-             dalloc(&c->sz[b], N) == cudaSuccess && dalloc(&c->loga[b], N) == cudaSuccess &&
-             dalloc(&c->id[b], N) == cudaSuccess;
+        ok = ok && dalloc(&c->sx[b], S) == cudaSuccess && dalloc(&c->sy[b], S) == cudaSuccess &&
+             dalloc(&c->sz[b], S) == cudaSuccess && dalloc(&c->dl[b], S) == cudaSuccess &&
+             dalloc(&c->id[b], S) == cudaSuccess &&
+             dalloc(&c->bstart[b], c->ntiles) == cudaSuccess &&
+             dalloc(&c->cap[b], c->ntiles) == cudaSuccess &&
+             dalloc(&c->cnt[b], c->ntiles) == cudaSuccess && dalloc(&c->ovf[b], 1) == cudaSuccess;
     }
-    ok = ok && dalloc(&c->count, H3) == cudaSuccess && dalloc(&c->cell_start, H3 + 1) == cudaSuccess &&
+    ok = ok && dalloc(&c->items, static_cast<size_t>(c->max_items)) == cudaSuccess &&
+         dalloc(&c->n_items, 1) == cudaSuccess && dalloc(&c->work, 1) == cudaSuccess &&
+         dalloc(&c->count, H3) == cudaSuccess && dalloc(&c->cell_start, H3 + 1) == cudaSuccess &&
          dalloc(&c->scan_tmp, static_cast<size_t>(scan_tiles(static_cast<int>(H3))) + 1) == cudaSuccess &&
          dalloc(&c->acc, H3) == cudaSuccess && dalloc(&c->v, H3) == cudaSuccess &&
          dalloc(&c->m, H3) == cudaSuccess && dalloc(&c->w, H3) == cudaSuccess &&
-         dalloc(&c->gx, H3) == cudaSuccess && dalloc(&c->gy, H3) == cudaSuccess &&
-         dalloc(&c->gz, H3) == cudaSuccess && dalloc(&c->specM, spec) == cudaSuccess &&
+         dalloc(&c->G, 4 * H3) == cudaSuccess && dalloc(&c->specM, spec) == cudaSuccess &&
          dalloc(&c->specW, spec) == cudaSuccess && dalloc(&c->specV, spec) == cudaSuccess &&
          dalloc(&c->specB, spec) == cudaSuccess && dalloc(&c->twiddle, c->H) == cudaSuccess &&
          dalloc(&c->status, 1) == cudaSuccess && dalloc(&c->voff, 1) == cudaSuccess &&
@@ -306,11 +331,25 @@ int sipf_create(const sipf_grid* grid, int64_t N, const sipf_params* params, voi
     std::vector<float2> tw(c->H);
     fill_twiddles(c->H, tw.data());
     cudaError_t e = cudaMemcpy(c->twiddle, tw.data(), c->H * sizeof(float2), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->count, 0, H3 * sizeof(int32_t), c->stream);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        e = cudaMemsetAsync(c->bstart[b], 0, sizeof(int) * c->ntiles, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->cap[b], 0, sizeof(int) * c->ntiles, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->cnt[b], 0, sizeof(int) * c->ntiles, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->ovf[b], 0, sizeof(int), c->stream);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, H3 * sizeof(long long), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->G, 0, 4 * H3 * sizeof(float), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return SIPF_ECUDA;
+    }
+    c->step_blocks = step_grid(c);
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         free_all(c);
         delete c;
         return SIPF_ECUDA;
@@ -336,13 +375,15 @@ int sipf_set_state(sipf_ctx* c, const float* x, const double* mass, const uint32
         SIPF_CUDA(c, cudaStreamSynchronize(c->stream));
         mp = hm.data();
     }
-    double M0 = 0.0;
+    double M0 = 0.0, amax = 0.0;
     for (size_t i = 0; i < N; ++i) {
         if (!(isfinite(mp[i]) && mp[i] >= 0.0))
             return fail(c, SIPF_EINVAL, "masses must be finite and >= 0");
         M0 += mp[i];
+        amax = mp[i] > amax ? mp[i] : amax;
     }
     c->logref = M0 > 0.0 ? log(M0 / static_cast<double>(N)) : 0.0;
+    c->maxrel = M0 > 0.0 ? amax / exp(c->logref) : 1.0;
     c->step = 0;
     c->time = 0.0;
     // upload into buffer 1 (unordered), then bin into buffer 0
@@ -361,7 +402,7 @@ int sipf_set_state(sipf_ctx* c, const float* x, const double* mass, const uint32
     }
     int r = SIPF_OK;
     cudaError_t e = launch_wrap_positions(c, where == SIPF_HOST ? xin : x, 1);
-    if (e == cudaSuccess) e = launch_log_mass(c, where == SIPF_HOST ? min_ : mass, 1);
+    if (e == cudaSuccess) e = launch_rel_log_mass(c, where == SIPF_HOST ? min_ : mass, 1);
     if (e == cudaSuccess) {
         if (id) {
             r = copy_in(c, c->id[1], id, N * sizeof(uint32_t), where);
@@ -395,8 +436,10 @@ int sipf_set_state(sipf_ctx* c, const float* x, const double* mass, const uint32
     }
     if (e == cudaSuccess && r == SIPF_OK) r = bin_initial(c);
     if (e == cudaSuccess && r == SIPF_OK) {
-        // grad v^(0) from the DFT of v^(0) (tau = 0: no reaction, v unchanged)
-        e = launch_spectral_step(c, spectral_args(c, 0.0, 0.0f, 0));
+        // w^(0) into the gather array; grad v^(0) from the DFT of v^(0) (tau = 0)
+        e = cudaMemcpy2DAsync(c->G + 3, 4 * sizeof(float), c->w, sizeof(float), sizeof(float), H3,
+                              cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) e = launch_spectral_step(c, spectral_args(c, 0.0, 0.0f, 0));
     }
     if (e == cudaSuccess && r == SIPF_OK) e = cudaStreamSynchronize(c->stream);
     if (xin) cudaFree(xin);
@@ -428,12 +471,26 @@ int sipf_fields(sipf_ctx* c, uint32_t mask, float* dst, int where) {
     if (where != SIPF_HOST && where != SIPF_DEVICE) return fail(c, SIPF_EINVAL, "bad where");
     if (!c->state_set) return fail(c, SIPF_EINVAL, "sipf_set_state has not been called");
     const size_t H3 = static_cast<size_t>(c->H) * c->H * c->H;
-    const float* src[7] = {nullptr, c->v, c->m, c->w, c->gx, c->gy, c->gz};
+    const float* src[4] = {nullptr, c->v, c->m, c->w};
     float* tmp = nullptr;
     size_t off = 0;
     for (int b = 0; b < 7; ++b) {
         if (!(mask & (1u << b))) continue;
-        if (b == 0) {
+        if (b >= 4) {
+            if (where == SIPF_DEVICE) {
+                SIPF_CUDA(c, launch_component(c, b - 4, dst + off));
+            } else {
+                SIPF_CUDA(c, dalloc(&tmp, H3));
+                cudaError_t e = launch_component(c, b - 4, tmp);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(dst + off, tmp, H3 * sizeof(float), cudaMemcpyDeviceToHost,
+                                        c->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+                cudaFree(tmp);
+                tmp = nullptr;
+                if (e != cudaSuccess) return cuda_fail(c, e, "sipf_fields(grad v)");
+            }
+        } else if (b == 0) {
             int r = deposit_current(c);
             if (r != SIPF_OK) return r;
             if (where == SIPF_DEVICE) {
@@ -446,6 +503,7 @@ int sipf_fields(sipf_ctx* c, uint32_t mask, float* dst, int where) {
                                         c->stream);
                 if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
                 cudaFree(tmp);
+                tmp = nullptr;
                 if (e != cudaSuccess) return cuda_fail(c, e, "sipf_fields(U)");
             }
         } else {
@@ -460,16 +518,21 @@ int sipf_fields(sipf_ctx* c, uint32_t mask, float* dst, int where) {
 int sipf_particle_state(sipf_ctx* c, float* s, double* loga, uint32_t* id, int where) {
     if (!c) return SIPF_EINVAL;
     if (where != SIPF_HOST && where != SIPF_DEVICE) return fail(c, SIPF_EINVAL, "bad where");
+    if (!c->state_set) return fail(c, SIPF_EINVAL, "sipf_set_state has not been called");
     const size_t N = static_cast<size_t>(c->N);
-    const int b = c->cur;
-    int r = SIPF_OK;
-    if (s) {
-        r = copy_out(c, s, c->sx[b], N * sizeof(float), where);
-        if (r == SIPF_OK) r = copy_out(c, s + N, c->sy[b], N * sizeof(float), where);
-        if (r == SIPF_OK) r = copy_out(c, s + 2 * N, c->sz[b], N * sizeof(float), where);
+    int r = compact_current(c);
+    const int o = c->cur ^ 1;
+    if (r == SIPF_OK && s) {
+        r = copy_out(c, s, c->sx[o], N * sizeof(float), where);
+        if (r == SIPF_OK) r = copy_out(c, s + N, c->sy[o], N * sizeof(float), where);
+        if (r == SIPF_OK) r = copy_out(c, s + 2 * N, c->sz[o], N * sizeof(float), where);
     }
-    if (r == SIPF_OK && loga) r = copy_out(c, loga, c->loga[b], N * sizeof(double), where);
-    if (r == SIPF_OK && id) r = copy_out(c, id, c->id[b], N * sizeof(uint32_t), where);
+    if (r == SIPF_OK && loga) {
+        // log a = dl + logref, in place in the free buffer
+        SIPF_CUDA(c, launch_export_mass(c, o, c->dl[o], 1));
+        r = copy_out(c, loga, c->dl[o], N * sizeof(double), where);
+    }
+    if (r == SIPF_OK && id) r = copy_out(c, id, c->id[o], N * sizeof(uint32_t), where);
     if (r != SIPF_OK) return r;
     return check_status(c);
 }
@@ -477,7 +540,11 @@ int sipf_particle_state(sipf_ctx* c, float* s, double* loga, uint32_t* id, int w
 int sipf_particles(sipf_ctx* c, float* x, double* mass, uint32_t* id, int where) {
     if (!c) return SIPF_EINVAL;
     if (where != SIPF_HOST && where != SIPF_DEVICE) return fail(c, SIPF_EINVAL, "bad where");
+    if (!c->state_set) return fail(c, SIPF_EINVAL, "sipf_set_state has not been called");
     const size_t N = static_cast<size_t>(c->N);
+    int r = compact_current(c);
+    if (r != SIPF_OK) return r;
+    const int o = c->cur ^ 1;
     float* tx = nullptr;
     double* tm = nullptr;
     cudaError_t e = cudaSuccess;
@@ -487,7 +554,7 @@ int sipf_particles(sipf_ctx* c, float* x, double* mass, uint32_t* id, int where)
             e = dalloc(&tx, 3 * N);
             dx = tx;
         }
-        if (e == cudaSuccess) e = launch_export_positions(c, dx);
+        if (e == cudaSuccess) e = launch_export_positions(c, o, dx);
         if (e == cudaSuccess && where == SIPF_HOST)
             e = cudaMemcpyAsync(x, tx, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
     }
@@ -497,12 +564,12 @@ int sipf_particles(sipf_ctx* c, float* x, double* mass, uint32_t* id, int where)
             e = dalloc(&tm, N);
             dm = tm;
         }
-        if (e == cudaSuccess) e = launch_export_mass(c, dm);
+        if (e == cudaSuccess) e = launch_export_mass(c, o, dm, 0);
         if (e == cudaSuccess && where == SIPF_HOST)
             e = cudaMemcpyAsync(mass, tm, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     }
     if (e == cudaSuccess && id)
-        e = cudaMemcpyAsync(id, c->id[c->cur], N * sizeof(uint32_t),
+        e = cudaMemcpyAsync(id, c->id[o], N * sizeof(uint32_t),
                             where == SIPF_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
                             c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -515,8 +582,12 @@ int sipf_particles(sipf_ctx* c, float* x, double* mass, uint32_t* id, int where)
 int sipf_cell_start(sipf_ctx* c, int32_t* cell_start, int where) {
     if (!c || !cell_start) return SIPF_EINVAL;
     if (where != SIPF_HOST && where != SIPF_DEVICE) return fail(c, SIPF_EINVAL, "bad where");
+    if (!c->state_set) return fail(c, SIPF_EINVAL, "sipf_set_state has not been called");
     const size_t H3 = static_cast<size_t>(c->H) * c->H * c->H;
-    int r = copy_out(c, cell_start, c->cell_start, (H3 + 1) * sizeof(int32_t), where);
+    int r = compact_current(c);
+    if (r != SIPF_OK) return r;
+    SIPF_CUDA(c, launch_cell_histogram(c, c->cur ^ 1, c->count, c->scan_tmp, c->cell_start));
+    r = copy_out(c, cell_start, c->cell_start, (H3 + 1) * sizeof(int32_t), where);
     if (r != SIPF_OK) return r;
     return check_status(c);
 }
@@ -524,9 +595,10 @@ int sipf_cell_start(sipf_ctx* c, int32_t* cell_start, int where) {
 int sipf_diagnostics(sipf_ctx* c, sipf_diag* out) {
     if (!c || !out) return SIPF_EINVAL;
     if (!c->state_set) return fail(c, SIPF_EINVAL, "sipf_set_state has not been called");
-    int r = deposit_current(c);
+    int r = compact_current(c);
+    if (r == SIPF_OK) r = deposit_current(c);
     if (r != SIPF_OK) return r;
-    SIPF_CUDA(c, launch_diagnostics(c, acc_to_u(c)));
+    SIPF_CUDA(c, launch_diagnostics(c, c->cur ^ 1, acc_to_u(c)));
     const size_t H3 = static_cast<size_t>(c->H) * c->H * c->H;
     SIPF_CUDA(c, cudaMemsetAsync(c->acc, 0, H3 * sizeof(long long), c->stream));
     double h[8];
@@ -554,6 +626,12 @@ void sipf_destroy(sipf_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     free_all(c);
     delete c;
 }
@@ -568,7 +646,7 @@ int sipf_profile(sipf_ctx* c, int enable) {
 int sipf_profile_read(sipf_ctx* c, double* ms, int64_t* launches, int n) {
     if (!c || !ms || !launches || n < 1) return SIPF_EINVAL;
     SIPF_CUDA(c, cudaStreamSynchronize(c->stream));
-    static const int per_step[kProfGroups] = {1, 3, 1, 1, 1, 1};
+    static const int per_step[kProfGroups] = {1, 1, 1, 1};
     for (int k = 0; k < n; ++k) {
         ms[k] = 0.0;
         launches[k] = 0;
@@ -586,9 +664,20 @@ int sipf_profile_read(sipf_ctx* c, double* ms, int64_t* launches, int n) {
 }
 
 const char* sipf_profile_name(int k) {
-    static const char* names[kProfGroups] = {"count", "scan", "scatter_deposit", "forward_xy",
-                                             "z_multiply", "inverse_xy"};
+    static const char* names[kProfGroups] = {"particle_step", "forward_xy", "z_multiply",
+                                             "inverse_xy"};
     return (k >= 0 && k < kProfGroups) ? names[k] : "";
+}
+
+int sipf_check_conversions(const float* f, const double* d, int64_t n, int32_t* mismatches,
+                           void* stream) {
+    if (!f || !d || !mismatches || n < 1 || n >= (int64_t{1} << 31)) return SIPF_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(mismatches, 0, 2 * sizeof(int32_t), s) != cudaSuccess) return SIPF_ECUDA;
+    if (launch_conv_check(f, d, static_cast<int>(n), mismatches, s) != cudaSuccess)
+        return SIPF_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SIPF_ECUDA;
+    return SIPF_OK;
 }
 
 int sipf_brownian_normals(const uint32_t* ids, int64_t N, uint32_t n, uint64_t seed, float* z,

@@ -426,37 +426,62 @@ __device__ __forceinline__ float2 pack_two(const float2* r1, const float2* r2, i
     return make_float2(a.x - b.y, a.y + b.x);
 }
 
+// Pack NR row pairs (rows 2r, 2r+1 of B, or row r of B and of B2) into
+// full complex rows Z[r][0..H) of pitch RP; all reads precede all writes.
+template <int H, int NR, int NT, bool PAIRS>
+__device__ __forceinline__ void pack_rows(const float2* B, const float2* B2, float2* Z) {
+    constexpr int KXP = kxp<H>(), RP = rowp<H>(), NE = NR * H, EPT = (NE + NT - 1) / NT;
+    float2 r[EPT];
+#pragma unroll
+    for (int s = 0; s < EPT; ++s) {
+        const int idx = threadIdx.x + s * NT;
+        if (idx < NE) {
+            const int row = idx / H, kx = idx % H;
+            r[s] = PAIRS ? pack_two<H>(B + (2 * row) * KXP, B + (2 * row + 1) * KXP, kx)
+                         : pack_two<H>(B + row * KXP, B2 + row * KXP, kx);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < EPT; ++s) {
+        const int idx = threadIdx.x + s * NT;
+        if (idx < NE) Z[(idx / H) * RP + idx % H] = r[s];
+    }
+    __syncthreads();
+}
+
+// group 0: (m, w) -> m^n, w^n; group 1: (i k_x V, i k_y V, B) -> grad v^n.
 template <int H>
 __global__ void __launch_bounds__(Cfg<H>::NT)
     k_inverse_xy(SpectralArgs a, const float2* __restrict__ gM, const float2* __restrict__ gW,
                  const float2* __restrict__ gV, const float2* __restrict__ gB,
-                 float* __restrict__ m_out, float* __restrict__ w_out, float* __restrict__ gx_out,
-                 float* __restrict__ gy_out, float* __restrict__ gz_out,
+                 float* __restrict__ m_out, float* __restrict__ w_out, float* __restrict__ G,
                  const float2* __restrict__ twg) {
     constexpr int NT = Cfg<H>::NT, KXP = kxp<H>(), HK = H / 2 + 1, RP = rowp<H>();
     static_assert(H * RP <= 2 * H * KXP, "packed rows must fit in B0/B1");
     extern __shared__ float2 sm[];
     float2* B0 = sm;              // [H][KXP]
     float2* B1 = B0 + H * KXP;    // [H][KXP]
+    float2* B2 = B1 + H * KXP;    // [H][KXP] (group 1)
+    float2* tw = B2 + H * KXP;
     float2* Z = sm;               // [H][RP] packed rows (aliases B0/B1)
-    float2* tw = B1 + H * KXP;
-    const int z = blockIdx.x, group = blockIdx.y;   // 0 (m, w), 1 (dv/dx, dv/dy), 2 dv/dz
+    float2* Z2 = B2;              // [H/2][RP] packed row pairs of B2 (aliases B2)
+    const int z = blockIdx.x, group = blockIdx.y;
     if (group == 0 && !a.do_mw) return;
     for (int i = threadIdx.x; i < H; i += NT) tw[i] = twg[i];
     {
         // whole planes of KXP/2 float4 per row, all loads issued first
         constexpr int NQ = H * (KXP / 2), ITER = (NQ + NT - 1) / NT;
         const size_t pbase = static_cast<size_t>(z) * H * KXP;
-        const float4* s0 = reinterpret_cast<const float4*>((group == 0 ? gM : group == 1 ? gV : gB) +
-                                                           pbase);
-        const float4* s1 = reinterpret_cast<const float4*>(gW + pbase);
+        const float4* s0 = reinterpret_cast<const float4*>((group == 0 ? gM : gV) + pbase);
+        const float4* s1 = reinterpret_cast<const float4*>((group == 0 ? gW : gB) + pbase);
         float4 r0[ITER], r1[ITER];
 #pragma unroll
         for (int i = 0; i < ITER; ++i) {
             const int q = threadIdx.x + i * NT;
             if (q < NQ) {
                 r0[i] = s0[q];
-                if (group == 0) r1[i] = s1[q];
+                r1[i] = s1[q];
             }
         }
 #pragma unroll
@@ -464,7 +489,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT)
             const int q = threadIdx.x + i * NT;
             if (q >= NQ) continue;
             if (group == 1) {
-                // i k_x V and i k_y V (Nyquist derivatives zero)
+                // i k_x V and i k_y V (Nyquist derivatives zero); B as loaded
                 const int ky = q / (KXP / 2), kx = 2 * (q % (KXP / 2));
                 const int qy = signed_mode(ky, H);
                 const float kyp = (qy == -H / 2) ? 0.0f : a.two_pi_over_L * static_cast<float>(qy);
@@ -479,75 +504,49 @@ __global__ void __launch_bounds__(Cfg<H>::NT)
                 }
                 reinterpret_cast<float4*>(B0)[q] = make_float4(dx[0].x, dx[0].y, dx[1].x, dx[1].y);
                 reinterpret_cast<float4*>(B1)[q] = make_float4(dy[0].x, dy[0].y, dy[1].x, dy[1].y);
+                reinterpret_cast<float4*>(B2)[q] = r1[i];
             } else {
                 reinterpret_cast<float4*>(B0)[q] = r0[i];
-                if (group == 0) reinterpret_cast<float4*>(B1)[q] = r1[i];
+                reinterpret_cast<float4*>(B1)[q] = r1[i];
             }
         }
     }
     __syncthreads();
     fft_axis<H, HK, KXP, 1, NT, +1>(B0, tw);
-    if (group < 2) {
-        fft_axis<H, HK, KXP, 1, NT, +1>(B1, tw);
-        constexpr int NE = H * H, EPT = (NE + NT - 1) / NT;
-        float2 r[EPT];
-#pragma unroll
-        for (int s = 0; s < EPT; ++s) {
-            const int idx = threadIdx.x + s * NT;
-            if (idx < NE) {
-                const int y = idx / H, kx = idx % H;
-                r[s] = pack_two<H>(B0 + y * KXP, B1 + y * KXP, kx);
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int s = 0; s < EPT; ++s) {
-            const int idx = threadIdx.x + s * NT;
-            if (idx < NE) Z[(idx / H) * RP + idx % H] = r[s];
-        }
-        __syncthreads();
-        fft_axis<H, H, 1, RP, NT, +1>(Z, tw);
-        float* o1 = group == 0 ? m_out : gx_out;
-        float* o2 = group == 0 ? w_out : gy_out;
-        const float sc = group == 0 ? a.out_scale : a.out_scale_xy;
-        const size_t plane = static_cast<size_t>(z) * H * H;
-        float4* p1 = reinterpret_cast<float4*>(o1 + plane);
-        float4* p2 = reinterpret_cast<float4*>(o2 + plane);
+    fft_axis<H, HK, KXP, 1, NT, +1>(B1, tw);
+    if (group == 1) fft_axis<H, HK, KXP, 1, NT, +1>(B2, tw);
+    pack_rows<H, H, NT, false>(B0, B1, Z);
+    if (group == 1) pack_rows<H, H / 2, NT, true>(B2, nullptr, Z2);
+    fft_axis<H, H, 1, RP, NT, +1>(Z, tw);
+    if (group == 1) fft_axis<H, H / 2, 1, RP, NT, +1>(Z2, tw);
+    const size_t plane = static_cast<size_t>(z) * H * H;
+    float* Gp = G + 4 * plane;
+    if (group == 0) {
+        // m^n, w^n, and w^n again as the fourth component of the gather array
+        const float sc = a.out_scale;
+        float4* p1 = reinterpret_cast<float4*>(m_out + plane);
+        float4* p2 = reinterpret_cast<float4*>(w_out + plane);
         for (int g = threadIdx.x; g < H * H / 4; g += NT) {
             const int y = (4 * g) / H, x0 = (4 * g) % H;
             const float2 e0 = Z[y * RP + x0], e1 = Z[y * RP + x0 + 1];
             const float2 e2 = Z[y * RP + x0 + 2], e3 = Z[y * RP + x0 + 3];
             p1[g] = make_float4(e0.x * sc, e1.x * sc, e2.x * sc, e3.x * sc);
-            p2[g] = make_float4(e0.y * sc, e1.y * sc, e2.y * sc, e3.y * sc);
+            const float4 wv = make_float4(e0.y * sc, e1.y * sc, e2.y * sc, e3.y * sc);
+            p2[g] = wv;
+            Gp[16 * g + 3] = wv.x;
+            Gp[16 * g + 7] = wv.y;
+            Gp[16 * g + 11] = wv.z;
+            Gp[16 * g + 15] = wv.w;
         }
     } else {
-        constexpr int NE = (H / 2) * H, EPT = (NE + NT - 1) / NT;
-        float2 r[EPT];
-#pragma unroll
-        for (int s = 0; s < EPT; ++s) {
-            const int idx = threadIdx.x + s * NT;
-            if (idx < NE) {
-                const int p = idx / H, kx = idx % H;
-                r[s] = pack_two<H>(B0 + (2 * p) * KXP, B0 + (2 * p + 1) * KXP, kx);
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int s = 0; s < EPT; ++s) {
-            const int idx = threadIdx.x + s * NT;
-            if (idx < NE) Z[(idx / H) * RP + idx % H] = r[s];
-        }
-        __syncthreads();
-        fft_axis<H, H / 2, 1, RP, NT, +1>(Z, tw);
-        const size_t plane = static_cast<size_t>(z) * H * H;
-        float4* g4 = reinterpret_cast<float4*>(gz_out + plane);
-        const float sc = a.out_scale;
-        for (int g = threadIdx.x; g < NE / 4; g += NT) {
-            const int p = (4 * g) / H, x0 = (4 * g) % H;
-            const float2 e0 = Z[p * RP + x0], e1 = Z[p * RP + x0 + 1];
-            const float2 e2 = Z[p * RP + x0 + 2], e3 = Z[p * RP + x0 + 3];
-            g4[(2 * p * H + x0) / 4] = make_float4(e0.x * sc, e1.x * sc, e2.x * sc, e3.x * sc);
-            g4[((2 * p + 1) * H + x0) / 4] = make_float4(e0.y * sc, e1.y * sc, e2.y * sc, e3.y * sc);
+        // (dv/dx, dv/dy, dv/dz) into components 0..2 of the gather array
+        const float sxy = a.out_scale_xy, sz_ = a.out_scale;
+        for (int i = threadIdx.x; i < H * H; i += NT) {
+            const int y = i / H, x = i % H;
+            const float2 e = Z[y * RP + x];
+            const float2 f = Z2[(y >> 1) * RP + x];
+            *reinterpret_cast<float2*>(Gp + 4 * i) = make_float2(e.x * sxy, e.y * sxy);
+            Gp[4 * i + 2] = ((y & 1) ? f.y : f.x) * sz_;
         }
     }
 }
@@ -557,7 +556,7 @@ cudaError_t spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass) {
     constexpr int NT = Cfg<H>::NT, KXP = kxp<H>(), HK = H / 2 + 1;
     const size_t sm1 = (static_cast<size_t>(H) * rowp<H>() + H * KXP + H) * sizeof(float2);
     const size_t sm2 = (static_cast<size_t>(H) * KXP + H) * sizeof(float2);
-    const size_t sm3 = (2 * static_cast<size_t>(H) * KXP + H) * sizeof(float2);
+    const size_t sm3 = (3 * static_cast<size_t>(H) * KXP + H) * sizeof(float2);
     static int configured_device = -1;   // attributes are set once per process and device
     if (configured_device != c->device) {
         cudaFuncSetAttribute(k_forward_xy<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -577,9 +576,9 @@ cudaError_t spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass) {
                                                              c->specB, c->specA, c->twiddle,
                                                              c->voff);
     } else {
-        k_inverse_xy<H><<<dim3(H, 3), NT, sm3, c->stream>>>(
-            a, c->specM, c->specW, a.filter ? c->specA : c->specV, c->specB, c->m, c->w, c->gx,
-            c->gy, c->gz, c->twiddle);
+        k_inverse_xy<H><<<dim3(H, 2), NT, sm3, c->stream>>>(
+            a, c->specM, c->specW, a.filter ? c->specA : c->specV, c->specB, c->m, c->w, c->G,
+            c->twiddle);
     }
     return cudaGetLastError();
 }

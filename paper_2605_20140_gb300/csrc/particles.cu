@@ -1,19 +1,26 @@
 // Particle side of the SIPF-W step on sm_103a: Philox noise, the
 // Euler-Maruyama push with trilinear gather (paper Eq. u_hat_update, Alg. 2,
-// Eq. g2ph), the per-step counting sort of particles by cell, the
-// particle-to-grid deposit (Alg. 1) and FP64 diagnostics.
+// Eq. g2ph), the particle-to-grid deposit (Alg. 1), the per-step binning of
+// particles by tile, and FP64 diagnostics.
 //
-// Storage: structure of arrays, positions in grid units s = (x - x_min)/h
-// (float32), log-masses (float64), persistent ids (uint32).  The store is
-// bucketed by cell key; each step is two passes over it:
-//   count   : recompute X^n from X^(n-1) and count particles per new cell;
-//   scatter : recompute X^n (bit-identical: same device function, explicit
-//             rounding intrinsics), update the log-mass, deposit u_bar^(n-1)
-//             from X^(n-1), and write each particle into its new cell's run.
-// Deposit values are summed as 64-bit fixed-point integers (a float32
-// contribution times 2^S, exact for all but sub-2^-S parts), so the grid
-// density does not depend on the order of particles within a cell and is
-// bit-reproducible without float atomics.
+// Storage (two buffers, ping-pong): structure of arrays with positions in
+// grid units s = (x - x_min)/h (float32), the log-mass relative to a fixed
+// reference, dl = log a - logref (float64), and persistent ids (uint32).
+// Particles are bucketed by tile (8^3 cells); bucket t of a buffer occupies
+// [bstart[t], bstart[t] + cap[t]) and holds min(cnt[t], cap[t]) particles in
+// unspecified order; arrivals beyond the capacity go to an overflow region
+// of N slots, so no particle is ever dropped.
+//
+// One step is one persistent kernel over "items" (<= 1024 particles of one
+// bucket, or of the overflow region): for each particle it deposits a R_h of
+// X^(n-1) into a 9^3 shared-memory node block of the tile (integer fixed
+// point: float32 contributions scaled by 2^S and rounded to integers, summed
+// exactly, so the density does not depend on particle order and needs no
+// float atomics), gathers grad v and w at X^(n-1), draws the Philox normals,
+// pushes, updates the log-mass, and writes the particle into its new tile's
+// bucket.  Slots are reserved per (item, neighbour tile) with one global
+// atomic; a one-block plan kernel then builds the next step's items and the
+// next bucket layout from the counts.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -24,7 +31,6 @@ namespace sipf {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kNT = 256;
 
 // ------------------------------------------------------------------ Philox
 // Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
@@ -65,52 +71,83 @@ __device__ __forceinline__ float3 brownian(uint32_t id, uint32_t n, uint32_t k0,
     return make_float3(r01 * c1, r01 * s1, r23 * c3);
 }
 
+// ------------------------------------------------------------------ float <-> double by bits
+// The exact IEEE conversions, done with integer operations so that they do
+// not occupy the (narrow) FP64 pipe.  Zeros, subnormals, infinities and NaN
+// take the hardware conversion.
+__device__ __forceinline__ double f2d_bits(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    if (e == 0u || e == 0xFFu) return static_cast<double>(f);
+    const uint32_t hi = (u & 0x80000000u) | ((e + (1023u - 127u)) << 20) | ((u & 0x7FFFFFu) >> 3);
+    const uint32_t lo = u << 29;
+    return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
+}
+
+// Round to nearest, ties to even.
+__device__ __forceinline__ float d2f_bits(double d) {
+    const uint32_t hi = static_cast<uint32_t>(__double2hiint(d));
+    const uint32_t lo = static_cast<uint32_t>(__double2loint(d));
+    const int e = static_cast<int>((hi >> 20) & 0x7FFu) - 1023 + 127;
+    if (e < 1 || e > 254) return __double2float_rn(d);
+    uint32_t m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);     // 23 mantissa bits
+    const uint32_t rem = lo & 0x1FFFFFFFu;                  // 29 dropped bits
+    uint32_t bits = (hi & 0x80000000u) | (static_cast<uint32_t>(e) << 23) | m;
+    if (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) bits += 1u;   // carries into e
+    if (((bits >> 23) & 0xFFu) == 0xFFu) return __double2float_rn(d);
+    return __uint_as_float(bits);
+}
+
 // ------------------------------------------------------------------ cells
 struct Cell {
-    int base;            // flat node index of the cell's lower corner (z*H + y)*H + x
-    int dx, dy, dz;      // offsets to the +1 neighbours (periodic)
+    int cx, cy, cz;      // cell of the particle
     float fx, fy, fz;    // fractional position in the cell
-    uint32_t key;        // tile-major cell key
 };
 
 __device__ __forceinline__ Cell locate(float x, float y, float z, int H) {
     Cell c;
-    int cx = min(static_cast<int>(x), H - 1);
-    int cy = min(static_cast<int>(y), H - 1);
-    int cz = min(static_cast<int>(z), H - 1);
-    c.fx = __fsub_rn(x, __int2float_rn(cx));
-    c.fy = __fsub_rn(y, __int2float_rn(cy));
-    c.fz = __fsub_rn(z, __int2float_rn(cz));
-    c.base = (cz * H + cy) * H + cx;
-    c.dx = (cx + 1 < H) ? 1 : 1 - H;
-    c.dy = (cy + 1 < H) ? H : H - H * H;
-    c.dz = (cz + 1 < H) ? H * H : H * H - H * H * H;
-    const int T = H >> 3;
-    const uint32_t tile = ((cz >> 3) * T + (cy >> 3)) * T + (cx >> 3);
-    c.key = (tile << 9) | ((cz & 7) << 6) | ((cy & 7) << 3) | (cx & 7);
+    c.cx = min(static_cast<int>(x), H - 1);
+    c.cy = min(static_cast<int>(y), H - 1);
+    c.cz = min(static_cast<int>(z), H - 1);
+    c.fx = __fsub_rn(x, __int2float_rn(c.cx));
+    c.fy = __fsub_rn(y, __int2float_rn(c.cy));
+    c.fz = __fsub_rn(z, __int2float_rn(c.cz));
     return c;
 }
 
-__device__ __forceinline__ uint32_t key_of(float x, float y, float z, int H) {
-    return locate(x, y, z, H).key;
+__device__ __forceinline__ int tile_of(int cx, int cy, int cz, int T) {
+    return ((cz >> 3) * T + (cy >> 3)) * T + (cx >> 3);
 }
 
-// Trilinear interpolation (K_h = h^3 R_h, Alg. 2) with a fixed evaluation
-// order: along x, then y, then z.
-__device__ __forceinline__ float interp(const float* __restrict__ f, const Cell& c, float wx0,
-                                        float wy0, float wz0) {
-    const int i = c.base;
-    const float f000 = __ldg(f + i), f100 = __ldg(f + i + c.dx);
-    const float f010 = __ldg(f + i + c.dy), f110 = __ldg(f + i + c.dy + c.dx);
-    const float f001 = __ldg(f + i + c.dz), f101 = __ldg(f + i + c.dz + c.dx);
-    const float f011 = __ldg(f + i + c.dz + c.dy), f111 = __ldg(f + i + c.dz + c.dy + c.dx);
-    const float c00 = __fmaf_rn(c.fx, f100, __fmul_rn(wx0, f000));
-    const float c10 = __fmaf_rn(c.fx, f110, __fmul_rn(wx0, f010));
-    const float c01 = __fmaf_rn(c.fx, f101, __fmul_rn(wx0, f001));
-    const float c11 = __fmaf_rn(c.fx, f111, __fmul_rn(wx0, f011));
-    const float c0 = __fmaf_rn(c.fy, c10, __fmul_rn(wy0, c00));
-    const float c1 = __fmaf_rn(c.fy, c11, __fmul_rn(wy0, c01));
-    return __fmaf_rn(c.fz, c1, __fmul_rn(wz0, c0));
+__device__ __forceinline__ uint32_t cell_key(int cx, int cy, int cz, int T) {
+    return (static_cast<uint32_t>(tile_of(cx, cy, cz, T)) << 9) |
+           static_cast<uint32_t>(((cz & 7) << 6) | ((cy & 7) << 3) | (cx & 7));
+}
+
+// Trilinear interpolation of the float4 field (dv/dx, dv/dy, dv/dz, w)
+// (K_h = h^3 R_h, Alg. 2): along x, then y, then z, with explicit rounding.
+__device__ __forceinline__ float4 gather4(const float4* __restrict__ G, const Cell& c, int H) {
+    const int x1 = c.cx + 1 < H ? c.cx + 1 : 0;
+    const int y1 = c.cy + 1 < H ? c.cy + 1 : 0;
+    const int z1 = c.cz + 1 < H ? c.cz + 1 : 0;
+    const int r00 = (c.cz * H + c.cy) * H, r10 = (c.cz * H + y1) * H;
+    const int r01 = (z1 * H + c.cy) * H, r11 = (z1 * H + y1) * H;
+    const float4 a000 = __ldg(G + r00 + c.cx), a100 = __ldg(G + r00 + x1);
+    const float4 a010 = __ldg(G + r10 + c.cx), a110 = __ldg(G + r10 + x1);
+    const float4 a001 = __ldg(G + r01 + c.cx), a101 = __ldg(G + r01 + x1);
+    const float4 a011 = __ldg(G + r11 + c.cx), a111 = __ldg(G + r11 + x1);
+    const float wx0 = __fsub_rn(1.0f, c.fx), wy0 = __fsub_rn(1.0f, c.fy),
+                wz0 = __fsub_rn(1.0f, c.fz);
+#define SIPF_TRI(f)                                                                      \
+    __fmaf_rn(c.fz,                                                                      \
+              __fmaf_rn(c.fy, __fmaf_rn(c.fx, a111.f, __fmul_rn(wx0, a011.f)),           \
+                        __fmul_rn(wy0, __fmaf_rn(c.fx, a101.f, __fmul_rn(wx0, a001.f)))), \
+              __fmul_rn(wz0,                                                             \
+                        __fmaf_rn(c.fy, __fmaf_rn(c.fx, a110.f, __fmul_rn(wx0, a010.f)), \
+                                  __fmul_rn(wy0, __fmaf_rn(c.fx, a100.f, __fmul_rn(wx0, a000.f))))))
+    const float4 r = make_float4(SIPF_TRI(x), SIPF_TRI(y), SIPF_TRI(z), SIPF_TRI(w));
+#undef SIPF_TRI
+    return r;
 }
 
 // Periodic wrap into [0, H); a result that rounds to H becomes 0.
@@ -126,173 +163,242 @@ __device__ __forceinline__ float wrap(float s, float Hf, int* bad) {
     return r;
 }
 
-struct Fields {
-    const float* gx;
-    const float* gy;
-    const float* gz;
-    const float* w;
-};
-
-// Euler-Maruyama push (Eq. u_hat_update) in grid units:
-// s <- s + (chi tau / h) grad v_H + (sqrt(2 Du tau) / h) z, then wrap.
-__device__ __forceinline__ void push(const PushArgs& a, const Fields& F, const Cell& c,
-                                     uint32_t id, float& x, float& y, float& z, int* bad) {
-    const float wx0 = __fsub_rn(1.0f, c.fx), wy0 = __fsub_rn(1.0f, c.fy),
-                wz0 = __fsub_rn(1.0f, c.fz);
-    const float g0 = interp(F.gx, c, wx0, wy0, wz0);
-    const float g1 = interp(F.gy, c, wx0, wy0, wz0);
-    const float g2 = interp(F.gz, c, wx0, wy0, wz0);
-    const float3 nz = brownian(id, a.n, a.k0, a.k1);
-    const float Hf = __int2float_rn(a.H);
-    x = wrap(__fmaf_rn(a.noise, nz.x, __fmaf_rn(a.drift, g0, x)), Hf, bad);
-    y = wrap(__fmaf_rn(a.noise, nz.y, __fmaf_rn(a.drift, g1, y)), Hf, bad);
-    z = wrap(__fmaf_rn(a.noise, nz.z, __fmaf_rn(a.drift, g2, z)), Hf, bad);
-}
-
-// ------------------------------------------------------------------ kernels
-
-// Pass 1: count particles per cell of X^n (or of X^(n-1) when a.push == 0).
-__global__ void __launch_bounds__(kNT) k_count(PushArgs a, Fields F, const float* __restrict__ sx,
-                                               const float* __restrict__ sy,
-                                               const float* __restrict__ sz,
-                                               const uint32_t* __restrict__ ids, int N,
-                                               int* __restrict__ count) {
-    const int i = blockIdx.x * kNT + threadIdx.x;
-    const bool valid = i < N;
-    uint32_t key = 0xffffffffu;
-    if (valid) {
-        float x = sx[i], y = sy[i], z = sz[i];
-        if (a.push) {
-            int bad = 0;
-            const Cell c = locate(x, y, z, a.H);
-            push(a, F, c, ids[i], x, y, z, &bad);
-        }
-        key = key_of(x, y, z, a.H);
-    }
-    const unsigned peers = __match_any_sync(kFull, key);
-    const int lane = threadIdx.x & 31;
-    if (valid && lane == __ffs(peers) - 1) atomicAdd(count + key, __popc(peers));
-}
-
-struct Store {
+struct Buf {
     float* sx;
     float* sy;
     float* sz;
-    double* loga;
+    double* dl;
     uint32_t* id;
 };
 
-// Pass 2: deposit u_bar^(n-1) (Alg. 1) from X^(n-1), then push, update the
-// log-mass and write the particle into its new cell's run.
-__global__ void __launch_bounds__(kNT)
-    k_scatter(PushArgs a, DepositArgs d, Fields F, Store src, Store dst, int N, int do_deposit,
-              int do_scatter, int* __restrict__ count, const int* __restrict__ cell_start,
-              unsigned long long* __restrict__ acc, int* __restrict__ status) {
-    const int i = blockIdx.x * kNT + threadIdx.x;
-    const bool valid = i < N;
+struct Layout {
+    const int* bstart;
+    const int* cap;
+    int* cnt;
+    int* ovf;
+    int ovf_base;
+    int ovf_cap;
+};
+
+// ------------------------------------------------------------------ the step kernel
+constexpr int kNT = 256;                  // threads of the step kernel
+constexpr int kPT = 4;                    // particles per thread and item
+constexpr int kItem = kNT * kPT;          // particles per item
+constexpr int kBlock = 9 * 9 * 9;         // nodes of a tile's deposit block
+
+// Per-item staging of the pushed particles between the two phases.
+struct Staged {
+    float x[kItem], y[kItem], z[kItem];
+    double l[kItem];
+    uint32_t id[kItem];
+    int tile[kItem];      // destination tile
+    int slot[kItem];      // neighbour index (< 27) << 22 | rank, or -1 (far / overflow item)
+};
+
+__global__ void __launch_bounds__(kNT, 3)
+    k_step(PushArgs a, DepositArgs d, const float4* __restrict__ G, Buf src, Buf dst, Layout L,
+           const Item* __restrict__ items, const int* __restrict__ n_items,
+           unsigned long long* __restrict__ acc, int do_deposit, int do_move,
+           int* __restrict__ status) {
+    __shared__ unsigned dep_lo[kBlock];     // node sums of the low / high 16 bits
+    __shared__ unsigned dep_hi[kBlock];
+    __shared__ Staged st;
+    __shared__ int nb_cnt[27];
+    __shared__ int nb_base[27];
+    __shared__ int nb_tile[27];     // tile index, bucket start and capacity of the
+    __shared__ int nb_start[27];    // 27 tiles around the item's tile
+    __shared__ int nb_cap[27];
+    const int H = a.H, T = H >> 3;
     const int lane = threadIdx.x & 31;
-    float x = 0.f, y = 0.f, z = 0.f;
-    double la = 0.0;
-    uint32_t id = 0;
-    Cell c{};
-    if (valid) {
-        x = src.sx[i];
-        y = src.sy[i];
-        z = src.sz[i];
-        la = src.loga[i];
-        id = src.id[i];
-        c = locate(x, y, z, a.H);
-    }
-    const float wx0 = __fsub_rn(1.0f, c.fx), wy0 = __fsub_rn(1.0f, c.fy),
-                wz0 = __fsub_rn(1.0f, c.fz);
-
-    if (do_deposit) {
-        // a_p * R_h(X_p, node) * h^3 in units of exp(logref) 2^-S.
-        long long q[8];
-        {
-            const float ea = valid ? __fmul_rn(expf(static_cast<float>(la - d.logref)), d.scale)
-                                   : 0.0f;
-            const float e0 = __fmul_rn(ea, wz0), e1 = __fmul_rn(ea, c.fz);
-            const float xy00 = __fmul_rn(wx0, wy0), xy10 = __fmul_rn(c.fx, wy0);
-            const float xy01 = __fmul_rn(wx0, c.fy), xy11 = __fmul_rn(c.fx, c.fy);
-            q[0] = __float2ll_rn(__fmul_rn(e0, xy00));
-            q[1] = __float2ll_rn(__fmul_rn(e0, xy10));
-            q[2] = __float2ll_rn(__fmul_rn(e0, xy01));
-            q[3] = __float2ll_rn(__fmul_rn(e0, xy11));
-            q[4] = __float2ll_rn(__fmul_rn(e1, xy00));
-            q[5] = __float2ll_rn(__fmul_rn(e1, xy10));
-            q[6] = __float2ll_rn(__fmul_rn(e1, xy01));
-            q[7] = __float2ll_rn(__fmul_rn(e1, xy11));
+    const float Hf = __int2float_rn(H);
+    const int total = *n_items;
+    // items are assigned statically: block b takes items b, b + grid, ...
+    for (int item_idx = blockIdx.x; item_idx < total; item_idx += gridDim.x) {
+        for (int i = threadIdx.x; i < kBlock; i += kNT) {
+            dep_lo[i] = 0u;
+            dep_hi[i] = 0u;
         }
-        const uint32_t key0 = __shfl_sync(kFull, c.key, 0);
-        const bool uniform = __all_sync(kFull, valid && c.key == key0);
-        const int node[8] = {c.base,
-                             c.base + c.dx,
-                             c.base + c.dy,
-                             c.base + c.dy + c.dx,
-                             c.base + c.dz,
-                             c.base + c.dz + c.dx,
-                             c.base + c.dz + c.dy,
-                             c.base + c.dz + c.dy + c.dx};
-        if (uniform) {
-            // whole warp in one cell: integer butterfly sum, one atomic per corner
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) q[j] += __shfl_xor_sync(kFull, q[j], off);
+        const Item it = items[item_idx];
+        const int tile = it.tile;
+        const int ttx = it.tx, tty = it.ty, ttz = it.tz;
+        const int tx0 = ttx * 8, ty0 = tty * 8, tz0 = ttz * 8;
+        if (threadIdx.x < 27) {
+            const int k = threadIdx.x;
+            nb_cnt[k] = 0;
+            if (do_move && tile >= 0) {
+                const int nx = ttx + k % 3 - 1, ny = tty + (k / 3) % 3 - 1, nz = ttz + k / 9 - 1;
+                const int nt = (((nz + T) % T) * T + (ny + T) % T) * T + (nx + T) % T;
+                nb_tile[k] = nt;
+                nb_start[k] = L.bstart[nt];
+                nb_cap[k] = L.cap[nt];
             }
-            if (lane == 0) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    atomicAdd(acc + node[j], static_cast<unsigned long long>(q[j]));
-            }
-        } else if (valid) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                if (q[j]) atomicAdd(acc + node[j], static_cast<unsigned long long>(q[j]));
         }
-    }
+        __syncthreads();
+        int bad = 0;
+        for (int j = 0; j < kPT; ++j) {
+            const int e = j * kNT + threadIdx.x;     // element of the item, coalesced
+            const int i = it.beg + e;
+            const bool valid = i < it.end;
+            float px = 0.f, py = 0.f, pz = 0.f;
+            double pl = 0.0;
+            uint32_t pid = 0u;
+            if (valid) {
+                px = src.sx[i];
+                py = src.sy[i];
+                pz = src.sz[i];
+                pl = src.dl[i];
+                pid = src.id[i];
+            }
+            const Cell c = locate(px, py, pz, H);
 
-    if (!do_scatter) return;
-    int bad = 0;
-    if (valid && a.push) {
-        // mass factor 1 + tau (rho(w_H) - 1), rho(w) = 2w/(1+w) (Eq. u_hat_update)
-        const float wH = interp(F.w, c, wx0, wy0, wz0);
-        const float rho = __fdiv_rn(2.0f * wH, __fadd_rn(1.0f, wH));
-        const float inc = log1pf(__fmul_rn(a.tau, __fsub_rn(rho, 1.0f)));
-        la += static_cast<double>(inc);
-        push(a, F, c, id, x, y, z, &bad);
+            if (do_deposit && valid) {
+                // a_p R_h(X_p, node) h^3 in units of exp(logref) 2^-S, as uint32 (< 2^31)
+                const float ea = __fmul_rn(expf(d2f_bits(pl)), d.scale);
+                const float wx0 = __fsub_rn(1.0f, c.fx), wy0 = __fsub_rn(1.0f, c.fy);
+                const float e0 = __fmul_rn(ea, __fsub_rn(1.0f, c.fz)), e1 = __fmul_rn(ea, c.fz);
+                const float xy[4] = {__fmul_rn(wx0, wy0), __fmul_rn(c.fx, wy0),
+                                     __fmul_rn(wx0, c.fy), __fmul_rn(c.fx, c.fy)};
+                uint32_t q[8];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    q[k] = __float2uint_rn(__fmul_rn(e0, xy[k]));
+                    q[4 + k] = __float2uint_rn(__fmul_rn(e1, xy[k]));
+                }
+                const int lx = c.cx - tx0, ly = c.cy - ty0, lz = c.cz - tz0;
+                const bool in_tile = tile >= 0 && ((lx | ly | lz) & ~7) == 0;
+                if (tile >= 0 && !in_tile) bad |= 2;   // bucket does not match position
+                if (in_tile) {
+                    // particles of a bucket are in random cells of the tile, so lanes
+                    // rarely collide: one shared atomic per corner and half (16-bit
+                    // halves keep the 32-bit sums of an item exact)
+                    const int nbase = (lz * 9 + ly) * 9 + lx;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int node = nbase + (k & 1) + ((k >> 1) & 1) * 9 + (k >> 2) * 81;
+                        if (q[k]) {
+                            atomicAdd(dep_lo + node, q[k] & 0xFFFFu);
+                            atomicAdd(dep_hi + node, q[k] >> 16);
+                        }
+                    }
+                } else {
+                    const int x1 = c.cx + 1 < H ? c.cx + 1 : 0;
+                    const int y1 = c.cy + 1 < H ? c.cy + 1 : 0;
+                    const int z1 = c.cz + 1 < H ? c.cz + 1 : 0;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int nx = (k & 1) ? x1 : c.cx, ny = ((k >> 1) & 1) ? y1 : c.cy;
+                        const int nz = (k >> 2) ? z1 : c.cz;
+                        if (q[k])
+                            atomicAdd(acc + (nz * H + ny) * H + nx,
+                                      static_cast<unsigned long long>(q[k]));
+                    }
+                }
+            }
+
+            if (do_move) {
+                if (a.push && valid) {
+                    const float4 g = gather4(G, c, H);
+                    // mass factor 1 + tau (rho(w_H) - 1), rho(w) = 2w/(1+w) (Eq. u_hat_update)
+                    const float rho = __fdiv_rn(2.0f * g.w, __fadd_rn(1.0f, g.w));
+                    const float inc = log1pf(__fmul_rn(a.tau, __fsub_rn(rho, 1.0f)));
+                    pl = pl + f2d_bits(inc);
+                    // Euler-Maruyama push in grid units
+                    const float3 nz = brownian(pid, a.n, a.k0, a.k1);
+                    px = wrap(__fmaf_rn(a.noise, nz.x, __fmaf_rn(a.drift, g.x, px)), Hf, &bad);
+                    py = wrap(__fmaf_rn(a.noise, nz.y, __fmaf_rn(a.drift, g.y, py)), Hf, &bad);
+                    pz = wrap(__fmaf_rn(a.noise, nz.z, __fmaf_rn(a.drift, g.z, pz)), Hf, &bad);
+                }
+                const Cell cn = locate(px, py, pz, H);
+                const int ntx = cn.cx >> 3, nty = cn.cy >> 3, ntz = cn.cz >> 3;
+                const int nt = (ntz * T + nty) * T + ntx;
+                int nb = -1;
+                if (tile >= 0) {
+                    int ddx = ntx - ttx, ddy = nty - tty, ddz = ntz - ttz;
+                    ddx = ddx == T - 1 ? -1 : ddx == 1 - T ? 1 : ddx;
+                    ddy = ddy == T - 1 ? -1 : ddy == 1 - T ? 1 : ddy;
+                    ddz = ddz == T - 1 ? -1 : ddz == 1 - T ? 1 : ddz;
+                    if (ddx >= -1 && ddx <= 1 && ddy >= -1 && ddy <= 1 && ddz >= -1 && ddz <= 1)
+                        nb = ((ddz + 1) * 3 + (ddy + 1)) * 3 + (ddx + 1);
+                }
+                // rank within this item among particles bound for the same neighbour tile
+                const int nkey = valid && nb >= 0 ? nb : -1;
+                const unsigned peers = __match_any_sync(kFull, nkey);
+                const int leader = __ffs(peers) - 1;
+                int old = 0;
+                if (nkey >= 0 && lane == leader) old = atomicAdd(nb_cnt + nb, __popc(peers));
+                old = __shfl_sync(kFull, old, leader);
+                st.x[e] = px;
+                st.y[e] = py;
+                st.z[e] = pz;
+                st.l[e] = pl;
+                st.id[e] = pid;
+                st.tile[e] = valid ? nt : -2;
+                st.slot[e] = nb >= 0 ? (nb << 22) | (old + __popc(peers & ((1u << lane) - 1u))) : -1;
+            }
+        }
+        if (bad & 1) atomicOr(status, kStatusNonfinite);
+        if (bad & 2) atomicOr(status, kStatusSlot);
+        __syncthreads();
+        if (do_move) {
+            if (threadIdx.x < 27 && nb_cnt[threadIdx.x] > 0)
+                nb_base[threadIdx.x] = atomicAdd(L.cnt + nb_tile[threadIdx.x], nb_cnt[threadIdx.x]);
+            __syncthreads();
+            for (int j = 0; j < kPT; ++j) {
+                const int e = j * kNT + threadIdx.x;
+                const int nt = st.tile[e];
+                const int code = st.slot[e];
+                // far moves and overflow items: per-warp aggregated reservation
+                // (every lane takes part in the warp-collective calls)
+                const int fkey = (nt >= 0 && code < 0) ? nt : -1;
+                const unsigned peers = __match_any_sync(kFull, fkey);
+                const int leader = __ffs(peers) - 1;
+                int old = 0;
+                if (fkey >= 0 && lane == leader) old = atomicAdd(L.cnt + nt, __popc(peers));
+                old = __shfl_sync(kFull, old, leader);
+                if (nt < 0) continue;
+                const int nb = code >= 0 ? (code >> 22) : -1;
+                const int slot = nb >= 0 ? nb_base[nb] + (code & 0x3FFFFF)
+                                         : old + __popc(peers & ((1u << lane) - 1u));
+                const int cp = nb >= 0 ? nb_cap[nb] : L.cap[nt];
+                int dest = -1;
+                if (slot < cp) {
+                    dest = (nb >= 0 ? nb_start[nb] : L.bstart[nt]) + slot;
+                } else {
+                    const int o = atomicAdd(L.ovf, 1);
+                    if (o < L.ovf_cap)
+                        dest = L.ovf_base + o;
+                    else
+                        atomicOr(status, kStatusSlot);
+                }
+                if (dest >= 0) {
+                    dst.sx[dest] = st.x[e];
+                    dst.sy[dest] = st.y[e];
+                    dst.sz[dest] = st.z[e];
+                    dst.dl[dest] = st.l[e];
+                    dst.id[dest] = st.id[e];
+                }
+            }
+        }
+        __syncthreads();
+        if (do_deposit && tile >= 0) {
+            // flush the tile's node block into the grid accumulator
+            for (int j = threadIdx.x; j < kBlock; j += kNT) {
+                const unsigned long long v =
+                    (static_cast<unsigned long long>(dep_hi[j]) << 16) + dep_lo[j];
+                if (v) {
+                    const int lx = j % 9, ly = (j / 9) % 9, lz = j / 81;
+                    const int nx = (tx0 + lx) % H, ny = (ty0 + ly) % H, nz = (tz0 + lz) % H;
+                    atomicAdd(acc + (nz * H + ny) * H + nx, v);
+                }
+            }
+        }
+        __syncthreads();
     }
-    const uint32_t key = valid ? key_of(x, y, z, a.H) : 0xffffffffu;
-    const unsigned peers = __match_any_sync(kFull, key);
-    const int leader = __ffs(peers) - 1;
-    int old = 0;
-    if (valid && lane == leader) old = atomicSub(count + key, __popc(peers));
-    old = __shfl_sync(kFull, old, leader);
-    if (!valid) return;
-    if (bad) atomicOr(status, kStatusNonfinite);
-    const int rank = __popc(peers & ((1u << lane) - 1u));
-    const int slot = old - 1 - rank;
-    const int start = cell_start[key], end = cell_start[key + 1];
-    const int dest = start + slot;
-    if (slot < 0 || dest >= end) {
-        atomicOr(status, kStatusSlot);
-        return;
-    }
-    dst.sx[dest] = x;
-    dst.sy[dest] = y;
-    dst.sz[dest] = z;
-    dst.loga[dest] = la;
-    dst.id[dest] = id;
 }
 
-// ------------------------------------------------------------------ scan
-// Exclusive prefix sum of the per-cell counts in three phases with fixed
-// tiles (no inter-block waits): tile sums, a one-block scan of the tile
-// sums, then the per-tile scan plus its offset.
-constexpr int kScanNT = 1024;
-constexpr int kScanIPT = 8;
-constexpr int kScanTile = kScanNT * kScanIPT;
+// ------------------------------------------------------------------ planning
+// Block-wide exclusive scan (one value per thread) of kPlanNT threads.
+constexpr int kPlanNT = 1024;
 
 __device__ __forceinline__ int block_exclusive_scan(int v, int* smem, int* total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -322,6 +428,140 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* smem, int* total
     return r;
 }
 
+// From the counts of buffer `b` (just written): the items that read it next
+// (tile buckets split into kItem chunks, then the overflow region) with
+// their offsets in the compacted particle order; and, when next_cnt is not
+// null, the bucket layout of the other buffer for the next step (capacity
+// count + count/8 + 32, rounded up to a multiple of 4) with its counters
+// reset.
+__global__ void __launch_bounds__(kPlanNT)
+    k_plan(int ntiles, int T, const int* __restrict__ cnt, const int* __restrict__ cap,
+           const int* __restrict__ bstart, const int* __restrict__ ovf, int ovf_base, Item* items,
+           int* n_items, int* next_bstart, int* next_cap, int* next_cnt, int* next_ovf,
+           int* __restrict__ status) {
+    __shared__ int smem[33];
+    const int per = (ntiles + kPlanNT - 1) / kPlanNT;
+    const int t0 = threadIdx.x * per;
+    int my_items = 0, my_fill = 0, my_cap = 0;
+    for (int k = 0; k < per; ++k) {
+        const int t = t0 + k;
+        if (t >= ntiles) break;
+        const int c = cnt[t];
+        const int f = min(c, cap[t]);
+        my_items += (f + kItem - 1) / kItem;
+        my_fill += f;
+        if (next_cnt) my_cap += ((c + c / 8 + 32) + 3) & ~3;
+    }
+    int tot_items, tot_fill, tot_cap;
+    int item0 = block_exclusive_scan(my_items, smem, &tot_items);
+    int out0 = block_exclusive_scan(my_fill, smem, &tot_fill);
+    int cap0 = next_cnt ? block_exclusive_scan(my_cap, smem, &tot_cap) : 0;
+    for (int k = 0; k < per; ++k) {
+        const int t = t0 + k;
+        if (t >= ntiles) break;
+        const int c = cnt[t];
+        const int f = min(c, cap[t]);
+        for (int q = 0; q * kItem < f; ++q) {
+            Item it;
+            it.tile = t;
+            it.beg = bstart[t] + q * kItem;
+            it.end = bstart[t] + min((q + 1) * kItem, f);
+            it.out = out0 + q * kItem;
+            it.tx = t % T;
+            it.ty = (t / T) % T;
+            it.tz = t / (T * T);
+            it.pad = 0;
+            items[item0++] = it;
+        }
+        out0 += f;
+        if (next_cnt) {
+            const int cp = ((c + c / 8 + 32) + 3) & ~3;
+            next_bstart[t] = cap0;
+            next_cap[t] = cp;
+            next_cnt[t] = 0;
+            cap0 += cp;
+        }
+    }
+    if (threadIdx.x == 0) {
+        const int no = *ovf;
+        int n = tot_items;
+        for (int q = 0; q * kItem < no; ++q) {
+            Item it;
+            it.tile = -1;
+            it.beg = ovf_base + q * kItem;
+            it.end = ovf_base + min((q + 1) * kItem, no);
+            it.out = tot_fill + q * kItem;
+            it.tx = it.ty = it.tz = it.pad = 0;
+            items[n++] = it;
+        }
+        *n_items = n;
+        if (next_ovf) *next_ovf = 0;
+        if (tot_fill + no < 0) atomicOr(status, kStatusTotal);
+    }
+}
+
+// Particles per tile of an unbinned input array (positions already wrapped).
+__global__ void k_tile_count(const float* __restrict__ sx, const float* __restrict__ sy,
+                             const float* __restrict__ sz, int N, int H, int* __restrict__ cnt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int t = -1;
+    if (i < N) {
+        const Cell c = locate(sx[i], sy[i], sz[i], H);
+        t = tile_of(c.cx, c.cy, c.cz, H >> 3);
+    }
+    const unsigned peers = __match_any_sync(kFull, t);
+    if (t >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(cnt + t, __popc(peers));
+}
+
+// Whole input as overflow-style items (tile -1) for the initial binning.
+__global__ void k_plan_flat(int N, Item* items, int* n_items) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nq = (N + kItem - 1) / kItem;
+    if (q < nq) {
+        Item it;
+        it.tile = -1;
+        it.beg = q * kItem;
+        it.end = min((q + 1) * kItem, N);
+        it.out = q * kItem;
+        it.tx = it.ty = it.tz = it.pad = 0;
+        items[q] = it;
+    }
+    if (q == 0) *n_items = nq;
+}
+
+// Compacted copy of the live particles (items in order) into `out`.
+__global__ void k_compact(const Item* __restrict__ items, const int* __restrict__ n_items,
+                          Buf src, Buf out) {
+    const int q = blockIdx.x;
+    if (q >= *n_items) return;
+    const Item it = items[q];
+    for (int i = it.beg + threadIdx.x; i < it.end; i += blockDim.x) {
+        const int o = it.out + (i - it.beg);
+        out.sx[o] = src.sx[i];
+        out.sy[o] = src.sy[i];
+        out.sz[o] = src.sz[i];
+        out.dl[o] = src.dl[i];
+        out.id[o] = src.id[i];
+    }
+}
+
+// ------------------------------------------------------------------ per-cell histogram
+__global__ void k_cell_count(const float* __restrict__ sx, const float* __restrict__ sy,
+                             const float* __restrict__ sz, int N, int H, int* __restrict__ count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t key = 0xffffffffu;
+    if (i < N) {
+        const Cell c = locate(sx[i], sy[i], sz[i], H);
+        key = cell_key(c.cx, c.cy, c.cz, H >> 3);
+    }
+    const unsigned peers = __match_any_sync(kFull, key);
+    if (i < N && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(count + key, __popc(peers));
+}
+
+constexpr int kScanNT = 1024;
+constexpr int kScanIPT = 8;
+constexpr int kScanTile = kScanNT * kScanIPT;
+
 __global__ void __launch_bounds__(kScanNT) k_scan_tiles(const int* __restrict__ count, int n,
                                                         int* __restrict__ tile_sum) {
     __shared__ int smem[33];
@@ -338,8 +578,7 @@ __global__ void __launch_bounds__(kScanNT) k_scan_tiles(const int* __restrict__ 
 }
 
 __global__ void __launch_bounds__(kScanNT) k_scan_tile_sums(int* __restrict__ tile_sum, int ntiles,
-                                                            int* __restrict__ cell_start, int n,
-                                                            int N, int* __restrict__ status) {
+                                                            int* __restrict__ cell_start, int n) {
     __shared__ int smem[33];
     int carry = 0;
     for (int b0 = 0; b0 < ntiles; b0 += kScanNT) {
@@ -350,10 +589,7 @@ __global__ void __launch_bounds__(kScanNT) k_scan_tile_sums(int* __restrict__ ti
         if (j < ntiles) tile_sum[j] = carry + ex;
         carry += total;
     }
-    if (threadIdx.x == 0) {
-        cell_start[n] = carry;
-        if (carry != N) atomicOr(status, kStatusTotal);
-    }
+    if (threadIdx.x == 0) cell_start[n] = carry;
 }
 
 __global__ void __launch_bounds__(kScanNT) k_scan_apply(const int* __restrict__ count, int n,
@@ -399,9 +635,9 @@ __global__ void k_wrap_positions(const float* __restrict__ x, int N, float o0, f
     if (bad) atomicOr(status, kStatusNonfinite);
 }
 
-__global__ void k_log_mass(const double* __restrict__ mass, int N, double* loga) {
+__global__ void k_rel_log_mass(const double* __restrict__ mass, int N, double logref, double* dl) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) loga[i] = log(mass[i]);
+    if (i < N) dl[i] = log(mass[i]) - logref;
 }
 
 __global__ void k_iota(uint32_t* id, int N) {
@@ -419,9 +655,10 @@ __global__ void k_export_positions(const float* __restrict__ sx, const float* __
     x[2 * N + i] = __fmaf_rn(sz[i], h, o2);
 }
 
-__global__ void k_export_mass(const double* __restrict__ loga, int N, double* mass) {
+__global__ void k_export_mass(const double* __restrict__ dl, int N, double logref, double* out,
+                              int as_log) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) mass[i] = exp(loga[i]);
+    if (i < N) out[i] = as_log ? dl[i] + logref : exp(dl[i] + logref);
 }
 
 // u_bar = acc * scale; the accumulator is cleared for the next deposit.
@@ -429,27 +666,29 @@ __global__ void k_acc_to_float(unsigned long long* __restrict__ acc, int n, floa
                                float* __restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const long long q = static_cast<long long>(acc[i]);
+    const unsigned long long q = acc[i];
     acc[i] = 0ull;
-    out[i] = __fmul_rn(__ll2float_rn(q), scale);
+    const float f = fmaf(__uint2float_rn(static_cast<unsigned>(q >> 32)), 4294967296.0f,
+                         __uint2float_rn(static_cast<unsigned>(q)));
+    out[i] = f * scale;
+}
+
+// One component of the interleaved (dv/dx, dv/dy, dv/dz, w) array.
+__global__ void k_component(const float4* __restrict__ G, int n, int comp, float* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 g = G[i];
+    out[i] = comp == 0 ? g.x : comp == 1 ? g.y : g.z;
 }
 
 // Diagnostics: deterministic two-level reduction (fixed grid, fixed trees).
 constexpr int kDiagBlocks = 304;
 constexpr int kDiagNT = 256;
 
-struct DiagPart {
-    double mass;      // sum exp(loga)
-    double minv, minm, minw;
-    double nonfinite;
-    long long accsum; // fixed-point sum of u_bar
-    long long accmin;
-};
-
 __device__ __forceinline__ double dmin(double a, double b) { return a < b ? a : b; }
 
 __global__ void __launch_bounds__(kDiagNT)
-    k_diag_partials(const double* __restrict__ loga, const float* __restrict__ sx,
+    k_diag_partials(const double* __restrict__ dl, double logref, const float* __restrict__ sx,
                     const float* __restrict__ sy, const float* __restrict__ sz, int N,
                     const float* __restrict__ v, const float* __restrict__ m,
                     const float* __restrict__ w, const unsigned long long* __restrict__ acc,
@@ -458,7 +697,7 @@ __global__ void __launch_bounds__(kDiagNT)
     long long as = 0, amin = LLONG_MAX;
     const int stride = kDiagBlocks * kDiagNT;
     for (int i = blockIdx.x * kDiagNT + threadIdx.x; i < N; i += stride) {
-        mass += exp(loga[i]);
+        mass += exp(dl[i] + logref);
         if (!isfinite(sx[i]) || !isfinite(sy[i]) || !isfinite(sz[i])) nf += 1.0;
     }
     for (int i = blockIdx.x * kDiagNT + threadIdx.x; i < ncell; i += stride) {
@@ -541,42 +780,95 @@ __global__ void k_normals(const uint32_t* __restrict__ ids, int N, uint32_t n, u
     }
 }
 
+// Bit-exactness check of the integer float<->double conversions.
+__global__ void k_conv_check(const float* __restrict__ f, const double* __restrict__ d, int n,
+                             int* __restrict__ mismatches) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double a = f2d_bits(f[i]);
+    const double b = static_cast<double>(f[i]);
+    const float c = d2f_bits(d[i]);
+    const float e = __double2float_rn(d[i]);
+    const bool same_ab = __double_as_longlong(a) == __double_as_longlong(b) || (isnan(a) && isnan(b));
+    const bool same_ce = __float_as_uint(c) == __float_as_uint(e) || (isnan(c) && isnan(e));
+    if (!same_ab) atomicAdd(mismatches, 1);
+    if (!same_ce) atomicAdd(mismatches + 1, 1);
+}
+
 inline int blocks_for(int64_t n, int nt) { return static_cast<int>((n + nt - 1) / nt); }
 
-inline Fields fields_of(sipf_ctx* c) { return Fields{c->gx, c->gy, c->gz, c->w}; }
+inline Buf buf_of(sipf_ctx* c, int b) {
+    return Buf{c->sx[b], c->sy[b], c->sz[b], c->dl[b], c->id[b]};
+}
 
-inline Store store_of(sipf_ctx* c, int b) {
-    return Store{c->sx[b], c->sy[b], c->sz[b], c->loga[b], c->id[b]};
+inline Layout layout_of(sipf_ctx* c, int b) {
+    return Layout{c->bstart[b], c->cap[b], c->cnt[b], c->ovf[b], c->ovf_base,
+                  static_cast<int>(c->N)};
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
-cudaError_t launch_count(sipf_ctx* c, const PushArgs& a) {
+int step_grid(sipf_ctx* c) {
+    int dev = c->device, nsm = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step, kNT, 0);
+    const int g = nsm * (per_sm > 0 ? per_sm : 1);
+    return g > 0 ? g : 1;
+}
+
+cudaError_t launch_step_kernel(sipf_ctx* c, const PushArgs& a, const DepositArgs& d,
+                               int do_deposit, int do_move) {
     const int b = c->cur;
-    k_count<<<blocks_for(c->N, kNT), kNT, 0, c->stream>>>(a, fields_of(c), c->sx[b], c->sy[b],
-                                                           c->sz[b], c->id[b],
-                                                           static_cast<int>(c->N), c->count);
+    k_step<<<c->step_blocks, kNT, 0, c->stream>>>(
+        a, d, reinterpret_cast<const float4*>(c->G), buf_of(c, b), buf_of(c, b ^ 1),
+        layout_of(c, b ^ 1), c->items, c->n_items,
+        reinterpret_cast<unsigned long long*>(c->acc), do_deposit, do_move, c->status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan(sipf_ctx* c) {
+// Items of buffer `b` and, with next_layout, the layout of b ^ 1.
+cudaError_t launch_plan(sipf_ctx* c, int b, int next_layout, cudaStream_t s) {
+    const int o = b ^ 1;
+    k_plan<<<1, kPlanNT, 0, s>>>(
+        c->ntiles, c->H / 8, c->cnt[b], c->cap[b], c->bstart[b], c->ovf[b], c->ovf_base, c->items,
+        c->n_items, next_layout ? c->bstart[o] : nullptr,
+        next_layout ? c->cap[o] : nullptr, next_layout ? c->cnt[o] : nullptr,
+        next_layout ? c->ovf[o] : nullptr, c->status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_count(sipf_ctx* c, int b, int* cnt) {
+    const int N = static_cast<int>(c->N);
+    k_tile_count<<<blocks_for(N, 256), 256, 0, c->stream>>>(c->sx[b], c->sy[b], c->sz[b], N, c->H,
+                                                             cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plan_flat(sipf_ctx* c) {
+    const int nq = (static_cast<int>(c->N) + kItem - 1) / kItem;
+    k_plan_flat<<<blocks_for(nq, 256), 256, 0, c->stream>>>(static_cast<int>(c->N), c->items,
+                                                             c->n_items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact(sipf_ctx* c, int b, int out) {
+    k_compact<<<c->max_items, 256, 0, c->stream>>>(c->items, c->n_items, buf_of(c, b),
+                                                   buf_of(c, out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_histogram(sipf_ctx* c, int b, int* count, int* tmp, int* cell_start) {
+    const int N = static_cast<int>(c->N);
     const int n = c->H * c->H * c->H;
     const int ntiles = (n + kScanTile - 1) / kScanTile;
-    k_scan_tiles<<<ntiles, kScanNT, 0, c->stream>>>(c->count, n, c->scan_tmp);
-    k_scan_tile_sums<<<1, kScanNT, 0, c->stream>>>(c->scan_tmp, ntiles, c->cell_start, n,
-                                                   static_cast<int>(c->N), c->status);
-    k_scan_apply<<<ntiles, kScanNT, 0, c->stream>>>(c->count, n, c->scan_tmp, c->cell_start);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_scatter(sipf_ctx* c, const PushArgs& a, const DepositArgs& d, int deposit,
-                           int scatter) {
-    const int b = c->cur;
-    k_scatter<<<blocks_for(c->N, kNT), kNT, 0, c->stream>>>(
-        a, d, fields_of(c), store_of(c, b), store_of(c, b ^ 1), static_cast<int>(c->N), deposit,
-        scatter, c->count, c->cell_start, reinterpret_cast<unsigned long long*>(c->acc),
-        c->status);
+    cudaError_t e = cudaMemsetAsync(count, 0, static_cast<size_t>(n) * sizeof(int), c->stream);
+    if (e != cudaSuccess) return e;
+    k_cell_count<<<blocks_for(N, 256), 256, 0, c->stream>>>(c->sx[b], c->sy[b], c->sz[b], N, c->H,
+                                                             count);
+    k_scan_tiles<<<ntiles, kScanNT, 0, c->stream>>>(count, n, tmp);
+    k_scan_tile_sums<<<1, kScanNT, 0, c->stream>>>(tmp, ntiles, cell_start, n);
+    k_scan_apply<<<ntiles, kScanNT, 0, c->stream>>>(count, n, tmp, cell_start);
     return cudaGetLastError();
 }
 
@@ -589,9 +881,9 @@ cudaError_t launch_wrap_positions(sipf_ctx* c, const float* x, int buf) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_log_mass(sipf_ctx* c, const double* mass, int buf) {
+cudaError_t launch_rel_log_mass(sipf_ctx* c, const double* mass, int buf) {
     const int N = static_cast<int>(c->N);
-    k_log_mass<<<blocks_for(N, 256), 256, 0, c->stream>>>(mass, N, c->loga[buf]);
+    k_rel_log_mass<<<blocks_for(N, 256), 256, 0, c->stream>>>(mass, N, c->logref, c->dl[buf]);
     return cudaGetLastError();
 }
 
@@ -601,8 +893,8 @@ cudaError_t launch_iota(sipf_ctx* c, int buf) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_export_positions(sipf_ctx* c, float* x) {
-    const int N = static_cast<int>(c->N), b = c->cur;
+cudaError_t launch_export_positions(sipf_ctx* c, int b, float* x) {
+    const int N = static_cast<int>(c->N);
     k_export_positions<<<blocks_for(N, 256), 256, 0, c->stream>>>(
         c->sx[b], c->sy[b], c->sz[b], N, static_cast<float>(c->origin[0]),
         static_cast<float>(c->origin[1]), static_cast<float>(c->origin[2]),
@@ -610,9 +902,9 @@ cudaError_t launch_export_positions(sipf_ctx* c, float* x) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_export_mass(sipf_ctx* c, double* mass) {
+cudaError_t launch_export_mass(sipf_ctx* c, int b, double* out, int as_log) {
     const int N = static_cast<int>(c->N);
-    k_export_mass<<<blocks_for(N, 256), 256, 0, c->stream>>>(c->loga[c->cur], N, mass);
+    k_export_mass<<<blocks_for(N, 256), 256, 0, c->stream>>>(c->dl[b], N, c->logref, out, as_log);
     return cudaGetLastError();
 }
 
@@ -623,11 +915,17 @@ cudaError_t launch_acc_to_float(sipf_ctx* c, float* dst, float scale) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_diagnostics(sipf_ctx* c, float acc_to_u) {
-    const int b = c->cur;
+cudaError_t launch_component(sipf_ctx* c, int comp, float* dst) {
+    const int n = c->H * c->H * c->H;
+    k_component<<<blocks_for(n, 256), 256, 0, c->stream>>>(reinterpret_cast<const float4*>(c->G), n,
+                                                            comp, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics(sipf_ctx* c, int b, float acc_to_u) {
     k_diag_partials<<<kDiagBlocks, kDiagNT, 0, c->stream>>>(
-        c->loga[b], c->sx[b], c->sy[b], c->sz[b], static_cast<int>(c->N), c->v, c->m, c->w,
-        reinterpret_cast<const unsigned long long*>(c->acc), c->H * c->H * c->H, c->diag_tmp,
+        c->dl[b], c->logref, c->sx[b], c->sy[b], c->sz[b], static_cast<int>(c->N), c->v, c->m,
+        c->w, reinterpret_cast<const unsigned long long*>(c->acc), c->H * c->H * c->H, c->diag_tmp,
         c->diag_ll);
     k_diag_final<<<1, 32, 0, c->stream>>>(c->diag_tmp, c->diag_ll, static_cast<double>(acc_to_u),
                                           c->diag_out);
@@ -642,8 +940,15 @@ cudaError_t launch_normals(const uint32_t* ids, int64_t N, uint32_t n, uint64_t 
     return cudaGetLastError();
 }
 
+cudaError_t launch_conv_check(const float* f, const double* d, int n, int* mismatches,
+                              cudaStream_t s) {
+    k_conv_check<<<blocks_for(n, 256), 256, 0, s>>>(f, d, n, mismatches);
+    return cudaGetLastError();
+}
+
 size_t diag_scratch_doubles() { return static_cast<size_t>(kDiagBlocks) * 5; }
 size_t diag_scratch_ll() { return static_cast<size_t>(kDiagBlocks) * 2; }
 int scan_tiles(int n) { return (n + kScanTile - 1) / kScanTile; }
+int item_size() { return kItem; }
 
 }  // namespace sipf

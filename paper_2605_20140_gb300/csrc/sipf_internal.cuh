@@ -17,11 +17,11 @@ constexpr int kMaxH = 128;          // largest grid of this build
 
 // Device status bits (ORed into ctx->status by kernels, read by sipf_sync).
 constexpr int kStatusNonfinite = 1;   // a pushed position was NaN/inf (reset to 0)
-constexpr int kStatusSlot = 2;        // scatter slot outside its cell's run
-constexpr int kStatusTotal = 4;       // cell counts did not sum to N
+constexpr int kStatusSlot = 2;        // overflow region full, or a bucket/position mismatch
+constexpr int kStatusTotal = 4;       // particle counts inconsistent
 
 // Kernel groups of a step, in launch order (tracing).
-constexpr int kProfGroups = 6;
+constexpr int kProfGroups = 4;
 constexpr int kProfMaxSteps = 4096;
 
 // Per-step scalars of the particle kernels.
@@ -36,10 +36,21 @@ struct PushArgs {
 };
 
 // Deposit scaling: contribution of a particle to a corner node is
-// exp(loga - logref) * weight, stored as the integer round(value * 2^S).
+// exp(log a - logref) * weight, stored as the integer round(value * 2^S) < 2^31.
 struct DepositArgs {
-    double logref;    // reference log-mass subtracted before the float exp
     float scale;      // 2^S
+};
+
+// A run of particles read by one block of the step kernel: [beg, end) of a
+// buffer, all in bucket `tile` (or tile = -1 for the overflow region / an
+// unbinned input), written at `out` in the compacted particle order.
+struct Item {
+    int tile;
+    int beg;
+    int end;
+    int out;
+    int tx, ty, tz;   // tile coordinates (0 for tile = -1)
+    int pad;
 };
 
 // Spectral-step scalars.
@@ -74,29 +85,43 @@ struct sipf_ctx {
     int64_t N = 0;
     sipf_params p{};
     cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;         // plan kernel, concurrent with the spectral passes
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join = nullptr;
     int device = 0;
 
-    // particle store, ping-pong (storage order = bucketed by cell key)
+    // particle store, ping-pong; positions in grid units, log-mass relative
+    // to logref, ids; tile buckets followed by an overflow region of N
     float* sx[2] = {nullptr, nullptr};
     float* sy[2] = {nullptr, nullptr};
     float* sz[2] = {nullptr, nullptr};
-    double* loga[2] = {nullptr, nullptr};
+    double* dl[2] = {nullptr, nullptr};
     uint32_t* id[2] = {nullptr, nullptr};
     int cur = 0;
+    int ntiles = 0;                      // (H/8)^3
+    int ovf_base = 0;                    // first slot of the overflow region
+    int64_t buf_slots = 0;               // slots per buffer
+    int* bstart[2] = {nullptr, nullptr}; // bucket layout per buffer
+    int* cap[2] = {nullptr, nullptr};
+    int* cnt[2] = {nullptr, nullptr};    // arrivals per bucket (incl. overflowed)
+    int* ovf[2] = {nullptr, nullptr};    // particles in the overflow region
+    sipf::Item* items = nullptr;         // items of the current buffer
+    int* n_items = nullptr;
+    int* work = nullptr;                 // work counter of the persistent step kernel
+    int max_items = 0;
+    int step_blocks = 0;
 
-    // binning
-    int32_t* count = nullptr;        // H^3, zero between steps
-    int32_t* cell_start = nullptr;   // H^3 + 1, of the current store
-    int32_t* scan_tmp = nullptr;     // block sums of the scan
+    // per-cell histogram (sipf_cell_start)
+    int32_t* count = nullptr;        // H^3
+    int32_t* cell_start = nullptr;   // H^3 + 1
+    int32_t* scan_tmp = nullptr;
 
     // grid
     long long* acc = nullptr;        // H^3 fixed-point deposit accumulator, zero between steps
     float* v = nullptr;
     float* m = nullptr;
     float* w = nullptr;
-    float* gx = nullptr;
-    float* gy = nullptr;
-    float* gz = nullptr;
+    float* G = nullptr;              // H^3 float4 (dv/dx, dv/dy, dv/dz, w) for the gather
     float2* specM = nullptr;         // half spectra [z][ky][kx], row pitch kxp
     float2* specW = nullptr;
     float2* specV = nullptr;
@@ -119,6 +144,7 @@ struct sipf_ctx {
     int64_t step = 0;
     double time = 0;
     double logref = 0;               // log(M0 / N) of the initial state
+    double maxrel = 1;               // max_p a_p(0) / exp(logref)
     float voff_host = 0;             // staging value for voff
     bool state_set = false;
     std::string last_error;
@@ -128,18 +154,30 @@ namespace sipf {
 
 // ---------------------------------------------------------------- launchers
 // particles.cu
-cudaError_t launch_count(sipf_ctx* c, const PushArgs& a);
-cudaError_t launch_scan(sipf_ctx* c);
-cudaError_t launch_scatter(sipf_ctx* c, const PushArgs& a, const DepositArgs& d, int deposit,
-                           int scatter);
+int step_grid(sipf_ctx* c);
+int item_size();
+size_t diag_scratch_doubles();
+size_t diag_scratch_ll();
+int scan_tiles(int n);
+cudaError_t launch_step_kernel(sipf_ctx* c, const PushArgs& a, const DepositArgs& d,
+                               int do_deposit, int do_move);
+cudaError_t launch_plan(sipf_ctx* c, int b, int next_layout, cudaStream_t s);
+cudaError_t launch_tile_count(sipf_ctx* c, int b, int* cnt);
+cudaError_t launch_plan_flat(sipf_ctx* c);
+cudaError_t launch_compact(sipf_ctx* c, int b, int out);
+cudaError_t launch_cell_histogram(sipf_ctx* c, int b, int* count, int* tmp, int* cell_start);
 cudaError_t launch_wrap_positions(sipf_ctx* c, const float* x, int buf);
-cudaError_t launch_log_mass(sipf_ctx* c, const double* mass, int buf);
-cudaError_t launch_export_positions(sipf_ctx* c, float* x);
-cudaError_t launch_export_mass(sipf_ctx* c, double* mass);
+cudaError_t launch_rel_log_mass(sipf_ctx* c, const double* mass, int buf);
+cudaError_t launch_iota(sipf_ctx* c, int buf);
+cudaError_t launch_export_positions(sipf_ctx* c, int b, float* x);
+cudaError_t launch_export_mass(sipf_ctx* c, int b, double* out, int as_log);
 cudaError_t launch_acc_to_float(sipf_ctx* c, float* dst, float scale);
-cudaError_t launch_diagnostics(sipf_ctx* c, float acc_to_u);
+cudaError_t launch_component(sipf_ctx* c, int comp, float* dst);
+cudaError_t launch_diagnostics(sipf_ctx* c, int b, float acc_to_u);
 cudaError_t launch_normals(const uint32_t* ids, int64_t N, uint32_t n, uint64_t seed, float* z,
                            uint32_t* bits, cudaStream_t s);
+cudaError_t launch_conv_check(const float* f, const double* d, int n, int* mismatches,
+                              cudaStream_t s);
 // fft.cu
 cudaError_t launch_spectral_step(sipf_ctx* c, const SpectralArgs& a);
 cudaError_t launch_spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass);

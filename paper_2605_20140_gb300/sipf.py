@@ -34,9 +34,9 @@ EXPORTED = (
     "sipf_create", "sipf_set_state", "sipf_step", "sipf_fields", "sipf_particles",
     "sipf_particle_state", "sipf_cell_start", "sipf_diagnostics", "sipf_sync",
     "sipf_destroy", "sipf_strerror", "sipf_last_error", "sipf_brownian_normals",
-    "sipf_profile", "sipf_profile_read", "sipf_profile_name",
+    "sipf_profile", "sipf_profile_read", "sipf_profile_name", "sipf_check_conversions",
 )
-PROFILE_GROUPS = 6
+PROFILE_GROUPS = 4
 
 
 class sipf_grid(ctypes.Structure):
@@ -95,6 +95,7 @@ def load() -> ctypes.CDLL:
         "sipf_profile": ([P, I32], I32),
         "sipf_profile_read": ([P, P, P, I32], I32),
         "sipf_profile_name": ([I32], ctypes.c_char_p),
+        "sipf_check_conversions": ([P, P, I64, P, P], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -184,6 +185,11 @@ def sipf_destroy(ctx):
 def sipf_brownian_normals(ids_dev, N: int, n: int, seed: int, z_dev, bits_dev=None, stream=0):
     _check(load().sipf_brownian_normals(_ptr(ids_dev), int(N), int(n), int(seed), _ptr(z_dev),
                                         _ptr(bits_dev), ctypes.c_void_p(stream or None)))
+
+
+def sipf_check_conversions(f_dev, d_dev, n: int, mism_dev, stream=0):
+    _check(load().sipf_check_conversions(_ptr(f_dev), _ptr(d_dev), int(n), _ptr(mism_dev),
+                                         ctypes.c_void_p(stream or None)))
 
 
 def sipf_profile(ctx, enable: bool):
