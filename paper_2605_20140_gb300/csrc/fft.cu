@@ -168,11 +168,13 @@ __device__ __forceinline__ void fft_axis(float2* buf, const float2* tw) {
     stage<L, R2, R1, NTRANS, ES, TS, NT, SIGN>(buf, tw);
 }
 
+// Threads per block of the three passes (forward xy, z, inverse xy).
 template <int H> struct Cfg;
-template <> struct Cfg<16> { static constexpr int NT = 256; };
-template <> struct Cfg<32> { static constexpr int NT = 256; };
-template <> struct Cfg<64> { static constexpr int NT = 512; };
-template <> struct Cfg<128> { static constexpr int NT = 512; };
+template <> struct Cfg<16> { static constexpr int NT1 = 256, NT2 = 256, NT3 = 256; };
+template <> struct Cfg<32> { static constexpr int NT1 = 256, NT2 = 256, NT3 = 256; };
+template <> struct Cfg<64> { static constexpr int NT1 = 512, NT2 = 512, NT3 = 512; };
+// 544 = 17 warps: one radix-16 butterfly per thread for the 65 z-transforms
+template <> struct Cfg<128> { static constexpr int NT1 = 1024, NT2 = 544, NT3 = 1024; };
 
 template <int H> constexpr int kxp() { return H / 2 + 2; }
 // shared-memory pitch (float2) of rows that are transformed along the row
@@ -206,13 +208,13 @@ __device__ __forceinline__ void react(const SpectralArgs& a, float vv, float mm,
 
 // ---------------------------------------------------------------- pass 1
 template <int H>
-__global__ void __launch_bounds__(Cfg<H>::NT)
+__global__ void __launch_bounds__(Cfg<H>::NT1)
     k_forward_xy(SpectralArgs a, const float* v, const float* __restrict__ m,
                  const float* __restrict__ w, unsigned long long* __restrict__ acc,
                  float* v_out, float2* __restrict__ gM, float2* __restrict__ gW,
                  float2* __restrict__ gV, const float2* __restrict__ twg,
                  const float* __restrict__ voff) {
-    constexpr int NT = Cfg<H>::NT, KXP = kxp<H>(), HK = H / 2 + 1, RP = rowp<H>();
+    constexpr int NT = Cfg<H>::NT1, KXP = kxp<H>(), HK = H / 2 + 1, RP = rowp<H>();
     extern __shared__ float2 sm[];
     float2* Z = sm;               // [H][RP]: m* + i w*
     float2* Vb = Z + H * RP;      // v^n: [H/2][RP] row pairs, then [H][KXP] half rows
@@ -333,11 +335,11 @@ __global__ void __launch_bounds__(Cfg<H>::NT)
 
 // ---------------------------------------------------------------- pass 2
 template <int H>
-__global__ void __launch_bounds__(Cfg<H>::NT)
+__global__ void __launch_bounds__(Cfg<H>::NT2)
     k_z_multiply(SpectralArgs a, float2* __restrict__ gM, float2* __restrict__ gW,
                  const float2* __restrict__ gV, float2* __restrict__ gB, float2* __restrict__ gA,
                  const float2* __restrict__ twg, float* __restrict__ voff) {
-    constexpr int NT = Cfg<H>::NT, KXP = kxp<H>(), HK = H / 2 + 1;
+    constexpr int NT = Cfg<H>::NT2, KXP = kxp<H>(), HK = H / 2 + 1;
     extern __shared__ float2 sm[];
     float2* buf = sm;             // [H (z)][KXP (kx)]
     float2* tw = buf + H * KXP;
@@ -452,12 +454,12 @@ __device__ __forceinline__ void pack_rows(const float2* B, const float2* B2, flo
 
 // group 0: (m, w) -> m^n, w^n; group 1: (i k_x V, i k_y V, B) -> grad v^n.
 template <int H>
-__global__ void __launch_bounds__(Cfg<H>::NT)
+__global__ void __launch_bounds__(Cfg<H>::NT3)
     k_inverse_xy(SpectralArgs a, const float2* __restrict__ gM, const float2* __restrict__ gW,
                  const float2* __restrict__ gV, const float2* __restrict__ gB,
                  float* __restrict__ m_out, float* __restrict__ w_out, float* __restrict__ G,
                  const float2* __restrict__ twg) {
-    constexpr int NT = Cfg<H>::NT, KXP = kxp<H>(), HK = H / 2 + 1, RP = rowp<H>();
+    constexpr int NT = Cfg<H>::NT3, KXP = kxp<H>(), HK = H / 2 + 1, RP = rowp<H>();
     static_assert(H * RP <= 2 * H * KXP, "packed rows must fit in B0/B1");
     extern __shared__ float2 sm[];
     float2* B0 = sm;              // [H][KXP]
@@ -553,7 +555,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT)
 
 template <int H>
 cudaError_t spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass) {
-    constexpr int NT = Cfg<H>::NT, KXP = kxp<H>(), HK = H / 2 + 1;
+    constexpr int KXP = kxp<H>();
     const size_t sm1 = (static_cast<size_t>(H) * rowp<H>() + H * KXP + H) * sizeof(float2);
     const size_t sm2 = (static_cast<size_t>(H) * KXP + H) * sizeof(float2);
     const size_t sm3 = (3 * static_cast<size_t>(H) * KXP + H) * sizeof(float2);
@@ -568,15 +570,15 @@ cudaError_t spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass) {
         configured_device = c->device;
     }
     if (pass == 0) {
-        k_forward_xy<H><<<H, NT, sm1, c->stream>>>(
+        k_forward_xy<H><<<H, Cfg<H>::NT1, sm1, c->stream>>>(
             a, c->v, c->m, c->w, reinterpret_cast<unsigned long long*>(c->acc), c->v, c->specM,
             c->specW, c->specV, c->twiddle, c->voff);
     } else if (pass == 1) {
-        k_z_multiply<H><<<dim3(H, 4), NT, sm2, c->stream>>>(a, c->specM, c->specW, c->specV,
+        k_z_multiply<H><<<dim3(H, 4), Cfg<H>::NT2, sm2, c->stream>>>(a, c->specM, c->specW, c->specV,
                                                              c->specB, c->specA, c->twiddle,
                                                              c->voff);
     } else {
-        k_inverse_xy<H><<<dim3(H, 2), NT, sm3, c->stream>>>(
+        k_inverse_xy<H><<<dim3(H, 2), Cfg<H>::NT3, sm3, c->stream>>>(
             a, c->specM, c->specW, a.filter ? c->specA : c->specV, c->specB, c->m, c->w, c->G,
             c->twiddle);
     }

@@ -27,6 +27,10 @@
 
 #include "sipf_internal.cuh"
 
+#ifndef SIPF_DEP64
+#define SIPF_DEP64 0
+#endif
+
 namespace sipf {
 namespace {
 
@@ -195,13 +199,21 @@ struct Staged {
     int slot[kItem];      // neighbour index (< 27) << 22 | rank, or -1 (far / overflow item)
 };
 
-__global__ void __launch_bounds__(kNT, 3)
+#ifndef SIPF_STEP_MIN_BLOCKS
+#define SIPF_STEP_MIN_BLOCKS 4
+#endif
+
+__global__ void __launch_bounds__(kNT, SIPF_STEP_MIN_BLOCKS)
     k_step(PushArgs a, DepositArgs d, const float4* __restrict__ G, Buf src, Buf dst, Layout L,
            const Item* __restrict__ items, const int* __restrict__ n_items,
            unsigned long long* __restrict__ acc, int do_deposit, int do_move,
            int* __restrict__ status) {
+#if SIPF_DEP64
+    __shared__ unsigned long long dep64[kBlock];   // node sums
+#else
     __shared__ unsigned dep_lo[kBlock];     // node sums of the low / high 16 bits
     __shared__ unsigned dep_hi[kBlock];
+#endif
     __shared__ Staged st;
     __shared__ int nb_cnt[27];
     __shared__ int nb_base[27];
@@ -215,8 +227,12 @@ __global__ void __launch_bounds__(kNT, 3)
     // items are assigned statically: block b takes items b, b + grid, ...
     for (int item_idx = blockIdx.x; item_idx < total; item_idx += gridDim.x) {
         for (int i = threadIdx.x; i < kBlock; i += kNT) {
+#if SIPF_DEP64
+            dep64[i] = 0ull;
+#else
             dep_lo[i] = 0u;
             dep_hi[i] = 0u;
+#endif
         }
         const Item it = items[item_idx];
         const int tile = it.tile;
@@ -269,16 +285,20 @@ __global__ void __launch_bounds__(kNT, 3)
                 if (tile >= 0 && !in_tile) bad |= 2;   // bucket does not match position
                 if (in_tile) {
                     // particles of a bucket are in random cells of the tile, so lanes
-                    // rarely collide: one shared atomic per corner and half (16-bit
-                    // halves keep the 32-bit sums of an item exact)
+                    // rarely collide: one shared atomic per corner
                     const int nbase = (lz * 9 + ly) * 9 + lx;
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
                         const int node = nbase + (k & 1) + ((k >> 1) & 1) * 9 + (k >> 2) * 81;
+#if SIPF_DEP64
+                        if (q[k]) atomicAdd(dep64 + node, static_cast<unsigned long long>(q[k]));
+#else
+                        // 16-bit halves keep the 32-bit sums of an item exact
                         if (q[k]) {
                             atomicAdd(dep_lo + node, q[k] & 0xFFFFu);
                             atomicAdd(dep_hi + node, q[k] >> 16);
                         }
+#endif
                     }
                 } else {
                     const int x1 = c.cx + 1 < H ? c.cx + 1 : 0;
@@ -350,11 +370,14 @@ __global__ void __launch_bounds__(kNT, 3)
                 // far moves and overflow items: per-warp aggregated reservation
                 // (every lane takes part in the warp-collective calls)
                 const int fkey = (nt >= 0 && code < 0) ? nt : -1;
-                const unsigned peers = __match_any_sync(kFull, fkey);
-                const int leader = __ffs(peers) - 1;
+                unsigned peers = 0u;
                 int old = 0;
-                if (fkey >= 0 && lane == leader) old = atomicAdd(L.cnt + nt, __popc(peers));
-                old = __shfl_sync(kFull, old, leader);
+                if (__any_sync(kFull, fkey >= 0)) {
+                    peers = __match_any_sync(kFull, fkey);
+                    const int leader = __ffs(peers) - 1;
+                    if (fkey >= 0 && lane == leader) old = atomicAdd(L.cnt + nt, __popc(peers));
+                    old = __shfl_sync(kFull, old, leader);
+                }
                 if (nt < 0) continue;
                 const int nb = code >= 0 ? (code >> 22) : -1;
                 const int slot = nb >= 0 ? nb_base[nb] + (code & 0x3FFFFF)
@@ -383,8 +406,12 @@ __global__ void __launch_bounds__(kNT, 3)
         if (do_deposit && tile >= 0) {
             // flush the tile's node block into the grid accumulator
             for (int j = threadIdx.x; j < kBlock; j += kNT) {
+#if SIPF_DEP64
+                const unsigned long long v = dep64[j];
+#else
                 const unsigned long long v =
                     (static_cast<unsigned long long>(dep_hi[j]) << 16) + dep_lo[j];
+#endif
                 if (v) {
                     const int lx = j % 9, ly = (j / 9) % 9, lz = j / 81;
                     const int nx = (tx0 + lx) % H, ny = (ty0 + ly) % H, nz = (tz0 + lz) % H;
