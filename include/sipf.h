@@ -211,6 +211,32 @@ int sipf_profile(sipf_ctx* ctx, int enable);
 int sipf_profile_read(sipf_ctx* ctx, double* ms, int64_t* launches, int n);
 const char* sipf_profile_name(int k);
 
+/* Allocation-free deposit.  The paper has no counterpart: this entry point
+ * exists for callers that may not allocate device memory when they need a
+ * density -- code running under another framework's memory budget (whose
+ * caching allocator must not see foreign cudaMalloc/cudaFree calls, which
+ * also synchronise the device), real-time loops that may not block or fail
+ * on allocation, or plug-ins that are handed only pre-allocated buffers.
+ * It computes the same particle-to-grid deposit u_bar as sipf_fields with
+ * SIPF_FIELD_U, for N particles with physical positions x (3*N floats, SoA,
+ * wrapped into the box) and masses `mass` (N doubles, >= 0), into u (H^3
+ * floats, [z][y][x]); x, mass and u are device pointers owned by the caller.
+ * It calls no cudaMalloc, cudaFree or other allocating routine: its integer
+ * accumulator is a fixed array in the library's device memory, sized for at
+ * most 64^3 nodes, which every GPU that loads the library keeps until the
+ * process exits.  Grids with H > 64 are rejected with SIPF_EINVAL, as are
+ * NULL pointers, N < 1 or N >= 2^31, and a non-positive or non-finite L.
+ * Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default
+ * stream) and the call returns without waiting; launch failures return
+ * SIPF_ECUDA.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and should come before any stream capture.
+ * Every call on a device shares the one array and clears it before use, so
+ * calls whose work overlaps on the GPU (different streams, or threads
+ * without ordering) race and corrupt each other's results; order them on
+ * one stream. */
+int sipf_deposit_noalloc(const sipf_grid* grid, const float* x, const double* mass, int64_t N,
+                         float* u, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,6 +35,7 @@ EXPORTED = (
     "sipf_particle_state", "sipf_cell_start", "sipf_diagnostics", "sipf_sync",
     "sipf_destroy", "sipf_strerror", "sipf_last_error", "sipf_brownian_normals",
     "sipf_profile", "sipf_profile_read", "sipf_profile_name", "sipf_check_conversions",
+    "sipf_deposit_noalloc",
 )
 PROFILE_GROUPS = 4
 
@@ -96,6 +97,7 @@ def load() -> ctypes.CDLL:
         "sipf_profile_read": ([P, P, P, I32], I32),
         "sipf_profile_name": ([I32], ctypes.c_char_p),
         "sipf_check_conversions": ([P, P, I64, P, P], I32),
+        "sipf_deposit_noalloc": ([ctypes.POINTER(sipf_grid), P, P, I64, P, P], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -190,6 +192,14 @@ def sipf_brownian_normals(ids_dev, N: int, n: int, seed: int, z_dev, bits_dev=No
 def sipf_check_conversions(f_dev, d_dev, n: int, mism_dev, stream=0):
     _check(load().sipf_check_conversions(_ptr(f_dev), _ptr(d_dev), int(n), _ptr(mism_dev),
                                          ctypes.c_void_p(stream or None)))
+
+
+def sipf_deposit_noalloc(grid: sipf_grid, x_dev, mass_dev, N: int, u_dev, stream=0):
+    """Deposit u_bar of N particles into u_dev without allocating device memory
+    (for callers that may not allocate; grids up to 64^3).  Asynchronous on
+    `stream`; overlapping calls on one GPU share the library's scratch and race."""
+    _check(load().sipf_deposit_noalloc(ctypes.byref(grid), _ptr(x_dev), _ptr(mass_dev), int(N),
+                                       _ptr(u_dev), ctypes.c_void_p(stream or None)))
 
 
 def sipf_profile(ctx, enable: bool):
