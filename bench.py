@@ -3,16 +3,17 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sipf|reference]
 
-One step = one pass of the whole hot path (count, scan, scatter+deposit,
-three spectral passes) over the synthetic headline workload (three Gaussian
+One step = one pass of the whole hot path (the particle step: deposit,
+gather, push, mass update and binning; the bucket plan; three spectral
+passes) over the synthetic headline workload (three Gaussian
 tumour seeds at seeded centres, sigma 0.04, unit periodic cube, dt 5e-4).
 Prints one JSON line on rank 0.  Under torchrun (N > 1) every rank runs an
 independent replica on its own GPU (no data-path collective); the timed
 region is bracketed by a barrier and the slowest rank's time is used.
 
 --impl reference times the FP64 oracle on the host cores (the paper ships
-no code; the oracle is the reference arm), each step on a particle sample
-of the same workload.
+no code; the oracle is the reference arm), each step on a bounded sample of
+the same workload recipe.
 """
 
 from __future__ import annotations
@@ -40,7 +41,7 @@ WORKLOAD = "headline: 128^3 grid, 2^22 particles, 3 Gaussian seeds (sigma 0.04),
 # float32 field touches of the reaction, solve, gather and deposit.
 ALGO_B_PER_PARTICLE = 40
 ALGO_B_PER_NODE = 60
-# share of the per-node bytes that belongs to the scatter/deposit kernel
+# share of the per-node bytes that belongs to the particle-step kernel
 # (gather of dv/dx, dv/dy, dv/dz, w: 16 B; deposit of u: 4 B)
 SCATTER_B_PER_NODE = 20
 
@@ -157,12 +158,23 @@ def _cpu_baseline(wl_fn, n_sample_steps=1):
 
 
 def run_reference(args, rank, world):
+    """The FP64 oracle on the host cores.  Each step is one oracle step of the
+    headline recipe on a bounded sample, sized from --steps and --warmup so
+    the whole run takes about two minutes: the full 128^3 grid with 2^16
+    particles when the budget allows (~1.4 s per step), else a 64^3 or 32^3
+    grid with fewer particles."""
     if rank != 0:
         return 0
     from oracle import sipf_oracle as O
     from sipf_inputs import workload
-    n_sample = 1 << 16
-    wl = workload("headline", N=n_sample)
+    budget = 120.0 / max(args.steps + args.warmup, 1)
+    if budget >= 2.0:
+        H, n_sample = 128, 1 << 16
+    elif budget >= 0.3:
+        H, n_sample = 64, 1 << 15
+    else:
+        H, n_sample = 32, 1 << 14
+    wl = workload("headline", H=H, N=n_sample)
     st = O.make_state(wl.H, wl.L, wl.origin, wl.params, wl.x, wl.mass, wl.ids, wl.v, wl.m, wl.w)
     for _ in range(args.warmup):
         st = O.step(st, wl.dt)
@@ -171,13 +183,13 @@ def run_reference(args, rank, world):
         st = O.step(st, wl.dt)
     el = time.perf_counter() - t0
     value = n_sample * args.steps / el
-    sample = (f"each step: one oracle step on the full 128^3 grid with a 2^16-particle sample "
-              f"of the workload ({el / args.steps:.2f} s/step)")
+    sample = (f"each step: one FP64 oracle step of the headline recipe on a {H}^3 grid with "
+              f"{n_sample} particles ({el / args.steps:.3f} s/step, NumPy, single thread)")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": WORKLOAD + " (particle-sampled)", "H": wl.H, "N": n_sample},
+           "config": {"workload": WORKLOAD + " (sampled)", "H": H, "N": n_sample},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -233,7 +245,7 @@ def run_sipf(args, rank, world, local):
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms, dom_launches = prof[dom]
     per_launch_s = dom_ms * 1e-3 / max(dom_launches, 1)
-    algo = {"scatter_deposit": ALGO_B_PER_PARTICLE * N + SCATTER_B_PER_NODE * H ** 3}
+    algo = {"particle_step": ALGO_B_PER_PARTICLE * N + SCATTER_B_PER_NODE * H ** 3}
     algo_bytes = algo.get(dom)
     roofline = None
     if algo_bytes is not None:
@@ -248,7 +260,8 @@ def run_sipf(args, rank, world, local):
     kernels = {k: {"ms_per_step": v[0] / max(args.steps, 1), "launches": v[1],
                    "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-12)}
                for k, v in prof.items()}
-    launches = sum(v[1] for v in prof.values())
+    # the bucket-layout plan kernel runs on the context's second stream, once per step
+    launches = sum(v[1] for v in prof.values()) + args.steps
     sim.close()
 
     # ---- end to end through the C ABI with host buffers
@@ -297,7 +310,7 @@ def run_sipf(args, rank, world, local):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["sipf", "reference"], default="sipf")
     ap.add_argument("--no-e2e", action="store_true")

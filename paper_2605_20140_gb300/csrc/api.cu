@@ -100,11 +100,12 @@ int check_status(sipf_ctx* c) {
 
 // Fixed-point scale 2^S of the deposit: one contribution is at most
 // max_p a_p / exp(logref) <= maxrel e^t (Lemma mass: a grows by at most
-// 1 + tau <= e^tau per step), and must stay below 2^31 after scaling; node
-// sums are accumulated in 64-bit integers.
+// 1 + tau <= e^tau per step), and must stay below 2^21 after scaling, so
+// that the sums of one 1024-particle item fit exactly in 32 bits; node sums
+// over the whole grid are accumulated in 64-bit integers.
 int deposit_shift(const sipf_ctx* c) {
     const double bound = log2(c->maxrel) + c->time * 1.4426950408889634 + 0.5;
-    int S = static_cast<int>(floor(30.0 - bound));
+    int S = static_cast<int>(floor(20.0 - bound));
     if (S > 40) S = 40;
     if (S < -60) S = -60;
     return S;

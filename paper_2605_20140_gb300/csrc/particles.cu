@@ -14,9 +14,9 @@
 // One step is one persistent kernel over "items" (<= 1024 particles of one
 // bucket, or of the overflow region): for each particle it deposits a R_h of
 // X^(n-1) into a 9^3 shared-memory node block of the tile (integer fixed
-// point: float32 contributions scaled by 2^S and rounded to integers, summed
-// exactly, so the density does not depend on particle order and needs no
-// float atomics), gathers grad v and w at X^(n-1), draws the Philox normals,
+// point: float32 contributions scaled by 2^S below 2^21 and rounded to
+// integers, summed exactly, so the density does not depend on particle order
+// and needs no float atomics), gathers grad v and w at X^(n-1), draws the Philox normals,
 // pushes, updates the log-mass, and writes the particle into its new tile's
 // bucket.  Slots are reserved per (item, neighbour tile) with one global
 // atomic; a one-block plan kernel then builds the next step's items and the
@@ -26,10 +26,6 @@
 #include <stdint.h>
 
 #include "sipf_internal.cuh"
-
-#ifndef SIPF_DEP64
-#define SIPF_DEP64 0
-#endif
 
 namespace sipf {
 namespace {
@@ -154,6 +150,27 @@ __device__ __forceinline__ float4 gather4(const float4* __restrict__ G, const Ce
     return r;
 }
 
+// The same interpolation from a tile's 9^3 node block in shared memory
+// (node (lx, ly, lz) at (lz * 9 + ly) * 9 + lx).
+__device__ __forceinline__ float4 gather4_block(const float4* B, const Cell& c, int base) {
+    const float4 a000 = B[base], a100 = B[base + 1];
+    const float4 a010 = B[base + 9], a110 = B[base + 10];
+    const float4 a001 = B[base + 81], a101 = B[base + 82];
+    const float4 a011 = B[base + 90], a111 = B[base + 91];
+    const float wx0 = __fsub_rn(1.0f, c.fx), wy0 = __fsub_rn(1.0f, c.fy),
+                wz0 = __fsub_rn(1.0f, c.fz);
+#define SIPF_TRI(f)                                                                      \
+    __fmaf_rn(c.fz,                                                                      \
+              __fmaf_rn(c.fy, __fmaf_rn(c.fx, a111.f, __fmul_rn(wx0, a011.f)),           \
+                        __fmul_rn(wy0, __fmaf_rn(c.fx, a101.f, __fmul_rn(wx0, a001.f)))), \
+              __fmul_rn(wz0,                                                             \
+                        __fmaf_rn(c.fy, __fmaf_rn(c.fx, a110.f, __fmul_rn(wx0, a010.f)), \
+                                  __fmul_rn(wy0, __fmaf_rn(c.fx, a100.f, __fmul_rn(wx0, a000.f))))))
+    const float4 r = make_float4(SIPF_TRI(x), SIPF_TRI(y), SIPF_TRI(z), SIPF_TRI(w));
+#undef SIPF_TRI
+    return r;
+}
+
 // Periodic wrap into [0, H); a result that rounds to H becomes 0.
 __device__ __forceinline__ float wrap(float s, float Hf, int* bad) {
     if (s >= 0.0f && s < Hf) return s;
@@ -208,12 +225,8 @@ __global__ void __launch_bounds__(kNT, SIPF_STEP_MIN_BLOCKS)
            const Item* __restrict__ items, const int* __restrict__ n_items,
            unsigned long long* __restrict__ acc, int do_deposit, int do_move,
            int* __restrict__ status) {
-#if SIPF_DEP64
-    __shared__ unsigned long long dep64[kBlock];   // node sums
-#else
-    __shared__ unsigned dep_lo[kBlock];     // node sums of the low / high 16 bits
-    __shared__ unsigned dep_hi[kBlock];
-#endif
+    __shared__ unsigned dep[kBlock];        // node sums of the item (exact: < 2^31)
+    __shared__ float4 gblk[kBlock];         // (dv/dx, dv/dy, dv/dz, w) on the tile's 9^3 nodes
     __shared__ Staged st;
     __shared__ int nb_cnt[27];
     __shared__ int nb_base[27];
@@ -226,18 +239,21 @@ __global__ void __launch_bounds__(kNT, SIPF_STEP_MIN_BLOCKS)
     const int total = *n_items;
     // items are assigned statically: block b takes items b, b + grid, ...
     for (int item_idx = blockIdx.x; item_idx < total; item_idx += gridDim.x) {
-        for (int i = threadIdx.x; i < kBlock; i += kNT) {
-#if SIPF_DEP64
-            dep64[i] = 0ull;
-#else
-            dep_lo[i] = 0u;
-            dep_hi[i] = 0u;
-#endif
-        }
+        for (int i = threadIdx.x; i < kBlock; i += kNT) dep[i] = 0u;
         const Item it = items[item_idx];
         const int tile = it.tile;
         const int ttx = it.tx, tty = it.ty, ttz = it.tz;
         const int tx0 = ttx * 8, ty0 = tty * 8, tz0 = ttz * 8;
+        if (do_move && a.push && tile >= 0) {
+            // the tile's node block of the gather array (periodic), 9 float4 per row
+            for (int q = threadIdx.x; q < kBlock; q += kNT) {
+                const int lx = q % 9, ly = (q / 9) % 9, lz = q / 81;
+                const int nx = tx0 + lx < H ? tx0 + lx : tx0 + lx - H;
+                const int ny = ty0 + ly < H ? ty0 + ly : ty0 + ly - H;
+                const int nz = tz0 + lz < H ? tz0 + lz : tz0 + lz - H;
+                gblk[q] = __ldg(G + (nz * H + ny) * H + nx);
+            }
+        }
         if (threadIdx.x < 27) {
             const int k = threadIdx.x;
             nb_cnt[k] = 0;
@@ -268,7 +284,7 @@ __global__ void __launch_bounds__(kNT, SIPF_STEP_MIN_BLOCKS)
             const Cell c = locate(px, py, pz, H);
 
             if (do_deposit && valid) {
-                // a_p R_h(X_p, node) h^3 in units of exp(logref) 2^-S, as uint32 (< 2^31)
+                // a_p R_h(X_p, node) h^3 in units of exp(logref) 2^-S, as uint32 (< 2^21)
                 const float ea = __fmul_rn(expf(d2f_bits(pl)), d.scale);
                 const float wx0 = __fsub_rn(1.0f, c.fx), wy0 = __fsub_rn(1.0f, c.fy);
                 const float e0 = __fmul_rn(ea, __fsub_rn(1.0f, c.fz)), e1 = __fmul_rn(ea, c.fz);
@@ -285,20 +301,13 @@ __global__ void __launch_bounds__(kNT, SIPF_STEP_MIN_BLOCKS)
                 if (tile >= 0 && !in_tile) bad |= 2;   // bucket does not match position
                 if (in_tile) {
                     // particles of a bucket are in random cells of the tile, so lanes
-                    // rarely collide: one shared atomic per corner
+                    // rarely collide: one shared 32-bit atomic per corner (an item has at
+                    // most kItem particles and each value is < 2^21, so sums are exact)
                     const int nbase = (lz * 9 + ly) * 9 + lx;
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
                         const int node = nbase + (k & 1) + ((k >> 1) & 1) * 9 + (k >> 2) * 81;
-#if SIPF_DEP64
-                        if (q[k]) atomicAdd(dep64 + node, static_cast<unsigned long long>(q[k]));
-#else
-                        // 16-bit halves keep the 32-bit sums of an item exact
-                        if (q[k]) {
-                            atomicAdd(dep_lo + node, q[k] & 0xFFFFu);
-                            atomicAdd(dep_hi + node, q[k] >> 16);
-                        }
-#endif
+                        if (q[k]) atomicAdd(dep + node, q[k]);
                     }
                 } else {
                     const int x1 = c.cx + 1 < H ? c.cx + 1 : 0;
@@ -317,7 +326,10 @@ __global__ void __launch_bounds__(kNT, SIPF_STEP_MIN_BLOCKS)
 
             if (do_move) {
                 if (a.push && valid) {
-                    const float4 g = gather4(G, c, H);
+                    const int lx = c.cx - tx0, ly = c.cy - ty0, lz = c.cz - tz0;
+                    const bool in_tile = tile >= 0 && ((lx | ly | lz) & ~7) == 0;
+                    const float4 g = in_tile ? gather4_block(gblk, c, (lz * 9 + ly) * 9 + lx)
+                                             : gather4(G, c, H);
                     // mass factor 1 + tau (rho(w_H) - 1), rho(w) = 2w/(1+w) (Eq. u_hat_update)
                     const float rho = __fdiv_rn(2.0f * g.w, __fadd_rn(1.0f, g.w));
                     const float inc = log1pf(__fmul_rn(a.tau, __fsub_rn(rho, 1.0f)));
@@ -406,12 +418,7 @@ __global__ void __launch_bounds__(kNT, SIPF_STEP_MIN_BLOCKS)
         if (do_deposit && tile >= 0) {
             // flush the tile's node block into the grid accumulator
             for (int j = threadIdx.x; j < kBlock; j += kNT) {
-#if SIPF_DEP64
-                const unsigned long long v = dep64[j];
-#else
-                const unsigned long long v =
-                    (static_cast<unsigned long long>(dep_hi[j]) << 16) + dep_lo[j];
-#endif
+                const unsigned long long v = dep[j];
                 if (v) {
                     const int lx = j % 9, ly = (j / 9) % 9, lz = j / 81;
                     const int nx = (tx0 + lx) % H, ny = (ty0 + ly) % H, nz = (tz0 + lz) % H;

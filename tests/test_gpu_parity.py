@@ -169,7 +169,9 @@ def test_deposit_matches_oracle_and_conserves_mass(name, H, N):
     assert u.min() >= 0.0
     h3 = (wl.L / wl.H) ** 3
     assert abs(u.astype(np.float64).sum() * h3 - wl.mass.sum()) <= 1e-6 * wl.mass.sum()
-    assert abs(d["mass_grid"] - wl.mass.sum()) <= 1e-9 * wl.mass.sum()
+    # each corner value is rounded to one fixed-point unit, a particle being
+    # ~2^19.5 units: relative noise of the total ~ sqrt(8/12) 2^-19.5 / sqrt(N)
+    assert abs(d["mass_grid"] - wl.mass.sum()) <= 6e-6 / np.sqrt(wl.N) * wl.mass.sum()
     assert abs(d["mass_particles"] - wl.mass.sum()) <= 1e-12 * wl.mass.sum()
 
 
