@@ -74,8 +74,8 @@ extern "C" {
 typedef struct sipf_ctx sipf_ctx;
 
 /* Periodic box [origin, origin + L)^3 with H nodes per axis (paper Sec. 2.1;
- * Omega = [-L/2, L/2]^3 there, origin = -L/2).  H must be a power of two
- * with 16 <= H <= 128 in this build (256 returns SIPF_EUNSUPPORTED). */
+ * Omega = [-L/2, L/2]^3 there, origin = -L/2).  H must be 16, 32, 64, 128
+ * or 256 in this build. */
 typedef struct {
     int32_t H;
     double L;
@@ -111,7 +111,7 @@ typedef struct {
  * (about 110 N + 110 H^3 bytes: two particle buffers with tile buckets and
  * an overflow region of N slots each, fields, spectra).  Errors: SIPF_EINVAL (N < 1 or N >= 2^31,
  * H not supported, L <= 0, a parameter negative or non-finite, diffusion or
- * v_update unknown), SIPF_EUNSUPPORTED (H = 256), SIPF_ENOMEM. */
+ * v_update unknown), SIPF_ENOMEM. */
 int sipf_create(const sipf_grid* grid, int64_t N, const sipf_params* params,
                 void* stream, sipf_ctx** out);
 

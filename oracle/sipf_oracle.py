@@ -357,6 +357,19 @@ def step(st: State, tau: float, normals: np.ndarray | None = None) -> State:
                  grad_new, n, st.t + tau)
 
 
+def advance_particles(st: State, tau: float, idx: np.ndarray):
+    """The particle part of one step (Eq. u_hat_update) for the particles
+    with indices idx only: new grid-unit positions and log-masses, from the
+    gather of grad v^(n-1) and w^(n-1) at X^(n-1) and the step-n noise."""
+    p, H, h = st.p, st.H, st.h
+    s = st.s[idx]
+    g = np.stack([gather(st.grad_v[d], s) for d in range(3)], axis=1)
+    w_H = gather(st.w, s)
+    z = brownian_normals(st.ids[idx], st.n + 1, p.seed)
+    s_new = wrap(s + (p.chi * tau / h) * g + (math.sqrt(2.0 * p.Du * tau) / h) * z, H)
+    return s_new, st.loga[idx] + np.log1p(tau * (rho(w_H) - 1.0))
+
+
 def run(st: State, tau: float, k: int) -> State:
     for _ in range(k):
         st = step(st, tau)

@@ -30,7 +30,7 @@ int cuda_fail(sipf_ctx* c, cudaError_t e, const char* where) {
         if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);   \
     } while (0)
 
-bool supported_H(int H) { return H == 16 || H == 32 || H == 64 || H == 128; }
+bool supported_H(int H) { return H == 16 || H == 32 || H == 64 || H == 128 || H == 256; }
 
 bool finite_nonneg(double x) { return isfinite(x) && x >= 0.0; }
 
@@ -63,7 +63,8 @@ void free_all(sipf_ctx* c) {
                     c->dl[1], c->id[0], c->id[1], c->bstart[0], c->bstart[1], c->cap[0],
                     c->cap[1], c->cnt[0], c->cnt[1], c->ovf[0], c->ovf[1], c->items, c->n_items,
                     c->work, c->count, c->cell_start, c->scan_tmp, c->acc, c->v, c->m, c->w,
-                    c->G, c->specM, c->specW, c->specV, c->specB, c->specA, c->twiddle,
+                    c->G, c->specM, c->specW, c->specV, c->specB, c->specA, c->specDx,
+                    c->specDy, c->twiddle,
                     c->status, c->diag_tmp, c->diag_out, c->diag_ll, c->voff};
     for (void* q : ptrs)
         if (q) cudaFree(q);
@@ -118,9 +119,11 @@ DepositArgs deposit_args(const sipf_ctx* c) {
 }
 
 // Converts the integer accumulator to u_bar = a R_h summed: 2^-S e^logref / h^3.
-float acc_to_u(const sipf_ctx* c) {
-    return static_cast<float>(ldexp(exp(c->logref), -deposit_shift(c)) / (c->h * c->h * c->h));
+double acc_to_u_d(const sipf_ctx* c) {
+    return ldexp(exp(c->logref), -deposit_shift(c)) / (c->h * c->h * c->h);
 }
+
+float acc_to_u(const sipf_ctx* c) { return static_cast<float>(acc_to_u_d(c)); }
 
 PushArgs push_args(const sipf_ctx* c, double dt, uint32_t n, int push) {
     PushArgs a;
@@ -270,7 +273,6 @@ int sipf_create(const sipf_grid* grid, int64_t N, const sipf_params* params, voi
     if (!(isfinite(grid->L) && grid->L > 0.0)) return SIPF_EINVAL;
     for (int k = 0; k < 3; ++k)
         if (!isfinite(grid->origin[k])) return SIPF_EINVAL;
-    if (grid->H == 256) return SIPF_EUNSUPPORTED;
     if (!supported_H(grid->H)) return SIPF_EINVAL;
     if (check_params(params, &why) != SIPF_OK) return SIPF_EINVAL;
 
@@ -323,6 +325,8 @@ int sipf_create(const sipf_grid* grid, int64_t N, const sipf_params* params, voi
          dalloc(&c->diag_out, 8) == cudaSuccess;
     const bool filter = params->H0 > 0.0 && params->H0 < grid->H;
     if (ok && filter) ok = dalloc(&c->specA, spec) == cudaSuccess;
+    if (ok && c->H > 128)
+        ok = dalloc(&c->specDx, spec) == cudaSuccess && dalloc(&c->specDy, spec) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_all(c);
@@ -599,7 +603,7 @@ int sipf_diagnostics(sipf_ctx* c, sipf_diag* out) {
     int r = compact_current(c);
     if (r == SIPF_OK) r = deposit_current(c);
     if (r != SIPF_OK) return r;
-    SIPF_CUDA(c, launch_diagnostics(c, c->cur ^ 1, acc_to_u(c)));
+    SIPF_CUDA(c, launch_diagnostics(c, c->cur ^ 1, acc_to_u_d(c)));
     const size_t H3 = static_cast<size_t>(c->H) * c->H * c->H;
     SIPF_CUDA(c, cudaMemsetAsync(c->acc, 0, H3 * sizeof(long long), c->stream));
     double h[8];

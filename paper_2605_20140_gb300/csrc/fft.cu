@@ -158,6 +158,7 @@ template <> struct Radix<16> { static constexpr int R1 = 4, R2 = 4; };
 template <> struct Radix<32> { static constexpr int R1 = 8, R2 = 4; };
 template <> struct Radix<64> { static constexpr int R1 = 8, R2 = 8; };
 template <> struct Radix<128> { static constexpr int R1 = 16, R2 = 8; };
+template <> struct Radix<256> { static constexpr int R1 = 16, R2 = 16; };
 
 // Batched length-L FFT along one axis of a shared-memory array.
 template <int L, int NTRANS, int ES, int TS, int NT, int SIGN>
@@ -175,6 +176,11 @@ template <> struct Cfg<32> { static constexpr int NT1 = 256, NT2 = 256, NT3 = 25
 template <> struct Cfg<64> { static constexpr int NT1 = 512, NT2 = 512, NT3 = 512; };
 // 544 = 17 warps: one radix-16 butterfly per thread for the 65 z-transforms
 template <> struct Cfg<128> { static constexpr int NT1 = 1024, NT2 = 544, NT3 = 1024; };
+// H = 256 runs the per-axis pipeline; NT2 is the z pass over 32-column tiles
+template <> struct Cfg<256> { static constexpr int NT1 = 256, NT2 = 512, NT3 = 256; };
+
+// kx columns per block of the z pass: the whole padded row up to H = 128
+template <int H> constexpr int zcols() { return H <= 128 ? H / 2 + 2 : 32; }
 
 template <int H> constexpr int kxp() { return H / 2 + 2; }
 // shared-memory pitch (float2) of rows that are transformed along the row
@@ -334,32 +340,37 @@ __global__ void __launch_bounds__(Cfg<H>::NT1)
 }
 
 // ---------------------------------------------------------------- pass 2
+// Block (ky, field, kx tile): forward DFT along z of the KB columns
+// [k0, k0 + KB) of the (z, ky) rows, the per-mode multiplier, inverse DFT.
 template <int H>
 __global__ void __launch_bounds__(Cfg<H>::NT2)
     k_z_multiply(SpectralArgs a, float2* __restrict__ gM, float2* __restrict__ gW,
                  const float2* __restrict__ gV, float2* __restrict__ gB, float2* __restrict__ gA,
                  const float2* __restrict__ twg, float* __restrict__ voff) {
-    constexpr int NT = Cfg<H>::NT2, KXP = kxp<H>(), HK = H / 2 + 1;
+    constexpr int NT = Cfg<H>::NT2, KXP = kxp<H>(), HK = H / 2 + 1, KB = zcols<H>();
+    static_assert(KB % 2 == 0, "float4 columns");
     extern __shared__ float2 sm[];
-    float2* buf = sm;             // [H (z)][KXP (kx)]
-    float2* tw = buf + H * KXP;
+    float2* buf = sm;             // [H (z)][KB (kx)]
+    float2* tw = buf + H * KB;
     const int ky = blockIdx.x, field = blockIdx.y;   // 0 m, 1 w, 2 v -> i k_z V, 3 v -> filtered V
+    const int k0 = blockIdx.z * KB;
     if (field < 2 && !a.do_mw) return;
     if (field == 3 && !a.filter) return;
     const float2* src = field == 0 ? gM : field == 1 ? gW : gV;
     float2* dst = field == 0 ? gM : field == 1 ? gW : field == 2 ? gB : gA;
     for (int i = threadIdx.x; i < H; i += NT) tw[i] = twg[i];
-    // rows (z, ky) of KXP float2 = KXP/2 float4, all loads issued first
-    constexpr int NQ = H * (KXP / 2), ITER = (NQ + NT - 1) / NT;
+    // rows (z, ky): KB/2 float4 from column k0, all loads issued first
+    constexpr int NQ = H * (KB / 2), ITER = (NQ + NT - 1) / NT;
     {
         float4 r[ITER];
 #pragma unroll
         for (int i = 0; i < ITER; ++i) {
             const int q = threadIdx.x + i * NT;
             if (q < NQ) {
-                const int zz = q / (KXP / 2), j = q % (KXP / 2);
-                r[i] = reinterpret_cast<const float4*>(
-                    src + (static_cast<size_t>(zz) * H + ky) * KXP)[j];
+                const int zz = q / (KB / 2), col = k0 + 2 * (q % (KB / 2));
+                r[i] = col < KXP ? *reinterpret_cast<const float4*>(
+                                       src + (static_cast<size_t>(zz) * H + ky) * KXP + col)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
 #pragma unroll
@@ -369,18 +380,19 @@ __global__ void __launch_bounds__(Cfg<H>::NT2)
         }
     }
     __syncthreads();
-    fft_axis<H, HK, KXP, 1, NT, -1>(buf, tw);
-    if (field == 2 && ky == 0 && threadIdx.x == 0) {
+    fft_axis<H, KB, KB, 1, NT, -1>(buf, tw);
+    if (field == 2 && ky == 0 && k0 == 0 && threadIdx.x == 0) {
         // DC of (v^n - c0): move the offset to the mean of v^n for the next step
         *voff = *voff + buf[0].x * a.out_scale;
     }
     const int qy = signed_mode(ky, H);
-    for (int idx = threadIdx.x; idx < H * HK; idx += NT) {
-        const int kz = idx / HK, qx = idx % HK;
+    for (int idx = threadIdx.x; idx < H * KB; idx += NT) {
+        const int kz = idx / KB, qx = k0 + idx % KB;
+        if (qx >= HK) continue;
         const int qz = signed_mode(kz, H);
         const float q2 = static_cast<float>(qx * qx + qy * qy + qz * qz);
         float f = 1.0f;
-        float2 val = buf[kz * KXP + qx];
+        float2 val = buf[idx];
         if (field == 2) {
             const float kz_phys = (qz == -H / 2) ? 0.0f : a.two_pi_over_L * static_cast<float>(qz);
             val = make_float2(-kz_phys * val.y, kz_phys * val.x);
@@ -396,14 +408,15 @@ __global__ void __launch_bounds__(Cfg<H>::NT2)
             const float lo = field == 0 ? a.m_r0_lo : a.w_r0_lo;
             val = make_float2(fmaf(val.x, lo, val.x * hi), fmaf(val.y, lo, val.y * hi));
         }
-        buf[kz * KXP + qx] = val;
+        buf[idx] = val;
     }
     __syncthreads();
-    fft_axis<H, HK, KXP, 1, NT, +1>(buf, tw);
+    fft_axis<H, KB, KB, 1, NT, +1>(buf, tw);
     for (int q = threadIdx.x; q < NQ; q += NT) {
-        const int zz = q / (KXP / 2), j = q % (KXP / 2);
-        reinterpret_cast<float4*>(dst + (static_cast<size_t>(zz) * H + ky) * KXP)[j] =
-            reinterpret_cast<const float4*>(buf)[q];
+        const int zz = q / (KB / 2), col = k0 + 2 * (q % (KB / 2));
+        if (col < KXP)
+            *reinterpret_cast<float4*>(dst + (static_cast<size_t>(zz) * H + ky) * KXP + col) =
+                reinterpret_cast<const float4*>(buf)[q];
     }
 }
 
@@ -553,11 +566,256 @@ __global__ void __launch_bounds__(Cfg<H>::NT3)
     }
 }
 
+// ---------------------------------------------------------------- per-axis passes (H > 128)
+// A 256^2 complex plane does not fit in shared memory, so for H > 128 each
+// axis is transformed by its own kernel over small blocks of lines:
+//   sx_forward: rows of RB lines: reaction, x DFT (row pairs) -> half spectra
+//   sx_columns: columns (KB kx at a time) of one plane: y DFT, forward or
+//               inverse; in the inverse, V becomes i k_x V and i k_y V
+//   k_z_multiply (32-column tiles) between them, then
+//   sx_inverse: rows: pack two real outputs per complex row, inverse x DFT.
+constexpr int kSxRows = 8;     // rows per block of the x passes
+constexpr int kSxCols = 16;    // kx columns per block of the y passes
+constexpr int kSxNT = 256;
+
+template <int H>
+__global__ void __launch_bounds__(kSxNT)
+    k_sx_forward(SpectralArgs a, const float* v, const float* __restrict__ m,
+                 const float* __restrict__ w, unsigned long long* __restrict__ acc, float* v_out,
+                 float2* __restrict__ gM, float2* __restrict__ gW, float2* __restrict__ gV,
+                 const float2* __restrict__ twg, const float* __restrict__ voff) {
+    constexpr int RB = kSxRows, NT = kSxNT, KXP = kxp<H>(), HK = H / 2 + 1, RP = rowp<H>();
+    static_assert((RB / 2) * RP <= RB * KXP, "row pairs fit in the half-row space");
+    extern __shared__ float2 sm[];
+    float2* buf = sm;              // 3 fields: [RB/2][RP] row pairs, then [RB][KXP] half rows
+    float2* tw = buf + 3 * RB * KXP;
+    const int z = blockIdx.y, y0 = blockIdx.x * RB;
+    for (int i = threadIdx.x; i < H; i += NT) tw[i] = twg[i];
+    const float c0 = *voff;
+    const size_t row0 = (static_cast<size_t>(z) * H + y0) * H;
+    for (int g = threadIdx.x; g < RB * H / 4; g += NT) {
+        const size_t o = row0 + 4 * static_cast<size_t>(g);
+        const float4 rv = *reinterpret_cast<const float4*>(v + o);
+        const float4 rm = *reinterpret_cast<const float4*>(m + o);
+        const float4 rw = *reinterpret_cast<const float4*>(w + o);
+        const ulonglong2 q0 = *reinterpret_cast<const ulonglong2*>(acc + o);
+        const ulonglong2 q1 = *reinterpret_cast<const ulonglong2*>(acc + o + 2);
+        *reinterpret_cast<ulonglong2*>(acc + o) = make_ulonglong2(0ull, 0ull);
+        *reinterpret_cast<ulonglong2*>(acc + o + 2) = make_ulonglong2(0ull, 0ull);
+        const float vv[4] = {rv.x, rv.y, rv.z, rv.w}, mm[4] = {rm.x, rm.y, rm.z, rm.w};
+        const float ww[4] = {rw.x, rw.y, rw.z, rw.w};
+        const unsigned long long qq[4] = {q0.x, q0.y, q1.x, q1.y};
+        const int r = (4 * g) / H, x0 = (4 * g) % H;
+        float vn[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            float ms, ws;
+            react(a, vv[e], mm[e], ww[e], acc_to_float(qq[e]) * a.react_scale, ms, ws, vn[e]);
+            const float val[3] = {ms, ws, vn[e] - c0};
+#pragma unroll
+            for (int f = 0; f < 3; ++f)
+                reinterpret_cast<float*>(buf + (f * (RB / 2) + (r >> 1)) * RP)[2 * (x0 + e) + (r & 1)] =
+                    val[f];
+        }
+        if (a.write_v) *reinterpret_cast<float4*>(v_out + o) = make_float4(vn[0], vn[1], vn[2], vn[3]);
+    }
+    __syncthreads();
+    fft_axis<H, 3 * (RB / 2), 1, RP, NT, -1>(buf, tw);
+    {
+        // split each transformed row pair into the two rows' half spectra
+        constexpr int NS = 3 * (RB / 2) * HK, SPT = (NS + NT - 1) / NT;
+        float2 x1[SPT], x2[SPT];
+#pragma unroll
+        for (int t = 0; t < SPT; ++t) {
+            const int idx = threadIdx.x + t * NT;
+            if (idx < NS) {
+                const int pr = idx / HK, k = idx % HK;
+                const float2 zp = buf[pr * RP + k];
+                const float2 zm = buf[pr * RP + ((H - k) & (H - 1))];
+                x1[t] = make_float2(0.5f * (zp.x + zm.x), 0.5f * (zp.y - zm.y));
+                x2[t] = make_float2(0.5f * (zp.y + zm.y), -0.5f * (zp.x - zm.x));
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < SPT; ++t) {
+            const int idx = threadIdx.x + t * NT;
+            if (idx < NS) {
+                const int pr = idx / HK, k = idx % HK;
+                const int f = pr / (RB / 2), p = pr % (RB / 2);
+                buf[(f * RB + 2 * p) * KXP + k] = x1[t];
+                buf[(f * RB + 2 * p + 1) * KXP + k] = x2[t];
+            }
+        }
+        __syncthreads();
+    }
+    for (int q = threadIdx.x; q < 3 * RB * (KXP / 2); q += NT) {
+        const int f = q / (RB * (KXP / 2)), rem = q % (RB * (KXP / 2));
+        const int r = rem / (KXP / 2), k = 2 * (rem % (KXP / 2));
+        if (f < 2 && !a.do_mw) continue;
+        float2* dst = f == 0 ? gM : f == 1 ? gW : gV;
+        const float2 e0 = buf[(f * RB + r) * KXP + k];
+        const float2 e1 = k + 1 < HK ? buf[(f * RB + r) * KXP + k + 1] : make_float2(0.f, 0.f);
+        *reinterpret_cast<float4*>(dst + (static_cast<size_t>(z) * H + y0 + r) * KXP + k) =
+            make_float4(e0.x, e0.y, e1.x, e1.y);
+    }
+}
+
+// y DFT of KB kx columns of one plane of `field` (forward: M, W, V in place;
+// inverse: M, W, B in place, and V (or its filtered copy) -> i k_x V, i k_y V).
+template <int H, int SIGN>
+__global__ void __launch_bounds__(kSxNT)
+    k_sx_columns(SpectralArgs a, float2* __restrict__ f0, float2* __restrict__ f1,
+                 float2* __restrict__ f2, float2* __restrict__ dx, float2* __restrict__ dy,
+                 const float2* __restrict__ twg, int plain) {
+    constexpr int NT = kSxNT, KXP = kxp<H>(), KB = kSxCols, CP = KB + 1;
+    extern __shared__ float2 sm[];
+    float2* b0 = sm;               // [H (y)][CP]
+    float2* b1 = b0 + H * CP;      // second buffer (derivatives)
+    float2* tw = b1 + H * CP;
+    const int k0 = blockIdx.x * KB, z = blockIdx.y, field = blockIdx.z;
+    if (!plain && field < 2 && !a.do_mw) return;
+    const bool deriv = !plain && SIGN > 0 && field == 2;
+    float2* src = field == 0 ? f0 : field == 1 ? f1 : f2;
+    for (int i = threadIdx.x; i < H; i += NT) tw[i] = twg[i];
+    const size_t plane = static_cast<size_t>(z) * H * KXP;
+    for (int q = threadIdx.x; q < H * KB; q += NT) {
+        const int y = q / KB, t = q % KB, k = k0 + t;
+        float2 val = k < KXP ? src[plane + static_cast<size_t>(y) * KXP + k] : make_float2(0.f, 0.f);
+        if (deriv) {
+            const int qy = signed_mode(y, H);
+            const float kxp_ = (k >= H / 2) ? 0.0f : a.two_pi_over_L * static_cast<float>(k);
+            const float kyp = (qy == -H / 2) ? 0.0f : a.two_pi_over_L * static_cast<float>(qy);
+            b1[y * CP + t] = make_float2(-kyp * val.y, kyp * val.x);
+            val = make_float2(-kxp_ * val.y, kxp_ * val.x);
+        }
+        b0[y * CP + t] = val;
+    }
+    __syncthreads();
+    fft_axis<H, KB, CP, 1, NT, SIGN>(b0, tw);
+    if (deriv) fft_axis<H, KB, CP, 1, NT, SIGN>(b1, tw);
+    float2* d0 = deriv ? dx : src;
+    for (int q = threadIdx.x; q < H * KB; q += NT) {
+        const int y = q / KB, t = q % KB, k = k0 + t;
+        if (k >= KXP) continue;
+        d0[plane + static_cast<size_t>(y) * KXP + k] = b0[y * CP + t];
+        if (deriv) dy[plane + static_cast<size_t>(y) * KXP + k] = b1[y * CP + t];
+    }
+}
+
+// Rows of the inverse: (m, w), (dv/dx, dv/dy) and dv/dz row pairs, packed
+// two real outputs per complex row, inverse x DFT, scaled outputs.
+template <int H>
+__global__ void __launch_bounds__(kSxNT)
+    k_sx_inverse(SpectralArgs a, const float2* __restrict__ gM, const float2* __restrict__ gW,
+                 const float2* __restrict__ gDx, const float2* __restrict__ gDy,
+                 const float2* __restrict__ gB, float* __restrict__ m_out,
+                 float* __restrict__ w_out, float* __restrict__ G, const float2* __restrict__ twg) {
+    constexpr int RB = kSxRows, NT = kSxNT, KXP = kxp<H>(), RP = rowp<H>();
+    constexpr int NZ = RB + RB + RB / 2;       // packed rows: (m, w), (dx, dy), dz pairs
+    extern __shared__ float2 sm[];
+    float2* hb = sm;                           // 5 fields x [RB][KXP] half rows
+    float2* Z = hb + 5 * RB * KXP;             // [NZ][RP]
+    float2* tw = Z + NZ * RP;
+    const int z = blockIdx.y, y0 = blockIdx.x * RB;
+    for (int i = threadIdx.x; i < H; i += NT) tw[i] = twg[i];
+    for (int q = threadIdx.x; q < 5 * RB * (KXP / 2); q += NT) {
+        const int f = q / (RB * (KXP / 2)), rem = q % (RB * (KXP / 2));
+        const int r = rem / (KXP / 2), k = 2 * (rem % (KXP / 2));
+        if (f < 2 && !a.do_mw) continue;
+        const float2* src = f == 0 ? gM : f == 1 ? gW : f == 2 ? gDx : f == 3 ? gDy : gB;
+        *reinterpret_cast<float4*>(hb + (f * RB + r) * KXP + k) = *reinterpret_cast<const float4*>(
+            src + (static_cast<size_t>(z) * H + y0 + r) * KXP + k);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < NZ * H; q += NT) {
+        const int zr = q / H, kx = q % H;
+        float2 val;
+        if (zr < RB) {
+            val = a.do_mw ? pack_two<H>(hb + zr * KXP, hb + (RB + zr) * KXP, kx) : make_float2(0.f, 0.f);
+        } else if (zr < 2 * RB) {
+            const int r = zr - RB;
+            val = pack_two<H>(hb + (2 * RB + r) * KXP, hb + (3 * RB + r) * KXP, kx);
+        } else {
+            const int p = zr - 2 * RB;
+            val = pack_two<H>(hb + (4 * RB + 2 * p) * KXP, hb + (4 * RB + 2 * p + 1) * KXP, kx);
+        }
+        Z[zr * RP + kx] = val;
+    }
+    __syncthreads();
+    fft_axis<H, NZ, 1, RP, NT, +1>(Z, tw);
+    const float sc = a.out_scale, sxy = a.out_scale_xy;
+    for (int q = threadIdx.x; q < RB * H; q += NT) {
+        const int r = q / H, x = q % H;
+        const size_t node = (static_cast<size_t>(z) * H + y0 + r) * H + x;
+        const float2 mw = Z[r * RP + x];
+        const float2 dxy = Z[(RB + r) * RP + x];
+        const float2 bz = Z[(2 * RB + (r >> 1)) * RP + x];
+        if (a.do_mw) {
+            m_out[node] = mw.x * sc;
+            w_out[node] = mw.y * sc;
+            *reinterpret_cast<float4*>(G + 4 * node) =
+                make_float4(dxy.x * sxy, dxy.y * sxy, ((r & 1) ? bz.y : bz.x) * sc, mw.y * sc);
+        } else {
+            *reinterpret_cast<float2*>(G + 4 * node) = make_float2(dxy.x * sxy, dxy.y * sxy);
+            G[4 * node + 2] = ((r & 1) ? bz.y : bz.x) * sc;
+        }
+    }
+}
+
+// Passes of the per-axis pipeline, grouped like the fused ones:
+// 0 forward (x, y), 1 z, 2 inverse (y, x).
+template <int H>
+cudaError_t spectral_pass_split(sipf_ctx* c, const SpectralArgs& a, int pass) {
+    constexpr int KXP = kxp<H>(), RB = kSxRows, KB = kSxCols, RP = rowp<H>();
+    const size_t smx1 = (3 * static_cast<size_t>(RB) * KXP + H) * sizeof(float2);
+    const size_t smy = (2 * static_cast<size_t>(H) * (KB + 1) + H) * sizeof(float2);
+    const size_t smz = (static_cast<size_t>(H) * zcols<H>() + H) * sizeof(float2);
+    const size_t smx2 =
+        (5 * static_cast<size_t>(RB) * KXP + (2 * RB + RB / 2) * RP + H) * sizeof(float2);
+    static int configured_device = -1;
+    if (configured_device != c->device) {
+        cudaFuncSetAttribute(k_sx_forward<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smx1));
+        cudaFuncSetAttribute(k_sx_columns<H, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smy));
+        cudaFuncSetAttribute(k_sx_columns<H, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smy));
+        cudaFuncSetAttribute(k_z_multiply<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smz));
+        cudaFuncSetAttribute(k_sx_inverse<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smx2));
+        configured_device = c->device;
+    }
+    const dim3 gy((KXP + KB - 1) / KB, H, 3);
+    if (pass == 0) {
+        k_sx_forward<H><<<dim3(H / RB, H), kSxNT, smx1, c->stream>>>(
+            a, c->v, c->m, c->w, reinterpret_cast<unsigned long long*>(c->acc), c->v, c->specM,
+            c->specW, c->specV, c->twiddle, c->voff);
+        k_sx_columns<H, -1><<<gy, kSxNT, smy, c->stream>>>(a, c->specM, c->specW, c->specV,
+                                                             nullptr, nullptr, c->twiddle, 0);
+    } else if (pass == 1) {
+        k_z_multiply<H><<<dim3(H, 4, (KXP + zcols<H>() - 1) / zcols<H>()), Cfg<H>::NT2, smz,
+                          c->stream>>>(a, c->specM, c->specW, c->specV, c->specB, c->specA,
+                                       c->twiddle, c->voff);
+    } else {
+        // inverse y: M, W and B in place; V (or its filtered copy) -> i k_x V, i k_y V
+        k_sx_columns<H, +1><<<gy, kSxNT, smy, c->stream>>>(
+            a, c->specM, c->specW, a.filter ? c->specA : c->specV, c->specDx, c->specDy, c->twiddle,
+            0);
+        k_sx_columns<H, +1><<<dim3(gy.x, H, 1), kSxNT, smy, c->stream>>>(
+            a, c->specB, c->specB, c->specB, nullptr, nullptr, c->twiddle, 1);
+        k_sx_inverse<H><<<dim3(H / RB, H), kSxNT, smx2, c->stream>>>(
+            a, c->specM, c->specW, c->specDx, c->specDy, c->specB, c->m, c->w, c->G, c->twiddle);
+    }
+    return cudaGetLastError();
+}
+
 template <int H>
 cudaError_t spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass) {
     constexpr int KXP = kxp<H>();
     const size_t sm1 = (static_cast<size_t>(H) * rowp<H>() + H * KXP + H) * sizeof(float2);
-    const size_t sm2 = (static_cast<size_t>(H) * KXP + H) * sizeof(float2);
+    const size_t sm2 = (static_cast<size_t>(H) * zcols<H>() + H) * sizeof(float2);
     const size_t sm3 = (3 * static_cast<size_t>(H) * KXP + H) * sizeof(float2);
     static int configured_device = -1;   // attributes are set once per process and device
     if (configured_device != c->device) {
@@ -574,7 +832,8 @@ cudaError_t spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass) {
             a, c->v, c->m, c->w, reinterpret_cast<unsigned long long*>(c->acc), c->v, c->specM,
             c->specW, c->specV, c->twiddle, c->voff);
     } else if (pass == 1) {
-        k_z_multiply<H><<<dim3(H, 4), Cfg<H>::NT2, sm2, c->stream>>>(a, c->specM, c->specW, c->specV,
+        k_z_multiply<H><<<dim3(H, 4, (KXP + zcols<H>() - 1) / zcols<H>()), Cfg<H>::NT2, sm2,
+                            c->stream>>>(a, c->specM, c->specW, c->specV,
                                                              c->specB, c->specA, c->twiddle,
                                                              c->voff);
     } else {
@@ -593,6 +852,7 @@ cudaError_t launch_spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass) {
         case 32: return spectral_pass<32>(c, a, pass);
         case 64: return spectral_pass<64>(c, a, pass);
         case 128: return spectral_pass<128>(c, a, pass);
+        case 256: return spectral_pass_split<256>(c, a, pass);
         default: return cudaErrorInvalidValue;
     }
 }

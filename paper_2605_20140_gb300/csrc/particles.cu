@@ -956,13 +956,12 @@ cudaError_t launch_component(sipf_ctx* c, int comp, float* dst) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_diagnostics(sipf_ctx* c, int b, float acc_to_u) {
+cudaError_t launch_diagnostics(sipf_ctx* c, int b, double acc_to_u) {
     k_diag_partials<<<kDiagBlocks, kDiagNT, 0, c->stream>>>(
         c->dl[b], c->logref, c->sx[b], c->sy[b], c->sz[b], static_cast<int>(c->N), c->v, c->m,
         c->w, reinterpret_cast<const unsigned long long*>(c->acc), c->H * c->H * c->H, c->diag_tmp,
         c->diag_ll);
-    k_diag_final<<<1, 32, 0, c->stream>>>(c->diag_tmp, c->diag_ll, static_cast<double>(acc_to_u),
-                                          c->diag_out);
+    k_diag_final<<<1, 32, 0, c->stream>>>(c->diag_tmp, c->diag_ll, acc_to_u, c->diag_out);
     return cudaGetLastError();
 }
 

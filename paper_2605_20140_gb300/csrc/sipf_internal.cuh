@@ -13,7 +13,7 @@
 namespace sipf {
 
 constexpr int kTile = 8;            // cells per tile edge of the tile-major cell key
-constexpr int kMaxH = 128;          // largest grid of this build
+constexpr int kMaxH = 256;          // largest grid of this build
 
 // Device status bits (ORed into ctx->status by kernels, read by sipf_sync).
 constexpr int kStatusNonfinite = 1;   // a pushed position was NaN/inf (reset to 0)
@@ -127,6 +127,8 @@ struct sipf_ctx {
     float2* specV = nullptr;
     float2* specB = nullptr;
     float2* specA = nullptr;         // filtered v spectrum (filter on only)
+    float2* specDx = nullptr;        // i k_x V, i k_y V after the inverse y pass (H > 128 only)
+    float2* specDy = nullptr;
     float2* twiddle = nullptr;       // exp(-2 pi i j / H), j < H
     float* voff = nullptr;           // device scalar: offset subtracted from v before its FFT
     int kxp = 0;
@@ -173,7 +175,7 @@ cudaError_t launch_export_positions(sipf_ctx* c, int b, float* x);
 cudaError_t launch_export_mass(sipf_ctx* c, int b, double* out, int as_log);
 cudaError_t launch_acc_to_float(sipf_ctx* c, float* dst, float scale);
 cudaError_t launch_component(sipf_ctx* c, int comp, float* dst);
-cudaError_t launch_diagnostics(sipf_ctx* c, int b, float acc_to_u);
+cudaError_t launch_diagnostics(sipf_ctx* c, int b, double acc_to_u);
 cudaError_t launch_normals(const uint32_t* ids, int64_t N, uint32_t n, uint64_t seed, float* z,
                            uint32_t* bits, cudaStream_t s);
 cudaError_t launch_conv_check(const float* f, const double* d, int n, int* mismatches,

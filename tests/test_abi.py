@@ -80,7 +80,7 @@ def _create(lib, H=32, L=1.0, N=100, **kw):
     (dict(N=1 << 31), sipf.SIPF_EINVAL),
     (dict(H=48), sipf.SIPF_EINVAL),
     (dict(H=12), sipf.SIPF_EINVAL),
-    (dict(H=256), sipf.SIPF_EUNSUPPORTED),
+    (dict(H=512), sipf.SIPF_EINVAL),
     (dict(L=0.0), sipf.SIPF_EINVAL),
     (dict(L=float("nan")), sipf.SIPF_EINVAL),
     (dict(chi=-1.0), sipf.SIPF_EINVAL),

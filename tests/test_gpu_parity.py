@@ -4,7 +4,11 @@ Tolerances (float32 path against float64 oracle):
 * integer work -- Philox words, cell keys, cell offsets, per-cell particle
   sets -- bit-exact;
 * grid fields u_bar, v, m, w after up to 100 steps -- relative L2 <= 1e-5
-  (the target tolerance for the float32 path);
+  (the target tolerance for the float32 path).  Exception: u_bar on grids
+  with fewer particles than nodes, where a node sees one or two particles
+  and their float32 position rounding (up to H 2^-24 grid units per step,
+  growing like sqrt(n)) moves its trilinear weights directly; there the bound
+  is 4 sqrt(3) H 2^-24 sqrt(n) (see u_tolerance());
 * grad v -- the spectral derivative of v.  Each step rounds v^n to float32
   (relative 2^-24 per rounding, two roundings per step), and these
   independent errors accumulate like sqrt(n); differentiation multiplies
@@ -175,7 +179,7 @@ def test_deposit_matches_oracle_and_conserves_mass(name, H, N):
     assert abs(d["mass_particles"] - wl.mass.sum()) <= 1e-12 * wl.mass.sum()
 
 
-@pytest.mark.parametrize("H", [16, 32, 64, 128])
+@pytest.mark.parametrize("H", [16, 32, 64, 128, 256])
 def test_initial_spectral_gradient(H):
     wl = workload("small", H=H, N=1024)
     sim = run_gpu(wl, 0)
@@ -204,12 +208,12 @@ def test_gradient_of_a_sine_mode_closed_form():
         assert np.max(np.abs(f[name] - ref)) <= 1e-5 * np.abs(ref).max(), name
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_single_mode_decay(mode):
+@pytest.mark.parametrize("mode,H", [(0, 32), (1, 32), (0, 256)])
+def test_single_mode_decay(mode, H):
     """Massless particles, gamma = alpha = 0: one step multiplies a Fourier
     mode of m by 1/(1 + tau beta + tau Dm |k|^2) (or the exponential) and of
     w by 1/(1 + tau + tau Dw |k|^2)."""
-    H, L, tau = 32, 1.0, 0.01
+    L, tau = 1.0, 0.01
     p = Params(chi=0.0, Du=0.0, Dm=0.03, Dw=0.07, alpha=0.0, beta=0.4, gamma=0.0, diffusion=mode)
     q = np.arange(H) * (L / H)
     Z, Y, X = np.meshgrid(q, q, q, indexing="ij")
@@ -244,11 +248,20 @@ def grad_tolerance(st, axis, L):
     return max(FIELD_TOL, 4.0 * k_rms * dv_rms / g_rms)
 
 
+def u_tolerance(st, N):
+    """Relative L2 bound on u_bar: FIELD_TOL, or on sparse grids (N < H^3) the
+    effect of float32 position rounding on one particle's weights."""
+    if N >= st.H ** 3:
+        return FIELD_TOL
+    return max(FIELD_TOL, 4.0 * np.sqrt(3.0) * st.H * 2.0 ** -24 * np.sqrt(max(st.n, 1)))
+
+
 def _compare(sim, st, wl, field_tol=FIELD_TOL, pos_tol=1e-4, loga_tol=1e-6):
     f = sim.fields()
     ref = oracle_fields(st)
     errs = {k: rel_l2(f[k], ref[k]) for k in ref}
     tols = {k: field_tol for k in ("u", "v", "m", "w")}
+    tols["u"] = max(field_tol, u_tolerance(st, wl.N))
     for axis, k in enumerate(("gx", "gy", "gz")):
         tols[k] = grad_tolerance(st, axis, wl.L)
     s, loga, ids = sim.particle_state()
@@ -446,3 +459,43 @@ def test_integer_float_double_conversions_match_hardware():
     out = torch.zeros(2, dtype=torch.int32, device="cuda")
     sipf.sipf_check_conversions(fd, dd, m, out)
     assert out.cpu().tolist() == [0, 0]
+
+
+def test_two_steps_match_oracle_256_grid():
+    """The per-axis spectral pipeline (H = 256) against the oracle."""
+    wl = workload("headline", H=256, N=1 << 16)
+    sim = run_gpu(wl, 2)
+    st = O.run(oracle_state(wl), wl.dt, 2)
+    _compare(sim, st, wl)
+    sim.close()
+
+
+def test_largest_configuration_sampled():
+    """256^3 grid, 2^25 particles, chi = 0.02, dt = 2.5e-4: one step, checked
+    on a sample of particles the oracle advances one by one (gather of the
+    initial grad v and w, the step-1 Philox noise), plus invariants that hold
+    at any size: bucket integrity, deposited mass and the mass lemma."""
+    wl = workload("large")
+    sim = run_gpu(wl, 1)
+    s, loga, ids = sim.particle_state()
+    cs = sim.cell_start()
+    d = sim.diagnostics()
+    sim.close()
+    assert cs[-1] == wl.N and np.all(np.diff(cs) >= 0)
+    np.testing.assert_array_equal(np.sort(ids), np.arange(wl.N, dtype=np.uint32))
+    st = oracle_state(wl)
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(wl.N, 20000, replace=False))
+    s_ref, l_ref = O.advance_particles(st, wl.dt, idx)
+    order = np.argsort(ids)
+    s_got, l_got = s[order][idx], loga[order][idx]
+    assert np.abs(periodic_diff(s_got, s_ref, wl.H)).max() <= 1e-4
+    assert np.max(np.abs(l_got - l_ref)) <= 1e-6
+    M0 = wl.mass.sum()
+    # deposit masses are exp(log a - logref) in float32: particles with equal
+    # masses share one expf rounding (<= 2 ulp, correlated), plus the
+    # independent fixed-point rounding of each corner value (~6e-6/sqrt(N))
+    tol = 2.0 * 2.0 ** -23 + 6e-6 / np.sqrt(wl.N)
+    assert abs(d["mass_grid"] - d["mass_particles"]) <= tol * M0
+    assert M0 * (1 - wl.dt) <= d["mass_particles"] <= M0 * (1 + wl.dt)
+    assert d["nonfinite"] == 0 and d["min_u"] >= 0 and d["min_v"] > 0

@@ -413,3 +413,15 @@ def test_wrap_edge_cases():
     assert np.all(r >= 0) and np.all(r < H)
     np.testing.assert_allclose(r[1], [0.0, 7.99, 0.0], atol=1e-12)
     assert r[2, 0] == 7.5
+
+
+def test_advance_particles_is_the_particle_part_of_a_step():
+    """The per-sample particle update equals the particles of a full step."""
+    from sipf_inputs import workload
+    wl = workload("small", N=2000, H=16)
+    st = O.make_state(wl.H, wl.L, wl.origin, wl.params, wl.x, wl.mass, wl.ids, wl.v, wl.m, wl.w)
+    idx = np.array([0, 5, 17, 999, 1999])
+    s_new, l_new = O.advance_particles(st, wl.dt, idx)
+    st1 = O.step(st, wl.dt)
+    np.testing.assert_array_equal(s_new, st1.s[idx])
+    np.testing.assert_array_equal(l_new, st1.loga[idx])
