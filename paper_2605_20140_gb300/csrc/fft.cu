@@ -153,6 +153,37 @@ __device__ __forceinline__ void stage(float2* buf, const float2* tw) {
     __syncthreads();
 }
 
+// First Stockham stage (NS = 1) with inputs from a loader: element j of
+// transform t is load(t, j).  All loads precede all writes (a block barrier
+// in between), so the loader may read the memory `out` overwrites.
+template <int L, int R, int NTRANS, int ES, int TS, int NT, int SIGN, class Load>
+__device__ __forceinline__ void stage1_from(float2* out, Load load) {
+    constexpr int NB = NTRANS * (L / R);
+    constexpr int BPT = (NB + NT - 1) / NT;
+    float2 v[BPT][R];
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        const int b = threadIdx.x + i * NT;
+        if (b < NB) {
+            const int t = b % NTRANS, j = b / NTRANS;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[i][r] = load(t, j + r * (L / R));
+            dft<R, SIGN>(v[i]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        const int b = threadIdx.x + i * NT;
+        if (b < NB) {
+            const int t = b % NTRANS, j = b / NTRANS;
+#pragma unroll
+            for (int r = 0; r < R; ++r) out[t * TS + (j * R + r) * ES] = v[i][r];
+        }
+    }
+    __syncthreads();
+}
+
 template <int L> struct Radix;
 template <> struct Radix<16> { static constexpr int R1 = 4, R2 = 4; };
 template <> struct Radix<32> { static constexpr int R1 = 8, R2 = 4; };
@@ -465,7 +496,39 @@ __device__ __forceinline__ void pack_rows(const float2* B, const float2* B2, flo
     __syncthreads();
 }
 
-// group 0: (m, w) -> m^n, w^n; group 1: (i k_x V, i k_y V, B) -> grad v^n.
+// Loaders for the fused first stages of the inverse pass.
+struct PlaneLoad {      // half-spectrum plane from global memory, optionally times i k
+    const float2* p;
+    int kxp;
+    float kx_scale, ky_scale;   // 2 pi / L, or 0 for "no multiplier"
+    int H, dir;                 // dir 0: plain, 1: i k_x, 2: i k_y
+    __device__ __forceinline__ float2 operator()(int kx, int ky) const {
+        const float2 val = __ldg(p + static_cast<size_t>(ky) * kxp + kx);
+        if (dir == 0) return val;
+        float k;
+        if (dir == 1) {
+            k = (kx >= H / 2) ? 0.0f : kx_scale * static_cast<float>(kx);
+        } else {
+            const int qy = ky < H / 2 ? ky : ky - H;
+            k = (qy == -H / 2) ? 0.0f : ky_scale * static_cast<float>(qy);
+        }
+        return make_float2(-k * val.y, k * val.x);
+    }
+};
+
+template <int H>
+struct PackLoad {       // complex row of two real signals from their half spectra
+    const float2* r1;
+    const float2* r2;
+    int pitch1, pitch2;         // row pitch (float2) of the two sources
+    __device__ __forceinline__ float2 operator()(int row, int kx) const {
+        return pack_two<H>(r1 + row * pitch1, r2 + row * pitch2, kx);
+    }
+};
+
+// group 1: (i k_x V, i k_y V, B) -> grad v^n; group 0: (m, w) -> m^n, w^n.
+// The first inverse-y stage reads the planes straight from global memory and
+// the first inverse-x stage reads the packed rows straight from the y output.
 template <int H>
 __global__ void __launch_bounds__(Cfg<H>::NT3)
     k_inverse_xy(SpectralArgs a, const float2* __restrict__ gM, const float2* __restrict__ gW,
@@ -473,6 +536,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT3)
                  float* __restrict__ m_out, float* __restrict__ w_out, float* __restrict__ G,
                  const float2* __restrict__ twg) {
     constexpr int NT = Cfg<H>::NT3, KXP = kxp<H>(), HK = H / 2 + 1, RP = rowp<H>();
+    constexpr int R1 = Radix<H>::R1, R2 = Radix<H>::R2;
     static_assert(H * RP <= 2 * H * KXP, "packed rows must fit in B0/B1");
     extern __shared__ float2 sm[];
     float2* B0 = sm;              // [H][KXP]
@@ -481,59 +545,32 @@ __global__ void __launch_bounds__(Cfg<H>::NT3)
     float2* tw = B2 + H * KXP;
     float2* Z = sm;               // [H][RP] packed rows (aliases B0/B1)
     float2* Z2 = B2;              // [H/2][RP] packed row pairs of B2 (aliases B2)
-    const int z = blockIdx.x, group = blockIdx.y;
+    const int z = blockIdx.x, group = 1 - blockIdx.y;
     if (group == 0 && !a.do_mw) return;
     for (int i = threadIdx.x; i < H; i += NT) tw[i] = twg[i];
-    {
-        // whole planes of KXP/2 float4 per row, all loads issued first
-        constexpr int NQ = H * (KXP / 2), ITER = (NQ + NT - 1) / NT;
-        const size_t pbase = static_cast<size_t>(z) * H * KXP;
-        const float4* s0 = reinterpret_cast<const float4*>((group == 0 ? gM : gV) + pbase);
-        const float4* s1 = reinterpret_cast<const float4*>((group == 0 ? gW : gB) + pbase);
-        float4 r0[ITER], r1[ITER];
-#pragma unroll
-        for (int i = 0; i < ITER; ++i) {
-            const int q = threadIdx.x + i * NT;
-            if (q < NQ) {
-                r0[i] = s0[q];
-                r1[i] = s1[q];
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < ITER; ++i) {
-            const int q = threadIdx.x + i * NT;
-            if (q >= NQ) continue;
-            if (group == 1) {
-                // i k_x V and i k_y V (Nyquist derivatives zero); B as loaded
-                const int ky = q / (KXP / 2), kx = 2 * (q % (KXP / 2));
-                const int qy = signed_mode(ky, H);
-                const float kyp = (qy == -H / 2) ? 0.0f : a.two_pi_over_L * static_cast<float>(qy);
-                float2 dx[2], dy[2];
-                const float2 val[2] = {make_float2(r0[i].x, r0[i].y), make_float2(r0[i].z, r0[i].w)};
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int k = kx + e;
-                    const float kxp_ = (k >= H / 2) ? 0.0f : a.two_pi_over_L * static_cast<float>(k);
-                    dx[e] = make_float2(-kxp_ * val[e].y, kxp_ * val[e].x);
-                    dy[e] = make_float2(-kyp * val[e].y, kyp * val[e].x);
-                }
-                reinterpret_cast<float4*>(B0)[q] = make_float4(dx[0].x, dx[0].y, dx[1].x, dx[1].y);
-                reinterpret_cast<float4*>(B1)[q] = make_float4(dy[0].x, dy[0].y, dy[1].x, dy[1].y);
-                reinterpret_cast<float4*>(B2)[q] = r1[i];
-            } else {
-                reinterpret_cast<float4*>(B0)[q] = r0[i];
-                reinterpret_cast<float4*>(B1)[q] = r1[i];
-            }
-        }
-    }
     __syncthreads();
-    fft_axis<H, HK, KXP, 1, NT, +1>(B0, tw);
-    fft_axis<H, HK, KXP, 1, NT, +1>(B1, tw);
-    if (group == 1) fft_axis<H, HK, KXP, 1, NT, +1>(B2, tw);
-    pack_rows<H, H, NT, false>(B0, B1, Z);
-    if (group == 1) pack_rows<H, H / 2, NT, true>(B2, nullptr, Z2);
-    fft_axis<H, H, 1, RP, NT, +1>(Z, tw);
-    if (group == 1) fft_axis<H, H / 2, 1, RP, NT, +1>(Z2, tw);
+    const size_t pbase = static_cast<size_t>(z) * H * KXP;
+    // inverse y: first stage from global, second in shared memory
+    if (group == 0) {
+        stage1_from<H, R1, HK, KXP, 1, NT, +1>(B0, PlaneLoad{gM + pbase, KXP, 0.f, 0.f, H, 0});
+        stage1_from<H, R1, HK, KXP, 1, NT, +1>(B1, PlaneLoad{gW + pbase, KXP, 0.f, 0.f, H, 0});
+    } else {
+        const float k = a.two_pi_over_L;
+        stage1_from<H, R1, HK, KXP, 1, NT, +1>(B0, PlaneLoad{gV + pbase, KXP, k, k, H, 1});
+        stage1_from<H, R1, HK, KXP, 1, NT, +1>(B1, PlaneLoad{gV + pbase, KXP, k, k, H, 2});
+        stage1_from<H, R1, HK, KXP, 1, NT, +1>(B2, PlaneLoad{gB + pbase, KXP, 0.f, 0.f, H, 0});
+    }
+    stage<H, R2, R1, HK, KXP, 1, NT, +1>(B0, tw);
+    stage<H, R2, R1, HK, KXP, 1, NT, +1>(B1, tw);
+    if (group == 1) stage<H, R2, R1, HK, KXP, 1, NT, +1>(B2, tw);
+    // inverse x: first stage from the packed half spectra (in place), second stage
+    if (group == 1) {
+        // B2's rows in pairs -> Z2 (B2's own space); done first, B0/B1 are still intact
+        stage1_from<H, R1, H / 2, 1, RP, NT, +1>(Z2, PackLoad<H>{B2, B2 + KXP, 2 * KXP, 2 * KXP});
+    }
+    stage1_from<H, R1, H, 1, RP, NT, +1>(Z, PackLoad<H>{B0, B1, KXP, KXP});
+    stage<H, R2, R1, H, 1, RP, NT, +1>(Z, tw);
+    if (group == 1) stage<H, R2, R1, H / 2, 1, RP, NT, +1>(Z2, tw);
     const size_t plane = static_cast<size_t>(z) * H * H;
     float* Gp = G + 4 * plane;
     if (group == 0) {
