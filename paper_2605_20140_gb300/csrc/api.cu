@@ -134,6 +134,10 @@ PushArgs push_args(const sipf_ctx* c, double dt, uint32_t n, int push) {
     a.n = n;
     a.k0 = static_cast<uint32_t>(c->p.seed);
     a.k1 = static_cast<uint32_t>(c->p.seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        a.rk[2 * r] = a.k0 + static_cast<uint32_t>(r) * 0x9E3779B9u;
+        a.rk[2 * r + 1] = a.k1 + static_cast<uint32_t>(r) * 0xBB67AE85u;
+    }
     a.push = push;
     return a;
 }

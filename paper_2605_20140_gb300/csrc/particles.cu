@@ -35,7 +35,14 @@ constexpr unsigned kFull = 0xffffffffu;
 // ------------------------------------------------------------------ Philox
 // Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
 // 32x32->64 multiplications with key mixing; the key advances by the Weyl
-// constants between rounds.
+// constants between rounds.  Each product is one wide multiply.
+__device__ __forceinline__ uint4 philox_round(uint4 c, uint32_t k0, uint32_t k1) {
+    const uint64_t p0 = static_cast<uint64_t>(0xD2511F53u) * c.x;
+    const uint64_t p1 = static_cast<uint64_t>(0xCD9E8D57u) * c.z;
+    return make_uint4(static_cast<uint32_t>(p1 >> 32) ^ c.y ^ k0, static_cast<uint32_t>(p1),
+                      static_cast<uint32_t>(p0 >> 32) ^ c.w ^ k1, static_cast<uint32_t>(p0));
+}
+
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
@@ -43,24 +50,26 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
             k0 += 0x9E3779B9u;
             k1 += 0xBB67AE85u;
         }
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        c = philox_round(c, k0, k1);
     }
     return c;
 }
 
-// (2 (b >> 9) + 1) 2^-24: exact in float32, in (0, 1).
-__device__ __forceinline__ float unit_open(uint32_t b) {
-    return __uint2float_rn(((b >> 9) << 1) | 1u) * 5.9604644775390625e-8f;
+// The same generator with the ten round keys given (rk[2r], rk[2r+1]).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const uint32_t (&rk)[20]) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) c = philox_round(c, rk[2 * r], rk[2 * r + 1]);
+    return c;
 }
 
-// Three standard normals of particle `id` in step n: Box-Muller on the four
-// Philox words of counter (n, 0, id, 0).
-__device__ __forceinline__ float3 brownian(uint32_t id, uint32_t n, uint32_t k0, uint32_t k1,
-                                           uint4* raw = nullptr) {
-    const uint4 b = philox4x32_10(make_uint4(n, 0u, id, 0u), k0, k1);
-    if (raw) *raw = b;
+// (2 (b >> 9) + 1) 2^-24, in (0, 1): the float 1 + (b >> 9) 2^-23 minus
+// 1 - 2^-24; the difference has at most 24 significant bits, so it is exact.
+__device__ __forceinline__ float unit_open(uint32_t b) {
+    return __fsub_rn(__uint_as_float(0x3F800000u | (b >> 9)), __uint_as_float(0x3F7FFFFFu));
+}
+
+// Box-Muller on the four words of one Philox block: three standard normals.
+__device__ __forceinline__ float3 box_muller(const uint4 b) {
     const float u0 = unit_open(b.x), u1 = unit_open(b.y);
     const float u2 = unit_open(b.z), u3 = unit_open(b.w);
     const float r01 = sqrtf(-2.0f * logf(u0));
@@ -69,6 +78,15 @@ __device__ __forceinline__ float3 brownian(uint32_t id, uint32_t n, uint32_t k0,
     sincospif(2.0f * u1, &s1, &c1);
     const float c3 = cospif(2.0f * u3);
     return make_float3(r01 * c1, r01 * s1, r23 * c3);
+}
+
+// Three standard normals of particle `id` in step n: Box-Muller on the four
+// Philox words of counter (n, 0, id, 0).
+__device__ __forceinline__ float3 brownian(uint32_t id, uint32_t n, uint32_t k0, uint32_t k1,
+                                           uint4* raw = nullptr) {
+    const uint4 b = philox4x32_10(make_uint4(n, 0u, id, 0u), k0, k1);
+    if (raw) *raw = b;
+    return box_muller(b);
 }
 
 // ------------------------------------------------------------------ float <-> double by bits
@@ -104,15 +122,28 @@ struct Cell {
     float fx, fy, fz;    // fractional position in the cell
 };
 
+// Positions are in [0, H).  For 0 <= s < 2^23, 2^23 + s rounded toward zero
+// is 2^23 + floor(s): its low mantissa bits are the cell and subtracting
+// 2^23 gives floor(s) as a float, both exact (no conversion instructions).
+// The cell is clamped to [0, H) whatever s is.
+__device__ __forceinline__ void split_cell(float s, int H, int& cell, float& frac) {
+    const float t = __fadd_rz(s, 8388608.0f);
+    cell = min(max(static_cast<int>(__float_as_uint(t) - 0x4B000000u), 0), H - 1);
+    frac = __fsub_rn(s, __fsub_rn(t, 8388608.0f));
+}
+
 __device__ __forceinline__ Cell locate(float x, float y, float z, int H) {
     Cell c;
-    c.cx = min(static_cast<int>(x), H - 1);
-    c.cy = min(static_cast<int>(y), H - 1);
-    c.cz = min(static_cast<int>(z), H - 1);
-    c.fx = __fsub_rn(x, __int2float_rn(c.cx));
-    c.fy = __fsub_rn(y, __int2float_rn(c.cy));
-    c.fz = __fsub_rn(z, __int2float_rn(c.cz));
+    split_cell(x, H, c.cx, c.fx);
+    split_cell(y, H, c.cy, c.fy);
+    split_cell(z, H, c.cz, c.fz);
     return c;
+}
+
+// round(v) for 0 <= v < 2^22, ties to even (as __float2uint_rn): the low
+// mantissa bits of 2^23 + v.
+__device__ __forceinline__ uint32_t round_small(float v) {
+    return __float_as_uint(__fadd_rn(v, 8388608.0f)) - 0x4B000000u;
 }
 
 __device__ __forceinline__ int tile_of(int cx, int cy, int cz, int T) {
@@ -226,6 +257,7 @@ __global__ void __launch_bounds__(kNT, SIPF_STEP_MIN_BLOCKS)
            unsigned long long* __restrict__ acc, int do_deposit, int do_move,
            int* __restrict__ status) {
     __shared__ unsigned dep[kBlock];        // node sums of the item (exact: < 2^31)
+    __shared__ unsigned long long dep64[kBlock];   // node sums of the tile's items so far
     __shared__ float4 gblk[kBlock];         // (dv/dx, dv/dy, dv/dz, w) on the tile's 9^3 nodes
     __shared__ Staged st;
     __shared__ int nb_cnt[27];
@@ -237,34 +269,61 @@ __global__ void __launch_bounds__(kNT, SIPF_STEP_MIN_BLOCKS)
     const int lane = threadIdx.x & 31;
     const float Hf = __int2float_rn(H);
     const int total = *n_items;
-    // items are assigned statically: block b takes items b, b + grid, ...
-    for (int item_idx = blockIdx.x; item_idx < total; item_idx += gridDim.x) {
-        for (int i = threadIdx.x; i < kBlock; i += kNT) dep[i] = 0u;
-        const Item it = items[item_idx];
+    for (int i = threadIdx.x; i < kBlock; i += kNT) {
+        dep[i] = 0u;
+        dep64[i] = 0ull;
+    }
+    // block b takes a contiguous run of items; consecutive items of one tile
+    // share the node block of the gather array and the deposit sums, which
+    // go to the grid accumulator once, when the tile changes
+    const int i_lo = static_cast<int>(static_cast<long long>(blockIdx.x) * total / gridDim.x);
+    const int i_hi = static_cast<int>(static_cast<long long>(blockIdx.x + 1) * total / gridDim.x);
+    int cur = -1, cx0 = 0, cy0 = 0, cz0 = 0;   // tile held in dep64 / gblk, its first cell
+    for (int item_idx = i_lo; item_idx <= i_hi; ++item_idx) {
+        const Item it = item_idx < i_hi ? items[item_idx] : Item{-1, 0, 0, 0, 0, 0, 0, 0};
         const int tile = it.tile;
-        const int ttx = it.tx, tty = it.ty, ttz = it.tz;
-        const int tx0 = ttx * 8, ty0 = tty * 8, tz0 = ttz * 8;
-        if (do_move && a.push && tile >= 0) {
-            // the tile's node block of the gather array (periodic), 9 float4 per row
-            for (int q = threadIdx.x; q < kBlock; q += kNT) {
-                const int lx = q % 9, ly = (q / 9) % 9, lz = q / 81;
-                const int nx = tx0 + lx < H ? tx0 + lx : tx0 + lx - H;
-                const int ny = ty0 + ly < H ? ty0 + ly : ty0 + ly - H;
-                const int nz = tz0 + lz < H ? tz0 + lz : tz0 + lz - H;
-                gblk[q] = __ldg(G + (nz * H + ny) * H + nx);
+        if (tile != cur || tile < 0) {
+            if (cur >= 0 && do_deposit) {
+                // flush the finished tile's node block into the grid accumulator
+                for (int j = threadIdx.x; j < kBlock; j += kNT) {
+                    const unsigned long long v = dep64[j];
+                    if (v) {
+                        const int lx = j % 9, ly = (j / 9) % 9, lz = j / 81;
+                        const int nx = cx0 + lx < H ? cx0 + lx : cx0 + lx - H;
+                        const int ny = cy0 + ly < H ? cy0 + ly : cy0 + ly - H;
+                        const int nz = cz0 + lz < H ? cz0 + lz : cz0 + lz - H;
+                        atomicAdd(acc + (nz * H + ny) * H + nx, v);
+                        dep64[j] = 0ull;
+                    }
+                }
             }
-        }
-        if (threadIdx.x < 27) {
-            const int k = threadIdx.x;
-            nb_cnt[k] = 0;
-            if (do_move && tile >= 0) {
-                const int nx = ttx + k % 3 - 1, ny = tty + (k / 3) % 3 - 1, nz = ttz + k / 9 - 1;
+            if (item_idx == i_hi) break;
+            cur = tile;
+            cx0 = it.tx * 8;
+            cy0 = it.ty * 8;
+            cz0 = it.tz * 8;
+            if (do_move && a.push && tile >= 0) {
+                // the tile's node block of the gather array (periodic), 9 float4 per row
+                for (int q = threadIdx.x; q < kBlock; q += kNT) {
+                    const int lx = q % 9, ly = (q / 9) % 9, lz = q / 81;
+                    const int nx = cx0 + lx < H ? cx0 + lx : cx0 + lx - H;
+                    const int ny = cy0 + ly < H ? cy0 + ly : cy0 + ly - H;
+                    const int nz = cz0 + lz < H ? cz0 + lz : cz0 + lz - H;
+                    gblk[q] = __ldg(G + (nz * H + ny) * H + nx);
+                }
+            }
+            if (threadIdx.x < 27 && do_move && tile >= 0) {
+                const int k = threadIdx.x;
+                const int nx = it.tx + k % 3 - 1, ny = it.ty + (k / 3) % 3 - 1, nz = it.tz + k / 9 - 1;
                 const int nt = (((nz + T) % T) * T + (ny + T) % T) * T + (nx + T) % T;
                 nb_tile[k] = nt;
                 nb_start[k] = L.bstart[nt];
                 nb_cap[k] = L.cap[nt];
             }
         }
+        const int ttx = it.tx, tty = it.ty, ttz = it.tz;
+        const int tx0 = cx0, ty0 = cy0, tz0 = cz0;
+        if (threadIdx.x < 27) nb_cnt[threadIdx.x] = 0;
         __syncthreads();
         int bad = 0;
         for (int j = 0; j < kPT; ++j) {
@@ -285,7 +344,9 @@ __global__ void __launch_bounds__(kNT, SIPF_STEP_MIN_BLOCKS)
 
             if (do_deposit && valid) {
                 // a_p R_h(X_p, node) h^3 in units of exp(logref) 2^-S, as uint32 (< 2^21)
-                const float ea = __fmul_rn(expf(d2f_bits(pl)), d.scale);
+                // (below 2^20 by the choice of S; the clamp keeps a non-finite
+                // mass inside round_small's range)
+                const float ea = fminf(__fmul_rn(expf(d2f_bits(pl)), d.scale), 4194304.0f);
                 const float wx0 = __fsub_rn(1.0f, c.fx), wy0 = __fsub_rn(1.0f, c.fy);
                 const float e0 = __fmul_rn(ea, __fsub_rn(1.0f, c.fz)), e1 = __fmul_rn(ea, c.fz);
                 const float xy[4] = {__fmul_rn(wx0, wy0), __fmul_rn(c.fx, wy0),
@@ -293,8 +354,8 @@ __global__ void __launch_bounds__(kNT, SIPF_STEP_MIN_BLOCKS)
                 uint32_t q[8];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    q[k] = __float2uint_rn(__fmul_rn(e0, xy[k]));
-                    q[4 + k] = __float2uint_rn(__fmul_rn(e1, xy[k]));
+                    q[k] = round_small(__fmul_rn(e0, xy[k]));
+                    q[4 + k] = round_small(__fmul_rn(e1, xy[k]));
                 }
                 const int lx = c.cx - tx0, ly = c.cy - ty0, lz = c.cz - tz0;
                 const bool in_tile = tile >= 0 && ((lx | ly | lz) & ~7) == 0;
@@ -335,7 +396,7 @@ __global__ void __launch_bounds__(kNT, SIPF_STEP_MIN_BLOCKS)
                     const float inc = log1pf(__fmul_rn(a.tau, __fsub_rn(rho, 1.0f)));
                     pl = pl + f2d_bits(inc);
                     // Euler-Maruyama push in grid units
-                    const float3 nz = brownian(pid, a.n, a.k0, a.k1);
+                    const float3 nz = box_muller(philox4x32_10(make_uint4(a.n, 0u, pid, 0u), a.rk));
                     px = wrap(__fmaf_rn(a.noise, nz.x, __fmaf_rn(a.drift, g.x, px)), Hf, &bad);
                     py = wrap(__fmaf_rn(a.noise, nz.y, __fmaf_rn(a.drift, g.y, py)), Hf, &bad);
                     pz = wrap(__fmaf_rn(a.noise, nz.z, __fmaf_rn(a.drift, g.z, pz)), Hf, &bad);
@@ -371,6 +432,16 @@ __global__ void __launch_bounds__(kNT, SIPF_STEP_MIN_BLOCKS)
         if (bad & 1) atomicOr(status, kStatusNonfinite);
         if (bad & 2) atomicOr(status, kStatusSlot);
         __syncthreads();
+        if (do_deposit && tile >= 0) {
+            // the item's exact 32-bit sums into the tile's 64-bit sums
+            for (int j = threadIdx.x; j < kBlock; j += kNT) {
+                const unsigned v = dep[j];
+                if (v) {
+                    dep64[j] += v;
+                    dep[j] = 0u;
+                }
+            }
+        }
         if (do_move) {
             if (threadIdx.x < 27 && nb_cnt[threadIdx.x] > 0)
                 nb_base[threadIdx.x] = atomicAdd(L.cnt + nb_tile[threadIdx.x], nb_cnt[threadIdx.x]);
@@ -411,18 +482,6 @@ __global__ void __launch_bounds__(kNT, SIPF_STEP_MIN_BLOCKS)
                     dst.sz[dest] = st.z[e];
                     dst.dl[dest] = st.l[e];
                     dst.id[dest] = st.id[e];
-                }
-            }
-        }
-        __syncthreads();
-        if (do_deposit && tile >= 0) {
-            // flush the tile's node block into the grid accumulator
-            for (int j = threadIdx.x; j < kBlock; j += kNT) {
-                const unsigned long long v = dep[j];
-                if (v) {
-                    const int lx = j % 9, ly = (j / 9) % 9, lz = j / 81;
-                    const int nx = (tx0 + lx) % H, ny = (ty0 + ly) % H, nz = (tz0 + lz) % H;
-                    atomicAdd(acc + (nz * H + ny) * H + nx, v);
                 }
             }
         }

@@ -32,6 +32,7 @@ struct PushArgs {
     float tau;
     uint32_t n;       // step index (Philox counter word 0)
     uint32_t k0, k1;  // Philox key
+    uint32_t rk[20];  // Philox round keys (k0 + r 0x9E3779B9, k1 + r 0xBB67AE85), r = 0..9
     int push;         // 0: positions unchanged (pure binning)
 };
 
