@@ -74,8 +74,9 @@ extern "C" {
 typedef struct sipf_ctx sipf_ctx;
 
 /* Periodic box [origin, origin + L)^3 with H nodes per axis (paper Sec. 2.1;
- * Omega = [-L/2, L/2]^3 there, origin = -L/2).  H must be 16, 32, 64, 128
- * or 256 in this build. */
+ * Omega = [-L/2, L/2]^3 there, origin = -L/2).  H must be a multiple of 8
+ * of the form 2^a 3^b up to 256: 8, 16, 24, 32, 48, 64, 72, 96, 128, 144,
+ * 192 or 256. */
 typedef struct {
     int32_t H;
     double L;
@@ -166,6 +167,34 @@ int sipf_diagnostics(sipf_ctx* ctx, sipf_diag* out);
 
 /* Wait for the context's stream and return any deferred device error. */
 int sipf_sync(sipf_ctx* ctx);
+
+/* Checkpoint / resume.  The paper has no checkpoint; what is saved is the
+ * state of the scheme after step n of Alg. 3: the particles X^n (grid units)
+ * with log a^n and ids, the grids v^n, m^n, w^n and the gather array
+ * (grad v^n, w^n), plus the step count, time, seed and the deposit's
+ * fixed-point reference (which fixes how u_bar is rounded).  A context
+ * loaded from the file and advanced k steps gives bit for bit the state of
+ * the saved context advanced k steps with the same dt sequence.
+ *
+ * sipf_save writes the file `path` (overwritten), native byte order, about
+ * 20 N + 28 H^3 bytes plus a header; synchronises.  Errors: SIPF_EINVAL
+ * (no state set, NULL path, file not writable), SIPF_ENOMEM (host buffer),
+ * SIPF_ECUDA, and any deferred device error.
+ *
+ * sipf_load creates a new context on the current device from the file, with
+ * all later work on `stream` (a cudaStream_t, NULL = legacy default), and
+ * stores it in *out (the caller destroys it).  Errors: SIPF_EINVAL (NULL
+ * argument, unreadable file, wrong magic/version, sizes that do not match
+ * the header, payload checksum mismatch, unsupported H), SIPF_ENOMEM,
+ * SIPF_ECUDA. */
+int sipf_save(sipf_ctx* ctx, const char* path);
+int sipf_load(const char* path, void* stream, sipf_ctx** out);
+
+/* The context's grid, particle count, parameters, steps taken and time
+ * (host scalars; any output pointer may be NULL).  Does not synchronise.
+ * Errors: SIPF_EINVAL (NULL ctx). */
+int sipf_describe(const sipf_ctx* ctx, sipf_grid* grid, int64_t* N, sipf_params* params,
+                  int64_t* step, double* time);
 
 /* Free all device state of the context (synchronising first); NULL is a
  * no-op. */

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <new>
@@ -30,7 +31,16 @@ int cuda_fail(sipf_ctx* c, cudaError_t e, const char* where) {
         if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);   \
     } while (0)
 
-bool supported_H(int H) { return H == 16 || H == 32 || H == 64 || H == 128 || H == 256; }
+// Grid sides with a radix plan (2^a 3^b) that are multiples of the 8-cell tile.
+bool supported_H(int H) {
+    switch (H) {
+        case 8: case 16: case 24: case 32: case 48: case 64: case 72: case 96: case 128:
+        case 144: case 192: case 256:
+            return true;
+        default:
+            return false;
+    }
+}
 
 bool finite_nonneg(double x) { return isfinite(x) && x >= 0.0; }
 
@@ -248,6 +258,55 @@ int enqueue_step(sipf_ctx* c, double dt) {
     c->time += dt;
     return SIPF_OK;
 }
+
+// ---------------------------------------------------------------- checkpoints
+// File layout (native byte order): CkptHeader, then the payload arrays in
+// the order sx, sy, sz (N float, grid units), dl (N double, log a - logref),
+// id (N uint32), v, m, w (H^3 float), G (4 H^3 float).
+constexpr char kCkptMagic[8] = {'S', 'I', 'P', 'F', 'C', 'K', 'P', 'T'};
+constexpr uint32_t kCkptVersion = 1;
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t header_bytes;   // sizeof(CkptHeader)
+    int32_t H;
+    int32_t pad0;
+    double L;
+    double origin[3];
+    int64_t N;
+    sipf_params params;
+    int64_t step;
+    double time;
+    double logref;
+    double maxrel;
+    float voff;
+    uint32_t pad1;
+    uint64_t payload_bytes;
+    uint64_t payload_hash;   // ckpt_hash of the payload
+};
+
+// 64-bit FNV-1a over 8-byte words (a final partial word is zero-padded).
+uint64_t ckpt_hash(uint64_t h, const void* data, size_t bytes) {
+    const unsigned char* b = static_cast<const unsigned char*>(data);
+    size_t i = 0;
+    for (; i + 8 <= bytes; i += 8) {
+        uint64_t w;
+        memcpy(&w, b + i, 8);
+        h = (h ^ w) * 0x100000001B3ull;
+    }
+    if (i < bytes) {
+        uint64_t w = 0;
+        memcpy(&w, b + i, bytes - i);
+        h = (h ^ w) * 0x100000001B3ull;
+    }
+    return h;
+}
+
+struct CkptArray {
+    void* dev;
+    size_t bytes;
+};
 
 }  // namespace
 
@@ -643,6 +702,153 @@ void sipf_destroy(sipf_ctx* c) {
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     free_all(c);
     delete c;
+}
+
+int sipf_save(sipf_ctx* c, const char* path) {
+    if (!c) return SIPF_EINVAL;
+    if (!path) return fail(c, SIPF_EINVAL, "NULL path");
+    if (!c->state_set) return fail(c, SIPF_EINVAL, "sipf_set_state has not been called");
+    const size_t N = static_cast<size_t>(c->N);
+    const size_t H3 = static_cast<size_t>(c->H) * c->H * c->H;
+    int r = compact_current(c);
+    if (r != SIPF_OK) return r;
+    const int o = c->cur ^ 1;
+    const CkptArray arrays[] = {
+        {c->sx[o], N * sizeof(float)}, {c->sy[o], N * sizeof(float)},
+        {c->sz[o], N * sizeof(float)}, {c->dl[o], N * sizeof(double)},
+        {c->id[o], N * sizeof(uint32_t)}, {c->v, H3 * sizeof(float)},
+        {c->m, H3 * sizeof(float)}, {c->w, H3 * sizeof(float)}, {c->G, 4 * H3 * sizeof(float)}};
+    size_t total = 0;
+    for (const CkptArray& a : arrays) total += a.bytes;
+    std::vector<unsigned char> payload;
+    try {
+        payload.resize(total);
+    } catch (...) {
+        return fail(c, SIPF_ENOMEM, "sipf_save: host buffer");
+    }
+    size_t off = 0;
+    for (const CkptArray& a : arrays) {
+        SIPF_CUDA(c, cudaMemcpyAsync(payload.data() + off, a.dev, a.bytes, cudaMemcpyDeviceToHost,
+                                     c->stream));
+        off += a.bytes;
+    }
+    float voff = 0.f;
+    SIPF_CUDA(c, cudaMemcpyAsync(&voff, c->voff, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    SIPF_CUDA(c, cudaStreamSynchronize(c->stream));
+    r = check_status(c);
+    if (r != SIPF_OK) return r;
+    CkptHeader hd;
+    memset(&hd, 0, sizeof(hd));
+    memcpy(hd.magic, kCkptMagic, 8);
+    hd.version = kCkptVersion;
+    hd.header_bytes = sizeof(CkptHeader);
+    hd.H = c->H;
+    hd.L = c->L;
+    for (int k = 0; k < 3; ++k) hd.origin[k] = c->origin[k];
+    hd.N = c->N;
+    hd.params = c->p;
+    hd.step = c->step;
+    hd.time = c->time;
+    hd.logref = c->logref;
+    hd.maxrel = c->maxrel;
+    hd.voff = voff;
+    hd.payload_bytes = total;
+    hd.payload_hash = ckpt_hash(0xCBF29CE484222325ull, payload.data(), total);
+    FILE* f = fopen(path, "wb");
+    if (!f) return fail(c, SIPF_EINVAL, std::string("sipf_save: cannot open ") + path);
+    const bool ok = fwrite(&hd, sizeof(hd), 1, f) == 1 &&
+                    fwrite(payload.data(), 1, total, f) == total;
+    const bool closed = fclose(f) == 0;
+    if (!ok || !closed) return fail(c, SIPF_EINVAL, std::string("sipf_save: write failed: ") + path);
+    return SIPF_OK;
+}
+
+int sipf_load(const char* path, void* stream, sipf_ctx** out) {
+    if (!path || !out) return SIPF_EINVAL;
+    *out = nullptr;
+    FILE* f = fopen(path, "rb");
+    if (!f) return SIPF_EINVAL;
+    CkptHeader hd;
+    if (fread(&hd, sizeof(hd), 1, f) != 1 || memcmp(hd.magic, kCkptMagic, 8) != 0 ||
+        hd.version != kCkptVersion || hd.header_bytes != sizeof(CkptHeader) ||
+        !supported_H(hd.H) || hd.N < 1 || hd.N >= (int64_t{1} << 31)) {
+        fclose(f);
+        return SIPF_EINVAL;
+    }
+    const size_t N = static_cast<size_t>(hd.N);
+    const size_t H3 = static_cast<size_t>(hd.H) * hd.H * hd.H;
+    const size_t total = N * (3 * sizeof(float) + sizeof(double) + sizeof(uint32_t)) +
+                         H3 * 7 * sizeof(float);
+    if (hd.payload_bytes != total) {
+        fclose(f);
+        return SIPF_EINVAL;
+    }
+    std::vector<unsigned char> payload;
+    try {
+        payload.resize(total);
+    } catch (...) {
+        fclose(f);
+        return SIPF_ENOMEM;
+    }
+    const bool got = fread(payload.data(), 1, total, f) == total;
+    fclose(f);
+    if (!got || ckpt_hash(0xCBF29CE484222325ull, payload.data(), total) != hd.payload_hash)
+        return SIPF_EINVAL;
+    sipf_grid g;
+    g.H = hd.H;
+    g.L = hd.L;
+    for (int k = 0; k < 3; ++k) g.origin[k] = hd.origin[k];
+    sipf_ctx* c = nullptr;
+    int r = sipf_create(&g, hd.N, &hd.params, stream, &c);
+    if (r != SIPF_OK) return r;
+    // particles unbinned into buffer 1, fields and the gather array as saved
+    const CkptArray arrays[] = {
+        {c->sx[1], N * sizeof(float)}, {c->sy[1], N * sizeof(float)},
+        {c->sz[1], N * sizeof(float)}, {c->dl[1], N * sizeof(double)},
+        {c->id[1], N * sizeof(uint32_t)}, {c->v, H3 * sizeof(float)},
+        {c->m, H3 * sizeof(float)}, {c->w, H3 * sizeof(float)}, {c->G, 4 * H3 * sizeof(float)}};
+    size_t off = 0;
+    cudaError_t e = cudaSuccess;
+    for (const CkptArray& a : arrays) {
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(a.dev, payload.data() + off, a.bytes, cudaMemcpyHostToDevice,
+                                c->stream);
+        off += a.bytes;
+    }
+    c->voff_host = hd.voff;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->voff, &c->voff_host, sizeof(float), cudaMemcpyHostToDevice,
+                            c->stream);
+    c->step = hd.step;
+    c->time = hd.time;
+    c->logref = hd.logref;
+    c->maxrel = hd.maxrel;
+    if (e == cudaSuccess) {
+        r = bin_initial(c);
+        if (r == SIPF_OK) e = cudaStreamSynchronize(c->stream);
+    }
+    if (e != cudaSuccess || r != SIPF_OK || check_status(c) != SIPF_OK) {
+        sipf_destroy(c);
+        return e != cudaSuccess ? SIPF_ECUDA : (r != SIPF_OK ? r : SIPF_EINTERNAL);
+    }
+    c->state_set = true;
+    *out = c;
+    return SIPF_OK;
+}
+
+int sipf_describe(const sipf_ctx* c, sipf_grid* grid, int64_t* N, sipf_params* params,
+                  int64_t* step, double* time) {
+    if (!c) return SIPF_EINVAL;
+    if (grid) {
+        grid->H = c->H;
+        grid->L = c->L;
+        for (int k = 0; k < 3; ++k) grid->origin[k] = c->origin[k];
+    }
+    if (N) *N = c->N;
+    if (params) *params = c->p;
+    if (step) *step = c->step;
+    if (time) *time = c->time;
+    return SIPF_OK;
 }
 
 int sipf_profile(sipf_ctx* c, int enable) {

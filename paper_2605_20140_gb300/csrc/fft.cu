@@ -100,12 +100,26 @@ struct DftLevel {
     }
 };
 
-// In-register R-point DFT (R = 2, 4, 8, 16), sign -1 forward, +1 inverse:
+// In-register R-point DFT, sign -1 forward, +1 inverse.  R = 2, 4, 8, 16:
 // bit-reversal permutation, then log2 R radix-2 levels (decimation in time).
+// R = 3: X0 = a + b + c, X1 = a - (b + c)/2 + SIGN i (sqrt 3 / 2)(b - c),
+// X2 = a - (b + c)/2 - SIGN i (sqrt 3 / 2)(b - c).
 template <int R, int SIGN>
 __device__ __forceinline__ void dft(float2 (&v)[R]) {
-    BitRevSwap<R, 0>::run(v);
-    DftLevel<R, 2, SIGN>::run(v);
+    if constexpr (R == 3) {
+        constexpr float s3 = 0.86602540378443865f;
+        const float2 sum = cadd(v[1], v[2]), dif = csub(v[1], v[2]);
+        const float2 mid = make_float2(v[0].x - 0.5f * sum.x, v[0].y - 0.5f * sum.y);
+        // rot = SIGN i s3 (b - c)
+        const float2 rot = SIGN < 0 ? make_float2(s3 * dif.y, -s3 * dif.x)
+                                    : make_float2(-s3 * dif.y, s3 * dif.x);
+        v[0] = cadd(v[0], sum);
+        v[1] = cadd(mid, rot);
+        v[2] = csub(mid, rot);
+    } else {
+        BitRevSwap<R, 0>::run(v);
+        DftLevel<R, 2, SIGN>::run(v);
+    }
 }
 
 // One Stockham stage of radix R after NS points have been combined.
@@ -184,30 +198,62 @@ __device__ __forceinline__ void stage1_from(float2* out, Load load) {
     __syncthreads();
 }
 
+// Radix plan of a length-L transform: two or three Stockham stages
+// (R3 = 1: two).  Lengths are 2^a 3^b with 8 <= L <= 256.
 template <int L> struct Radix;
-template <> struct Radix<16> { static constexpr int R1 = 4, R2 = 4; };
-template <> struct Radix<32> { static constexpr int R1 = 8, R2 = 4; };
-template <> struct Radix<64> { static constexpr int R1 = 8, R2 = 8; };
-template <> struct Radix<128> { static constexpr int R1 = 16, R2 = 8; };
-template <> struct Radix<256> { static constexpr int R1 = 16, R2 = 16; };
+template <> struct Radix<8> { static constexpr int R1 = 4, R2 = 2, R3 = 1; };
+template <> struct Radix<16> { static constexpr int R1 = 4, R2 = 4, R3 = 1; };
+template <> struct Radix<24> { static constexpr int R1 = 8, R2 = 3, R3 = 1; };
+template <> struct Radix<32> { static constexpr int R1 = 8, R2 = 4, R3 = 1; };
+template <> struct Radix<48> { static constexpr int R1 = 16, R2 = 3, R3 = 1; };
+template <> struct Radix<64> { static constexpr int R1 = 8, R2 = 8, R3 = 1; };
+template <> struct Radix<72> { static constexpr int R1 = 8, R2 = 3, R3 = 3; };
+template <> struct Radix<96> { static constexpr int R1 = 8, R2 = 4, R3 = 3; };
+template <> struct Radix<128> { static constexpr int R1 = 16, R2 = 8, R3 = 1; };
+template <> struct Radix<144> { static constexpr int R1 = 16, R2 = 3, R3 = 3; };
+template <> struct Radix<192> { static constexpr int R1 = 16, R2 = 4, R3 = 3; };
+template <> struct Radix<256> { static constexpr int R1 = 16, R2 = 16, R3 = 1; };
+
+// The stages after the first of a batched length-L FFT.
+template <int L, int NTRANS, int ES, int TS, int NT, int SIGN>
+__device__ __forceinline__ void fft_rest(float2* buf, const float2* tw) {
+    constexpr int R1 = Radix<L>::R1, R2 = Radix<L>::R2, R3 = Radix<L>::R3;
+    static_assert(R1 * R2 * R3 == L, "radix plan");
+    stage<L, R2, R1, NTRANS, ES, TS, NT, SIGN>(buf, tw);
+    if constexpr (R3 > 1) stage<L, R3, R1 * R2, NTRANS, ES, TS, NT, SIGN>(buf, tw);
+}
 
 // Batched length-L FFT along one axis of a shared-memory array.
 template <int L, int NTRANS, int ES, int TS, int NT, int SIGN>
 __device__ __forceinline__ void fft_axis(float2* buf, const float2* tw) {
-    constexpr int R1 = Radix<L>::R1, R2 = Radix<L>::R2;
-    static_assert(R1 * R2 == L, "radix plan");
-    stage<L, R1, 1, NTRANS, ES, TS, NT, SIGN>(buf, tw);
-    stage<L, R2, R1, NTRANS, ES, TS, NT, SIGN>(buf, tw);
+    stage<L, Radix<L>::R1, 1, NTRANS, ES, TS, NT, SIGN>(buf, tw);
+    fft_rest<L, NTRANS, ES, TS, NT, SIGN>(buf, tw);
 }
 
-// Threads per block of the three passes (forward xy, z, inverse xy).
+// (H - k) mod H for 0 <= k <= H: the index of the mode -k.
+template <int H>
+__device__ __forceinline__ int neg_mod(int k) {
+    if constexpr ((H & (H - 1)) == 0) return (H - k) & (H - 1);
+    else return k == 0 ? 0 : H - k;
+}
+
+// Threads of the three fused passes (H <= 128) or of the z pass (H > 128),
+// chosen so that the radix-16 or radix-8 stages hold at most two butterflies
+// per thread.
 template <int H> struct Cfg;
+template <> struct Cfg<8> { static constexpr int NT1 = 64, NT2 = 64, NT3 = 64; };
 template <> struct Cfg<16> { static constexpr int NT1 = 256, NT2 = 256, NT3 = 256; };
+template <> struct Cfg<24> { static constexpr int NT1 = 256, NT2 = 128, NT3 = 256; };
 template <> struct Cfg<32> { static constexpr int NT1 = 256, NT2 = 256, NT3 = 256; };
+template <> struct Cfg<48> { static constexpr int NT1 = 256, NT2 = 256, NT3 = 256; };
 template <> struct Cfg<64> { static constexpr int NT1 = 512, NT2 = 512, NT3 = 512; };
+template <> struct Cfg<72> { static constexpr int NT1 = 512, NT2 = 352, NT3 = 512; };
+template <> struct Cfg<96> { static constexpr int NT1 = 768, NT2 = 608, NT3 = 768; };
 // 544 = 17 warps: one radix-16 butterfly per thread for the 65 z-transforms
 template <> struct Cfg<128> { static constexpr int NT1 = 1024, NT2 = 544, NT3 = 1024; };
-// H = 256 runs the per-axis pipeline; NT2 is the z pass over 32-column tiles
+// H > 128 runs the per-axis pipeline; NT2 is the z pass over 32-column tiles
+template <> struct Cfg<144> { static constexpr int NT1 = 256, NT2 = 288, NT3 = 256; };
+template <> struct Cfg<192> { static constexpr int NT1 = 256, NT2 = 384, NT3 = 256; };
 template <> struct Cfg<256> { static constexpr int NT1 = 256, NT2 = 512, NT3 = 256; };
 
 // kx columns per block of the z pass: the whole padded row up to H = 128
@@ -262,7 +308,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT1)
     const float c0 = *voff;   // the v spectrum only feeds derivatives: remove a constant
     {
         // groups of 4 consecutive x; all loads of a batch are issued first
-        constexpr int NG = H * H / 4, ITER = (NG + NT - 1) / NT, CH = ITER < 4 ? ITER : 4;
+        constexpr int NG = H * H / 4, ITER = (NG + NT - 1) / NT, CH = ITER < 2 ? ITER : 2;
         const float4* v4 = reinterpret_cast<const float4*>(v + plane);
         const float4* m4 = reinterpret_cast<const float4*>(m + plane);
         const float4* w4 = reinterpret_cast<const float4*>(w + plane);
@@ -321,7 +367,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT1)
             if (idx < NS) {
                 const int p = idx / HK, k = idx % HK;
                 const float2 zp = Vb[p * RP + k];
-                const float2 zm = Vb[p * RP + ((H - k) & (H - 1))];
+                const float2 zm = Vb[p * RP + neg_mod<H>(k)];
                 x1[s] = make_float2(0.5f * (zp.x + zm.x), 0.5f * (zp.y - zm.y));
                 x2[s] = make_float2(0.5f * (zp.y + zm.y), -0.5f * (zp.x - zm.x));
             }
@@ -354,7 +400,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT1)
             const int k = kx + e;
             if (k < HK) {
                 const float2 zk = Z[ky * RP + k];
-                const float2 zc = Z[((H - ky) & (H - 1)) * RP + ((H - k) & (H - 1))];
+                const float2 zc = Z[neg_mod<H>(ky) * RP + neg_mod<H>(k)];
                 M[e] = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y - zc.y));
                 W[e] = make_float2(0.5f * (zk.y + zc.y), -0.5f * (zk.x - zc.x));
                 V[e] = Vb[ky * KXP + k];
@@ -536,7 +582,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT3)
                  float* __restrict__ m_out, float* __restrict__ w_out, float* __restrict__ G,
                  const float2* __restrict__ twg) {
     constexpr int NT = Cfg<H>::NT3, KXP = kxp<H>(), HK = H / 2 + 1, RP = rowp<H>();
-    constexpr int R1 = Radix<H>::R1, R2 = Radix<H>::R2;
+    constexpr int R1 = Radix<H>::R1;
     static_assert(H * RP <= 2 * H * KXP, "packed rows must fit in B0/B1");
     extern __shared__ float2 sm[];
     float2* B0 = sm;              // [H][KXP]
@@ -560,17 +606,17 @@ __global__ void __launch_bounds__(Cfg<H>::NT3)
         stage1_from<H, R1, HK, KXP, 1, NT, +1>(B1, PlaneLoad{gV + pbase, KXP, k, k, H, 2});
         stage1_from<H, R1, HK, KXP, 1, NT, +1>(B2, PlaneLoad{gB + pbase, KXP, 0.f, 0.f, H, 0});
     }
-    stage<H, R2, R1, HK, KXP, 1, NT, +1>(B0, tw);
-    stage<H, R2, R1, HK, KXP, 1, NT, +1>(B1, tw);
-    if (group == 1) stage<H, R2, R1, HK, KXP, 1, NT, +1>(B2, tw);
+    fft_rest<H, HK, KXP, 1, NT, +1>(B0, tw);
+    fft_rest<H, HK, KXP, 1, NT, +1>(B1, tw);
+    if (group == 1) fft_rest<H, HK, KXP, 1, NT, +1>(B2, tw);
     // inverse x: first stage from the packed half spectra (in place), second stage
     if (group == 1) {
         // B2's rows in pairs -> Z2 (B2's own space); done first, B0/B1 are still intact
         stage1_from<H, R1, H / 2, 1, RP, NT, +1>(Z2, PackLoad<H>{B2, B2 + KXP, 2 * KXP, 2 * KXP});
     }
     stage1_from<H, R1, H, 1, RP, NT, +1>(Z, PackLoad<H>{B0, B1, KXP, KXP});
-    stage<H, R2, R1, H, 1, RP, NT, +1>(Z, tw);
-    if (group == 1) stage<H, R2, R1, H / 2, 1, RP, NT, +1>(Z2, tw);
+    fft_rest<H, H, 1, RP, NT, +1>(Z, tw);
+    if (group == 1) fft_rest<H, H / 2, 1, RP, NT, +1>(Z2, tw);
     const size_t plane = static_cast<size_t>(z) * H * H;
     float* Gp = G + 4 * plane;
     if (group == 0) {
@@ -668,7 +714,7 @@ __global__ void __launch_bounds__(kSxNT)
             if (idx < NS) {
                 const int pr = idx / HK, k = idx % HK;
                 const float2 zp = buf[pr * RP + k];
-                const float2 zm = buf[pr * RP + ((H - k) & (H - 1))];
+                const float2 zm = buf[pr * RP + neg_mod<H>(k)];
                 x1[t] = make_float2(0.5f * (zp.x + zm.x), 0.5f * (zp.y - zm.y));
                 x2[t] = make_float2(0.5f * (zp.y + zm.y), -0.5f * (zp.x - zm.x));
             }
@@ -885,10 +931,17 @@ cudaError_t spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass) {
 
 cudaError_t launch_spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass) {
     switch (c->H) {
+        case 8: return spectral_pass<8>(c, a, pass);
         case 16: return spectral_pass<16>(c, a, pass);
+        case 24: return spectral_pass<24>(c, a, pass);
         case 32: return spectral_pass<32>(c, a, pass);
+        case 48: return spectral_pass<48>(c, a, pass);
         case 64: return spectral_pass<64>(c, a, pass);
+        case 72: return spectral_pass<72>(c, a, pass);
+        case 96: return spectral_pass<96>(c, a, pass);
         case 128: return spectral_pass<128>(c, a, pass);
+        case 144: return spectral_pass_split<144>(c, a, pass);
+        case 192: return spectral_pass_split<192>(c, a, pass);
         case 256: return spectral_pass_split<256>(c, a, pass);
         default: return cudaErrorInvalidValue;
     }

@@ -775,6 +775,10 @@ __global__ void k_component(const float4* __restrict__ G, int n, int comp, float
 }
 
 // Diagnostics: deterministic two-level reduction (fixed grid, fixed trees).
+// The particle mass is summed exactly, as 128-bit fixed point: each
+// a_p / exp(logref) times 2^K (K chosen on the host so that a term stays
+// below 2^62) rounded to an integer, so the total does not depend on the
+// order in which the particles are stored.
 constexpr int kDiagBlocks = 304;
 constexpr int kDiagNT = 256;
 
@@ -785,12 +789,13 @@ __global__ void __launch_bounds__(kDiagNT)
                     const float* __restrict__ sy, const float* __restrict__ sz, int N,
                     const float* __restrict__ v, const float* __restrict__ m,
                     const float* __restrict__ w, const unsigned long long* __restrict__ acc,
-                    int ncell, double* __restrict__ part_d, long long* __restrict__ part_l) {
-    double mass = 0.0, mv = INFINITY, mm = INFINITY, mw = INFINITY, nf = 0.0;
+                    int ncell, int K, double* __restrict__ part_d, long long* __restrict__ part_l) {
+    double mv = INFINITY, mm = INFINITY, mw = INFINITY, nf = 0.0;
+    unsigned __int128 mass = 0;
     long long as = 0, amin = LLONG_MAX;
     const int stride = kDiagBlocks * kDiagNT;
     for (int i = blockIdx.x * kDiagNT + threadIdx.x; i < N; i += stride) {
-        mass += exp(dl[i] + logref);
+        mass += __double2ull_rn(scalbn(exp(dl[i]), K));
         if (!isfinite(sx[i]) || !isfinite(sy[i]) || !isfinite(sz[i])) nf += 1.0;
     }
     for (int i = blockIdx.x * kDiagNT + threadIdx.x; i < ncell; i += stride) {
@@ -805,7 +810,9 @@ __global__ void __launch_bounds__(kDiagNT)
     }
     __shared__ double sd[5][kDiagNT];
     __shared__ long long sl[2][kDiagNT];
-    sd[0][threadIdx.x] = mass;
+    __shared__ unsigned __int128 sq[kDiagNT];
+    sq[threadIdx.x] = mass;
+    sd[0][threadIdx.x] = 0.0;
     sd[1][threadIdx.x] = mv;
     sd[2][threadIdx.x] = mm;
     sd[3][threadIdx.x] = mw;
@@ -816,7 +823,7 @@ __global__ void __launch_bounds__(kDiagNT)
     for (int s = kDiagNT / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) {
             const int j = threadIdx.x + s;
-            sd[0][threadIdx.x] += sd[0][j];
+            sq[threadIdx.x] += sq[j];
             sd[1][threadIdx.x] = dmin(sd[1][threadIdx.x], sd[1][j]);
             sd[2][threadIdx.x] = dmin(sd[2][threadIdx.x], sd[2][j]);
             sd[3][threadIdx.x] = dmin(sd[3][threadIdx.x], sd[3][j]);
@@ -828,26 +835,32 @@ __global__ void __launch_bounds__(kDiagNT)
     }
     if (threadIdx.x == 0) {
         for (int k = 0; k < 5; ++k) part_d[blockIdx.x * 5 + k] = sd[k][0];
-        part_l[blockIdx.x * 2] = sl[0][0];
-        part_l[blockIdx.x * 2 + 1] = sl[1][0];
+        part_l[blockIdx.x * 4] = sl[0][0];
+        part_l[blockIdx.x * 4 + 1] = sl[1][0];
+        part_l[blockIdx.x * 4 + 2] = static_cast<long long>(static_cast<uint64_t>(sq[0]));
+        part_l[blockIdx.x * 4 + 3] = static_cast<long long>(static_cast<uint64_t>(sq[0] >> 64));
     }
 }
 
 __global__ void k_diag_final(const double* __restrict__ part_d, const long long* __restrict__ part_l,
-                             double acc_to_u, double* __restrict__ out) {
+                             double acc_to_u, int K, double logref, double* __restrict__ out) {
     if (threadIdx.x != 0) return;
-    double mass = 0, mv = INFINITY, mm = INFINITY, mw = INFINITY, nf = 0;
+    double mv = INFINITY, mm = INFINITY, mw = INFINITY, nf = 0;
+    unsigned __int128 mass = 0;
     long long as = 0, amin = LLONG_MAX;
     for (int b = 0; b < kDiagBlocks; ++b) {
-        mass += part_d[b * 5];
         mv = dmin(mv, part_d[b * 5 + 1]);
         mm = dmin(mm, part_d[b * 5 + 2]);
         mw = dmin(mw, part_d[b * 5 + 3]);
         nf += part_d[b * 5 + 4];
-        as += part_l[b * 2];
-        amin = part_l[b * 2 + 1] < amin ? part_l[b * 2 + 1] : amin;
+        as += part_l[b * 4];
+        amin = part_l[b * 4 + 1] < amin ? part_l[b * 4 + 1] : amin;
+        mass += (static_cast<unsigned __int128>(static_cast<uint64_t>(part_l[b * 4 + 3])) << 64) |
+                static_cast<uint64_t>(part_l[b * 4 + 2]);
     }
-    out[0] = mass;
+    const double mass_d = static_cast<double>(static_cast<uint64_t>(mass >> 64)) * 18446744073709551616.0 +
+                          static_cast<double>(static_cast<uint64_t>(mass));
+    out[0] = scalbn(mass_d, -K) * exp(logref);
     out[1] = static_cast<double>(as) * acc_to_u;   // sum of u_bar (times h^3 on the host)
     out[2] = static_cast<double>(amin) * acc_to_u;
     out[3] = mv;
@@ -1016,11 +1029,16 @@ cudaError_t launch_component(sipf_ctx* c, int comp, float* dst) {
 }
 
 cudaError_t launch_diagnostics(sipf_ctx* c, int b, double acc_to_u) {
+    // a_p / exp(logref) <= maxrel e^time (growth factor of a step < e^tau)
+    const double bound = log2(c->maxrel) + c->time * 1.4426950408889634 + 1.0;
+    int K = 61 - static_cast<int>(ceil(bound));
+    K = K < -900 ? -900 : (K > 900 ? 900 : K);
     k_diag_partials<<<kDiagBlocks, kDiagNT, 0, c->stream>>>(
         c->dl[b], c->logref, c->sx[b], c->sy[b], c->sz[b], static_cast<int>(c->N), c->v, c->m,
-        c->w, reinterpret_cast<const unsigned long long*>(c->acc), c->H * c->H * c->H, c->diag_tmp,
-        c->diag_ll);
-    k_diag_final<<<1, 32, 0, c->stream>>>(c->diag_tmp, c->diag_ll, acc_to_u, c->diag_out);
+        c->w, reinterpret_cast<const unsigned long long*>(c->acc), c->H * c->H * c->H, K,
+        c->diag_tmp, c->diag_ll);
+    k_diag_final<<<1, 32, 0, c->stream>>>(c->diag_tmp, c->diag_ll, acc_to_u, K, c->logref,
+                                          c->diag_out);
     return cudaGetLastError();
 }
 
@@ -1039,7 +1057,7 @@ cudaError_t launch_conv_check(const float* f, const double* d, int n, int* misma
 }
 
 size_t diag_scratch_doubles() { return static_cast<size_t>(kDiagBlocks) * 5; }
-size_t diag_scratch_ll() { return static_cast<size_t>(kDiagBlocks) * 2; }
+size_t diag_scratch_ll() { return static_cast<size_t>(kDiagBlocks) * 4; }
 int scan_tiles(int n) { return (n + kScanTile - 1) / kScanTile; }
 int item_size() { return kItem; }
 

@@ -35,7 +35,8 @@ EXPORTED = (
     "sipf_particle_state", "sipf_cell_start", "sipf_diagnostics", "sipf_sync",
     "sipf_destroy", "sipf_strerror", "sipf_last_error", "sipf_brownian_normals",
     "sipf_profile", "sipf_profile_read", "sipf_profile_name", "sipf_check_conversions",
-    "sipf_deposit_noalloc",
+    "sipf_deposit_noalloc", "sipf_save", "sipf_load",
+    "sipf_describe",
 )
 PROFILE_GROUPS = 4
 
@@ -98,6 +99,11 @@ def load() -> ctypes.CDLL:
         "sipf_profile_name": ([I32], ctypes.c_char_p),
         "sipf_check_conversions": ([P, P, I64, P, P], I32),
         "sipf_deposit_noalloc": ([ctypes.POINTER(sipf_grid), P, P, I64, P, P], I32),
+        "sipf_save": ([P, ctypes.c_char_p], I32),
+        "sipf_describe": ([P, ctypes.POINTER(sipf_grid), ctypes.POINTER(I64),
+                           ctypes.POINTER(sipf_params), ctypes.POINTER(I64),
+                           ctypes.POINTER(ctypes.c_double)], I32),
+        "sipf_load": ([ctypes.c_char_p, P, ctypes.POINTER(P)], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -184,6 +190,26 @@ def sipf_destroy(ctx):
         load().sipf_destroy(ctx)
 
 
+def sipf_save(ctx, path: str):
+    _check(load().sipf_save(ctx, os.fsencode(path)), ctx)
+
+
+def sipf_load(path: str, stream: int = 0) -> int:
+    out = ctypes.c_void_p()
+    _check(load().sipf_load(os.fsencode(path), ctypes.c_void_p(stream or None), ctypes.byref(out)))
+    return out.value
+
+
+def sipf_describe(ctx) -> dict:
+    g, n, p = sipf_grid(), ctypes.c_int64(), sipf_params()
+    step, time = ctypes.c_int64(), ctypes.c_double()
+    _check(load().sipf_describe(ctx, ctypes.byref(g), ctypes.byref(n), ctypes.byref(p),
+                                ctypes.byref(step), ctypes.byref(time)), ctx)
+    return {"H": g.H, "L": g.L, "origin": tuple(g.origin), "N": n.value,
+            "params": {k: getattr(p, k) for k, _ in sipf_params._fields_},
+            "step": step.value, "time": time.value}
+
+
 def sipf_brownian_normals(ids_dev, N: int, n: int, seed: int, z_dev, bits_dev=None, stream=0):
     _check(load().sipf_brownian_normals(_ptr(ids_dev), int(N), int(n), int(seed), _ptr(z_dev),
                                         _ptr(bits_dev), ctypes.c_void_p(stream or None)))
@@ -242,9 +268,20 @@ def make_params(p) -> sipf_params:
 class Simulation:
     """Owns one context; host NumPy in and out (SoA conversions included)."""
 
-    def __init__(self, H, L, origin, N, params, stream: int = 0):
+    def __init__(self, H, L, origin, N, params, stream: int = 0, _ctx=None):
         self.H, self.L, self.N = H, L, N
-        self.ctx = sipf_create(make_grid(H, L, origin), N, make_params(params), stream)
+        self.ctx = _ctx if _ctx is not None else sipf_create(make_grid(H, L, origin), N,
+                                                             make_params(params), stream)
+
+    @classmethod
+    def load(cls, path: str, stream: int = 0) -> "Simulation":
+        """A simulation resumed from a checkpoint written by save()."""
+        ctx = sipf_load(path, stream)
+        d = sipf_describe(ctx)
+        return cls(d["H"], d["L"], d["origin"], d["N"], None, _ctx=ctx)
+
+    def save(self, path: str):
+        sipf_save(self.ctx, path)
 
     def close(self):
         if self.ctx:

@@ -78,7 +78,8 @@ def _create(lib, H=32, L=1.0, N=100, **kw):
 @pytest.mark.parametrize("kw,code", [
     (dict(N=0), sipf.SIPF_EINVAL),
     (dict(N=1 << 31), sipf.SIPF_EINVAL),
-    (dict(H=48), sipf.SIPF_EINVAL),
+    (dict(H=40), sipf.SIPF_EINVAL),
+    (dict(H=36), sipf.SIPF_EINVAL),
     (dict(H=12), sipf.SIPF_EINVAL),
     (dict(H=512), sipf.SIPF_EINVAL),
     (dict(L=0.0), sipf.SIPF_EINVAL),
@@ -101,3 +102,15 @@ def test_null_arguments_and_strerror(lib):
     for code in (0, -1, -2, -3, -4, -6, -7):
         assert lib.sipf_strerror(code)
     assert lib.sipf_last_error(None) == b""
+
+
+def test_load_rejects_missing_and_foreign_files_without_touching_the_gpu(lib, tmp_path):
+    out = ctypes.c_void_p()
+    assert lib.sipf_load(b"/nonexistent/dir/state.sipf", None, ctypes.byref(out)) == sipf.SIPF_EINVAL
+    junk = tmp_path / "junk.sipf"
+    junk.write_bytes(b"not a checkpoint" * 64)
+    assert lib.sipf_load(os.fsencode(str(junk)), None, ctypes.byref(out)) == sipf.SIPF_EINVAL
+    assert out.value is None
+    assert lib.sipf_load(None, None, ctypes.byref(out)) == sipf.SIPF_EINVAL
+    assert lib.sipf_save(None, b"x") == sipf.SIPF_EINVAL
+    assert lib.sipf_describe(None, None, None, None, None, None) == sipf.SIPF_EINVAL

@@ -142,6 +142,32 @@ def test_binning_cell_offsets_and_sets_bit_exact(H):
     np.testing.assert_array_equal(got_sorted, ref_sorted)
 
 
+@pytest.mark.parametrize("H", [24, 48, 96])
+def test_binning_radix3_grids_bit_exact(H):
+    """On grids that are not powers of two, s = (x - x_min)/h is rounded; the
+    cell decision is compared with the oracle's keys of the same float32 s
+    (IEEE single division, as the kernel does it)."""
+    wl = workload("small", H=H, N=1 << 14)
+    sim = run_gpu(wl, 0)
+    s, loga, ids = sim.particle_state()
+    cs = sim.cell_start()
+    sim.close()
+    h32, H32 = np.float32(wl.L / H), np.float32(H)
+    s32 = (wl.x - np.float32(0.0)) / h32
+    # periodic wrap in float32: s - H floor(s / H), then into [0, H)
+    out = (s32 < 0) | (s32 >= H32)
+    r = (s32 - H32 * np.floor(s32 / H32)).astype(np.float32)
+    r = np.where(r < 0, r + H32, r).astype(np.float32)
+    r = np.where(r < H32, r, np.float32(0.0)).astype(np.float32)
+    s32 = np.where(out, r, s32).astype(np.float32)
+    s_id, _, i_id = by_id(s, loga, ids)
+    np.testing.assert_array_equal(s_id, s32)
+    keys = O.cell_keys(s32.astype(np.float64), H)
+    np.testing.assert_array_equal(cs.astype(np.int64), O.cell_start(keys, H))
+    gkeys = O.cell_keys(s.astype(np.float64), H)
+    assert np.all(np.diff(gkeys >> 9) >= 0)
+
+
 def test_binning_after_a_step_without_motion_is_bit_exact():
     """chi = Du = 0: the push leaves positions unchanged, so the count and
     scatter passes of a real step must rebuild exactly the oracle's cells."""
@@ -179,7 +205,7 @@ def test_deposit_matches_oracle_and_conserves_mass(name, H, N):
     assert abs(d["mass_particles"] - wl.mass.sum()) <= 1e-12 * wl.mass.sum()
 
 
-@pytest.mark.parametrize("H", [16, 32, 64, 128, 256])
+@pytest.mark.parametrize("H", [8, 16, 24, 32, 48, 64, 72, 96, 128, 144, 192, 256])
 def test_initial_spectral_gradient(H):
     wl = workload("small", H=H, N=1024)
     sim = run_gpu(wl, 0)
@@ -208,7 +234,8 @@ def test_gradient_of_a_sine_mode_closed_form():
         assert np.max(np.abs(f[name] - ref)) <= 1e-5 * np.abs(ref).max(), name
 
 
-@pytest.mark.parametrize("mode,H", [(0, 32), (1, 32), (0, 256)])
+@pytest.mark.parametrize("mode,H", [(0, 32), (1, 32), (0, 256), (0, 48), (1, 72), (0, 96),
+                                    (0, 144), (1, 192)])
 def test_single_mode_decay(mode, H):
     """Massless particles, gamma = alpha = 0: one step multiplies a Fourier
     mode of m by 1/(1 + tau beta + tau Dm |k|^2) (or the exponential) and of
@@ -302,6 +329,16 @@ def test_hundred_steps_match_oracle_small_workload():
     tol_m = wl.dt * wl.steps * 2.0 * FIELD_TOL * float(np.abs(st.w).max())
     assert abs(d["mass_particles"] - od["mass_particles"]) <= tol_m * od["mass_particles"]
     print("rel-L2 after 100 steps:", {k: f"{v:.2e}" for k, v in errs.items()})
+
+
+@pytest.mark.parametrize("H", [24, 48, 96])
+def test_steps_match_oracle_radix3_grids(H):
+    """Grids 2^a 3^b (radix-3 DFT stages): ten steps against the oracle."""
+    wl = workload("small", H=H, N=1 << 15)
+    sim = run_gpu(wl, 10)
+    st = O.run(oracle_state(wl), wl.dt, 10)
+    _compare(sim, st, wl)
+    sim.close()
 
 
 def test_hundred_steps_match_oracle_64_grid():
@@ -459,6 +496,15 @@ def test_integer_float_double_conversions_match_hardware():
     out = torch.zeros(2, dtype=torch.int32, device="cuda")
     sipf.sipf_check_conversions(fd, dd, m, out)
     assert out.cpu().tolist() == [0, 0]
+
+
+def test_two_steps_match_oracle_192_grid():
+    """The per-axis pipeline with a radix-3 stage (192 = 16 * 4 * 3)."""
+    wl = workload("small", H=192, N=1 << 18)
+    sim = run_gpu(wl, 2)
+    st = O.run(oracle_state(wl), wl.dt, 2)
+    _compare(sim, st, wl)
+    sim.close()
 
 
 def test_two_steps_match_oracle_256_grid():
