@@ -168,6 +168,24 @@ int sipf_diagnostics(sipf_ctx* ctx, sipf_diag* out);
 /* Wait for the context's stream and return any deferred device error. */
 int sipf_sync(sipf_ctx* ctx);
 
+/* Residual resampling (paper Alg. 4): the particles are replaced by N
+ * equal-weight particles.  Particle p (in id order) is copied k_p =
+ * floor(a_p / a_0) times, a_0 = (sum a_p) / N, and the remaining
+ * N - sum k_p particles are drawn independently with probabilities
+ * proportional to the residuals a_p - k_p a_0 (Philox4x32-10, key = seed,
+ * counter (step, 1, draw, 0)).  The integer decisions use the masses in
+ * 31-bit fixed point relative to the largest, so they are exact; the new
+ * particles carry the ids 0..N-1 in the order (copies in order of p, then
+ * draws) and the mass a_0 of the exact fixed-point total.  Resamples only when
+ * max a_p > ratio * min a_p (ratio <= 0: always); *resampled (may be NULL)
+ * receives 1 if it did.  Requires the ids to be a permutation of 0..N-1
+ * (true for ids assigned by sipf_set_state with id = NULL and after a
+ * resampling).  Synchronises.  Uses about 40 N bytes of work space, allocated
+ * on the first call and kept by the context.  Errors: SIPF_EINVAL (no state,
+ * ratio not finite, ids not a permutation, all masses zero), SIPF_ENONFINITE
+ * (a mass is not finite), SIPF_ENOMEM, SIPF_ECUDA. */
+int sipf_resample(sipf_ctx* ctx, double ratio, int32_t* resampled);
+
 /* Checkpoint / resume.  The paper has no checkpoint; what is saved is the
  * state of the scheme after step n of Alg. 3: the particles X^n (grid units)
  * with log a^n and ids, the grids v^n, m^n, w^n and the gather array

@@ -75,7 +75,7 @@ void free_all(sipf_ctx* c) {
                     c->work, c->count, c->cell_start, c->scan_tmp, c->acc, c->v, c->m, c->w,
                     c->G, c->specM, c->specW, c->specV, c->specB, c->specA, c->specDx,
                     c->specDy, c->twiddle,
-                    c->status, c->diag_tmp, c->diag_out, c->diag_ll, c->voff};
+                    c->status, c->diag_tmp, c->diag_out, c->diag_ll, c->voff, c->rs_scratch};
     for (void* q : ptrs)
         if (q) cudaFree(q);
 }
@@ -185,21 +185,23 @@ SpectralArgs spectral_args(const sipf_ctx* c, double dt, float react_scale, int 
     return s;
 }
 
-// Bin the unbinned particles of buffer 1 into tile buckets of buffer 0, and
-// plan the items of buffer 0 and the layout of buffer 1.
-int bin_initial(sipf_ctx* c) {
-    SIPF_CUDA(c, cudaMemsetAsync(c->cnt[1], 0, sizeof(int) * c->ntiles, c->stream));
-    SIPF_CUDA(c, cudaMemsetAsync(c->ovf[1], 0, sizeof(int), c->stream));
-    SIPF_CUDA(c, launch_tile_count(c, 1, c->cnt[1]));
-    SIPF_CUDA(c, launch_plan(c, 1, 1, c->stream));   // layout of buffer 0 from the tile counts
+// Bin the unbinned particles of buffer b (slots [0, N)) into tile buckets of
+// buffer b ^ 1, and plan the items of b ^ 1 and the layout of b.
+int bin_from(sipf_ctx* c, int b) {
+    SIPF_CUDA(c, cudaMemsetAsync(c->cnt[b], 0, sizeof(int) * c->ntiles, c->stream));
+    SIPF_CUDA(c, cudaMemsetAsync(c->ovf[b], 0, sizeof(int), c->stream));
+    SIPF_CUDA(c, launch_tile_count(c, b, c->cnt[b]));
+    SIPF_CUDA(c, launch_plan(c, b, 1, c->stream));   // layout of buffer b ^ 1 from the tile counts
     SIPF_CUDA(c, launch_plan_flat(c));           // items: the raw input array
-    c->cur = 1;
+    c->cur = b;
     const PushArgs a = push_args(c, 0.0, 0, 0);
     SIPF_CUDA(c, launch_step_kernel(c, a, deposit_args(c), 0, 1));
-    c->cur = 0;
-    SIPF_CUDA(c, launch_plan(c, 0, 1, c->stream));
+    c->cur = b ^ 1;
+    SIPF_CUDA(c, launch_plan(c, b ^ 1, 1, c->stream));
     return SIPF_OK;
 }
+
+int bin_initial(sipf_ctx* c) { return bin_from(c, 1); }
 
 // Deposit the current particles into the accumulator (Alg. 1).
 int deposit_current(sipf_ctx* c) {
@@ -833,6 +835,30 @@ int sipf_load(const char* path, void* stream, sipf_ctx** out) {
     }
     c->state_set = true;
     *out = c;
+    return SIPF_OK;
+}
+
+int sipf_resample(sipf_ctx* c, double ratio, int32_t* resampled) {
+    if (!c) return SIPF_EINVAL;
+    if (resampled) *resampled = 0;
+    if (!c->state_set) return fail(c, SIPF_EINVAL, "sipf_set_state has not been called");
+    if (!isfinite(ratio)) return fail(c, SIPF_EINVAL, "ratio must be finite");
+    // compacted particles in the free buffer; the binned one is then free too
+    int r = compact_current(c);
+    if (r != SIPF_OK) return r;
+    const int src = c->cur ^ 1, dst = c->cur;
+    int done = 0;
+    std::string why;
+    r = resample_device(c, src, dst, ratio, &done, &why);
+    if (r != SIPF_OK) return fail(c, r, "sipf_resample: " + why);
+    if (done) {
+        r = bin_from(c, dst);
+        if (r != SIPF_OK) return r;
+        SIPF_CUDA(c, cudaStreamSynchronize(c->stream));
+        r = check_status(c);
+        if (r != SIPF_OK) return r;
+    }
+    if (resampled) *resampled = done;
     return SIPF_OK;
 }
 

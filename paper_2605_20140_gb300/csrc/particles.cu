@@ -32,36 +32,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// ------------------------------------------------------------------ Philox
-// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
-// 32x32->64 multiplications with key mixing; the key advances by the Weyl
-// constants between rounds.  Each product is one wide multiply.
-__device__ __forceinline__ uint4 philox_round(uint4 c, uint32_t k0, uint32_t k1) {
-    const uint64_t p0 = static_cast<uint64_t>(0xD2511F53u) * c.x;
-    const uint64_t p1 = static_cast<uint64_t>(0xCD9E8D57u) * c.z;
-    return make_uint4(static_cast<uint32_t>(p1 >> 32) ^ c.y ^ k0, static_cast<uint32_t>(p1),
-                      static_cast<uint32_t>(p0 >> 32) ^ c.w ^ k1, static_cast<uint32_t>(p0));
-}
-
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r > 0) {
-            k0 += 0x9E3779B9u;
-            k1 += 0xBB67AE85u;
-        }
-        c = philox_round(c, k0, k1);
-    }
-    return c;
-}
-
-// The same generator with the ten round keys given (rk[2r], rk[2r+1]).
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const uint32_t (&rk)[20]) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) c = philox_round(c, rk[2 * r], rk[2 * r + 1]);
-    return c;
-}
-
 // (2 (b >> 9) + 1) 2^-24, in (0, 1): the float 1 + (b >> 9) 2^-23 minus
 // 1 - 2^-24; the difference has at most 24 significant bits, so it is exact.
 __device__ __forceinline__ float unit_open(uint32_t b) {

@@ -24,6 +24,36 @@ constexpr int kStatusTotal = 4;       // particle counts inconsistent
 constexpr int kProfGroups = 4;
 constexpr int kProfMaxSteps = 4096;
 
+// ------------------------------------------------------------------ Philox
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplications with key mixing; the key advances by the Weyl
+// constants between rounds.  Each product is one wide multiply.
+__device__ __forceinline__ uint4 philox_round(uint4 c, uint32_t k0, uint32_t k1) {
+    const uint64_t p0 = static_cast<uint64_t>(0xD2511F53u) * c.x;
+    const uint64_t p1 = static_cast<uint64_t>(0xCD9E8D57u) * c.z;
+    return make_uint4(static_cast<uint32_t>(p1 >> 32) ^ c.y ^ k0, static_cast<uint32_t>(p1),
+                      static_cast<uint32_t>(p0 >> 32) ^ c.w ^ k1, static_cast<uint32_t>(p0));
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        c = philox_round(c, k0, k1);
+    }
+    return c;
+}
+
+// The same generator with the ten round keys given (rk[2r], rk[2r+1]).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const uint32_t (&rk)[20]) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) c = philox_round(c, rk[2 * r], rk[2 * r + 1]);
+    return c;
+}
+
 // Per-step scalars of the particle kernels.
 struct PushArgs {
     int H;
@@ -134,6 +164,9 @@ struct sipf_ctx {
     float* voff = nullptr;           // device scalar: offset subtracted from v before its FFT
     int kxp = 0;
 
+    void* rs_scratch = nullptr;      // residual resampling work space (allocated on first use)
+    size_t rs_bytes = 0;
+
     int* status = nullptr;           // device status word
     double* diag_tmp = nullptr;      // diagnostics partials
     double* diag_out = nullptr;      // 8 doubles
@@ -181,6 +214,8 @@ cudaError_t launch_normals(const uint32_t* ids, int64_t N, uint32_t n, uint64_t 
                            uint32_t* bits, cudaStream_t s);
 cudaError_t launch_conv_check(const float* f, const double* d, int n, int* mismatches,
                               cudaStream_t s);
+// resample.cu
+int resample_device(sipf_ctx* c, int src, int dst, double ratio, int* done, std::string* err);
 // fft.cu
 cudaError_t launch_spectral_step(sipf_ctx* c, const SpectralArgs& a);
 cudaError_t launch_spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass);

@@ -36,7 +36,7 @@ EXPORTED = (
     "sipf_destroy", "sipf_strerror", "sipf_last_error", "sipf_brownian_normals",
     "sipf_profile", "sipf_profile_read", "sipf_profile_name", "sipf_check_conversions",
     "sipf_deposit_noalloc", "sipf_save", "sipf_load",
-    "sipf_describe",
+    "sipf_describe", "sipf_resample",
 )
 PROFILE_GROUPS = 4
 
@@ -100,6 +100,7 @@ def load() -> ctypes.CDLL:
         "sipf_check_conversions": ([P, P, I64, P, P], I32),
         "sipf_deposit_noalloc": ([ctypes.POINTER(sipf_grid), P, P, I64, P, P], I32),
         "sipf_save": ([P, ctypes.c_char_p], I32),
+        "sipf_resample": ([P, ctypes.c_double, ctypes.POINTER(ctypes.c_int32)], I32),
         "sipf_describe": ([P, ctypes.POINTER(sipf_grid), ctypes.POINTER(I64),
                            ctypes.POINTER(sipf_params), ctypes.POINTER(I64),
                            ctypes.POINTER(ctypes.c_double)], I32),
@@ -200,6 +201,13 @@ def sipf_load(path: str, stream: int = 0) -> int:
     return out.value
 
 
+def sipf_resample(ctx, ratio: float = 0.0) -> bool:
+    """Residual resampling (Alg. 4) when max/min mass > ratio; True if done."""
+    done = ctypes.c_int32(0)
+    _check(load().sipf_resample(ctx, float(ratio), ctypes.byref(done)), ctx)
+    return bool(done.value)
+
+
 def sipf_describe(ctx) -> dict:
     g, n, p = sipf_grid(), ctypes.c_int64(), sipf_params()
     step, time = ctypes.c_int64(), ctypes.c_double()
@@ -282,6 +290,9 @@ class Simulation:
 
     def save(self, path: str):
         sipf_save(self.ctx, path)
+
+    def resample(self, ratio: float = 0.0) -> bool:
+        return sipf_resample(self.ctx, ratio)
 
     def close(self):
         if self.ctx:
