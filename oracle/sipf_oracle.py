@@ -33,7 +33,11 @@ Readings of the paper taken here (where it is silent or inconsistent):
   when on it multiplies the m and w spectra and the v spectrum used for
   grad v, never the stored v.
 * Deposit: u_bar(qh) = sum_p a_p R_h(X_p, qh) (Alg. 1; the extra factor
-  u_hat(X_p) printed in Eq. def_u_overline is read as a typo).
+  u_hat(X_p) printed in Eq. def_u_overline is read as a typo).  R_h is the
+  trilinear function, or (p2g_order = 4) the fourth-order R_h^(4) of
+  Sec. 2.2.1, whose printed cases leave nodes with two or more distances above
+  1 at weight 0; the grid-to-particle interpolation stays trilinear
+  (Theorem overall: fourth-order P2G, second-order G2P).
 * Mass update a <- a (1 + tau rho(w_H) - tau) (Eq. u_hat_update) held as
   log a <- log a + log1p(tau (rho(w_H) - 1)).
 * Brownian increments: W = sqrt(2 Du tau) z, z from Philox4x32-10 (Salmon et
@@ -172,6 +176,54 @@ def deposit(s: np.ndarray, a: np.ndarray, H: int, h: float) -> np.ndarray:
     for idx, wgt in _corner_terms(s, H):
         u += np.bincount(idx, weights=a * wgt, minlength=H ** 3)
     return (u / h ** 3).reshape(H, H, H)
+
+
+def r4_weight(p1, p2, p3):
+    """h^3 R_h^(4) (Sec. 2.2.1, the fourth-order assignment function) as a
+    function of the per-axis distances p_j = |x_j - q_j h| / h, case by case:
+    all p_j <= 1: prod_j (1 - p_j) (1 + sum_j p_j (1 - p_j) / 2);
+    one p_j in (1, 2], the others <= 1:
+        -(1/6) prod_{k != j} (1 - p_k) (p_j - 1)(2 - p_j)(3 - p_j);
+    otherwise 0."""
+    p = [np.asarray(x, dtype=np.float64) for x in (p1, p2, p3)]
+    near = [x <= 1.0 for x in p]
+    mid = [(x > 1.0) & (x <= 2.0) for x in p]
+    w = np.zeros(np.broadcast(*p).shape)
+    core = near[0] & near[1] & near[2]
+    w = np.where(core, (1 - p[0]) * (1 - p[1]) * (1 - p[2]) *
+                 (1 + (p[0] * (1 - p[0]) + p[1] * (1 - p[1]) + p[2] * (1 - p[2])) / 2), w)
+    for j in range(3):
+        k, l = [i for i in range(3) if i != j]
+        arm = mid[j] & near[k] & near[l]
+        w = np.where(arm, -(1 - p[k]) * (1 - p[l]) * (p[j] - 1) * (2 - p[j]) * (3 - p[j]) / 6, w)
+    return w
+
+
+def deposit4(s: np.ndarray, a: np.ndarray, H: int, h: float) -> np.ndarray:
+    """Alg. 1 with the fourth-order assignment function R_h^(4): every node
+    q with offset d in {-1, 0, 1, 2}^3 from the particle's cell is tried and
+    weighted by r4_weight of its distances (32 of the 64 are non-zero)."""
+    c = cells(s)
+    u = np.zeros(H ** 3)
+    for dz in (-1, 0, 1, 2):
+        for dy in (-1, 0, 1, 2):
+            for dx in (-1, 0, 1, 2):
+                q = c + np.array([dx, dy, dz])
+                d = np.abs(s - q)
+                wgt = r4_weight(d[:, 0], d[:, 1], d[:, 2])
+                qq = q % H
+                idx = (qq[:, 2] * H + qq[:, 1]) * H + qq[:, 0]
+                u += np.bincount(idx, weights=a * wgt, minlength=H ** 3)
+    return (u / h ** 3).reshape(H, H, H)
+
+
+def deposit_order(s: np.ndarray, a: np.ndarray, H: int, h: float, order: int) -> np.ndarray:
+    """u_bar with the trilinear (order 2) or the fourth-order assignment."""
+    if order == 4:
+        return deposit4(s, a, H, h)
+    if order != 2:
+        raise ValueError("p2g_order must be 2 or 4")
+    return deposit(s, a, H, h)
 
 
 def gather(f: np.ndarray, s: np.ndarray) -> np.ndarray:
@@ -329,7 +381,7 @@ def make_state(H, L, origin, p, x, mass, ids, v, m, w) -> State:
 
 def density(st: State) -> np.ndarray:
     """u_bar of the current particles (Alg. 1)."""
-    return deposit(st.s, st.mass, st.H, st.h)
+    return deposit_order(st.s, st.mass, st.H, st.h, getattr(st.p, "p2g_order", 2))
 
 
 def step(st: State, tau: float, normals: np.ndarray | None = None) -> State:
@@ -338,8 +390,9 @@ def step(st: State, tau: float, normals: np.ndarray | None = None) -> State:
     p, H, h, L = st.p, st.H, st.h, st.L
     n = st.n + 1
     a = st.mass
-    # Alg. 1: u_bar^(n-1) on the nodes from (X^(n-1), a^(n-1)).
-    ubar = deposit(st.s, a, H, h)
+    # Alg. 1: u_bar^(n-1) on the nodes from (X^(n-1), a^(n-1)); the gather
+    # stays trilinear for either assignment order (Theorem overall).
+    ubar = deposit_order(st.s, a, H, h, getattr(p, "p2g_order", 2))
     # Alg. 2 / Eq. g2ph: grad v_H^(n-1) and w_H^(n-1) at X^(n-1).
     g = np.stack([gather(st.grad_v[d], st.s) for d in range(3)], axis=1)
     w_H = gather(st.w, st.s)

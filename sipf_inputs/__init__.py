@@ -64,6 +64,7 @@ class Params:
     v_update: int = 0       # 0 implicit v/(1+alpha tau m), 1 explicit v(1-alpha tau m)
     H0: float = 0.0         # low-pass filter cut-off; 0 (or >= H) means off
     seed: int = 0           # Philox key for the Brownian increments
+    p2g_order: int = 2      # particle-to-grid assignment: 2 trilinear, 4 the star stencil R^(4)
 
 
 @dataclasses.dataclass

@@ -425,3 +425,62 @@ def test_advance_particles_is_the_particle_part_of_a_step():
     st1 = O.step(st, wl.dt)
     np.testing.assert_array_equal(s_new, st1.s[idx])
     np.testing.assert_array_equal(l_new, st1.loga[idx])
+
+
+# ---------------------------------------------------------------- fourth-order assignment R^(4)
+
+def _single_particle_weights(x, H=16):
+    """Node weights h^3 R^(4)(x, q) of one unit-mass particle at x (grid units)
+    on an H^3 grid with h = 1, as an (H, H, H) array."""
+    return O.deposit4(np.asarray([x], dtype=np.float64), np.ones(1), H, 1.0)
+
+
+def test_r4_worked_values_at_a_cell_centre():
+    # p = (1/2, 1/2, 1/2) at the 8 corners: (1/8)(1 + 3/8) = 0.171875;
+    # at a star node p = (3/2, 1/2, 1/2): -(1/6)(1/4)(1/2)(1/2)(3/2) = -0.015625
+    u = _single_particle_weights([7.5, 7.5, 7.5])
+    assert u[7, 7, 7] == 0.171875 and u[8, 8, 8] == 0.171875
+    assert u[7, 7, 6] == -0.015625 and u[8, 7, 9] == -0.015625
+    assert u[6, 6, 7] == 0.0                      # two distances above 1
+    assert np.count_nonzero(u) == 32
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_r4_reproduces_polynomials_up_to_degree_three(seed):
+    rng = np.random.default_rng(seed)
+    for _ in range(20):
+        x = rng.uniform(6.0, 9.0, 3)
+        u = _single_particle_weights(x)
+        idx = np.nonzero(u)
+        w = u[idx]
+        dz, dy, dx = (np.asarray(i, dtype=np.float64) - x[k] for i, k in zip(idx, (2, 1, 0)))
+        assert np.count_nonzero(u) == 32
+        for a in range(5):
+            for b in range(5 - a):
+                for c in range(5 - a - b):
+                    m = np.sum(w * dx ** a * dy ** b * dz ** c)
+                    want = 1.0 if a + b + c == 0 else 0.0
+                    if a + b + c <= 3:
+                        assert abs(m - want) <= 1e-12, (a, b, c, m)
+        # not an accident of degree 4: the fourth x-moment is non-zero
+        assert abs(np.sum(w * dx ** 4)) > 1e-3
+
+
+def test_r4_on_a_node_plane_is_cubic_lagrange_interpolation():
+    nodes = np.array([-1.0, 0.0, 1.0, 2.0])
+    for f in (0.1, 0.25, 0.5, 0.8):
+        u = _single_particle_weights([7.0 + f, 7.0, 7.0])
+        for i, xi in enumerate(nodes):
+            others = np.delete(nodes, i)
+            ell = np.prod((f - others) / (xi - others))
+            assert abs(u[7, 7, 7 + int(xi)] - ell) <= 1e-14
+        assert np.count_nonzero(np.abs(u) > 1e-15) == 4
+
+
+def test_r4_deposit_conserves_mass():
+    rng = np.random.default_rng(4)
+    H = 16
+    s = rng.uniform(0, H, (500, 3))
+    a = rng.uniform(0.5, 2.0, 500)
+    u = O.deposit4(s, a, H, 0.25)
+    assert abs(u.sum() * 0.25 ** 3 - a.sum()) <= 1e-12 * a.sum()
