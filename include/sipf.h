@@ -86,13 +86,20 @@ typedef struct {
 /* Model and scheme parameters (paper Eq. haptotaxis-system; all >= 0 and
  * finite).  H0: low-pass cut-off exp(-2 pi^2 |q|^2 / H0^2) of Alg. 3 applied
  * to the m, w spectra and to the v spectrum used for grad v; 0 or >= H is
- * off (the paper's experiments run with it off). */
+ * off (the paper's experiments run with it off; the Theorem-overall
+ * configuration takes H0 = H^(8/13)).  p2g_order: assignment function of the
+ * particle-to-grid transfer, 2 (or 0) the trilinear R_h, 4 the fourth-order
+ * star stencil R_h^(4) of Sec. 2.2.1 (32 nodes; negative weights, so u_bar
+ * may be negative); the grid-to-particle interpolation is trilinear either
+ * way.  reserved must be 0. */
 typedef struct {
     double chi, Du, Dm, Dw, alpha, beta, gamma;
     int32_t diffusion;   /* SIPF_DIFFUSION_*  */
     int32_t v_update;    /* SIPF_V_*          */
     double H0;
     uint64_t seed;       /* Philox key        */
+    int32_t p2g_order;   /* 0 or 2: trilinear, 4: R^(4) */
+    int32_t reserved;
 } sipf_params;
 
 /* FP64 diagnostics of the current state (Lemma mass, Corollary mass and the
@@ -111,8 +118,8 @@ typedef struct {
  * later work of the context is enqueued.  Allocates all device state
  * (about 110 N + 110 H^3 bytes: two particle buffers with tile buckets and
  * an overflow region of N slots each, fields, spectra).  Errors: SIPF_EINVAL (N < 1 or N >= 2^31,
- * H not supported, L <= 0, a parameter negative or non-finite, diffusion or
- * v_update unknown), SIPF_ENOMEM. */
+ * H not supported, L <= 0, a parameter negative or non-finite, diffusion,
+ * v_update or p2g_order unknown), SIPF_ENOMEM. */
 int sipf_create(const sipf_grid* grid, int64_t N, const sipf_params* params,
                 void* stream, sipf_ctx** out);
 

@@ -60,6 +60,10 @@ int check_params(const sipf_params* p, std::string* why) {
         *why = "unknown v_update mode";
         return SIPF_EINVAL;
     }
+    if ((p->p2g_order != 0 && p->p2g_order != 2 && p->p2g_order != 4) || p->reserved != 0) {
+        *why = "p2g_order must be 0, 2 or 4 (and reserved 0)";
+        return SIPF_EINVAL;
+    }
     return SIPF_OK;
 }
 
@@ -349,6 +353,7 @@ int sipf_create(const sipf_grid* grid, int64_t N, const sipf_params* params, voi
     for (int k = 0; k < 3; ++k) c->origin[k] = grid->origin[k];
     c->N = N;
     c->p = *params;
+    if (c->p.p2g_order == 0) c->p.p2g_order = 2;
     c->stream = static_cast<cudaStream_t>(stream);
     cudaGetDevice(&c->device);
     const size_t H3 = static_cast<size_t>(c->H) * c->H * c->H;

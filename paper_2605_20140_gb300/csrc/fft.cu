@@ -266,10 +266,11 @@ template <int H> constexpr int rowp() { return H + 1; }
 __device__ __forceinline__ int signed_mode(int k, int H) { return k < H / 2 ? k : k - H; }
 
 // ---------------------------------------------------------------- I/O helpers
-// int64 deposit accumulator -> float, via two exact 32-bit halves (the
-// single 64-bit conversion would run on the FP64 pipe).
+// int64 (two's complement) deposit accumulator -> float, via the signed high
+// and the unsigned low 32-bit halves (the single 64-bit conversion would run
+// on the FP64 pipe).
 __device__ __forceinline__ float acc_to_float(unsigned long long q) {
-    const float hi = __uint2float_rn(static_cast<unsigned>(q >> 32));
+    const float hi = __int2float_rn(static_cast<int>(static_cast<unsigned>(q >> 32)));
     const float lo = __uint2float_rn(static_cast<unsigned>(q));
     return fmaf(hi, 4294967296.0f, lo);
 }

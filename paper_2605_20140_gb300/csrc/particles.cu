@@ -110,6 +110,9 @@ __device__ __forceinline__ Cell locate(float x, float y, float z, int H) {
     return c;
 }
 
+// i mod H for -H <= i < 2H.
+__device__ __forceinline__ int wrap_index(int i, int H) { return i < 0 ? i + H : (i >= H ? i - H : i); }
+
 // round(v) for 0 <= v < 2^22, ties to even (as __float2uint_rn): the low
 // mantissa bits of 2^23 + v.
 __device__ __forceinline__ uint32_t round_small(float v) {
@@ -206,7 +209,7 @@ struct Layout {
 constexpr int kNT = 256;                  // threads of the step kernel
 constexpr int kPT = 4;                    // particles per thread and item
 constexpr int kItem = kNT * kPT;          // particles per item
-constexpr int kBlock = 9 * 9 * 9;         // nodes of a tile's deposit block
+constexpr int kBlock = 9 * 9 * 9;         // nodes of a tile's gather block
 
 // Per-item staging of the pushed particles between the two phases.
 struct Staged {
@@ -217,17 +220,34 @@ struct Staged {
     int slot[kItem];      // neighbour index (< 27) << 22 | rank, or -1 (far / overflow item)
 };
 
-#ifndef SIPF_STEP_MIN_BLOCKS
-#define SIPF_STEP_MIN_BLOCKS 4
-#endif
+// Deposit node block of a tile for assignment order ORDER: local node
+// coordinates [-DO, 8 + DO] per axis (trilinear: the cells' corners 0..8;
+// R^(4): one more node on each side for the star arms).
+template <int ORDER> struct DepBlock {
+    static constexpr int DO = ORDER == 4 ? 1 : 0;
+    static constexpr int B = 9 + 2 * DO;
+    static constexpr int N = B * B * B;
+    static constexpr int MIN_BLOCKS = ORDER == 4 ? 3 : 4;
+    static __device__ __forceinline__ int idx(int lx, int ly, int lz) {
+        return ((lz + DO) * B + (ly + DO)) * B + (lx + DO);
+    }
+};
 
-__global__ void __launch_bounds__(kNT, SIPF_STEP_MIN_BLOCKS)
+// round(v) for |v| < 2^22, ties to even (as __float2int_rn): the low mantissa
+// bits of 1.5 2^23 + v.
+__device__ __forceinline__ int round_signed_small(float v) {
+    return __float_as_int(__fadd_rn(v, 12582912.0f)) - 0x4B400000;
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
     k_step(PushArgs a, DepositArgs d, const float4* __restrict__ G, Buf src, Buf dst, Layout L,
            const Item* __restrict__ items, const int* __restrict__ n_items,
            unsigned long long* __restrict__ acc, int do_deposit, int do_move,
            int* __restrict__ status) {
-    __shared__ unsigned dep[kBlock];        // node sums of the item (exact: < 2^31)
-    __shared__ unsigned long long dep64[kBlock];   // node sums of the tile's items so far
+    using DB = DepBlock<ORDER>;
+    __shared__ int dep[DB::N];              // node sums of the item (exact: |sum| < 2^31)
+    __shared__ long long dep64[DB::N];      // node sums of the tile's items so far
     __shared__ float4 gblk[kBlock];         // (dv/dx, dv/dy, dv/dz, w) on the tile's 9^3 nodes
     __shared__ Staged st;
     __shared__ int nb_cnt[27];
@@ -239,9 +259,9 @@ __global__ void __launch_bounds__(kNT, SIPF_STEP_MIN_BLOCKS)
     const int lane = threadIdx.x & 31;
     const float Hf = __int2float_rn(H);
     const int total = *n_items;
-    for (int i = threadIdx.x; i < kBlock; i += kNT) {
-        dep[i] = 0u;
-        dep64[i] = 0ull;
+    for (int i = threadIdx.x; i < DB::N; i += kNT) {
+        dep[i] = 0;
+        dep64[i] = 0;
     }
     // block b takes a contiguous run of items; consecutive items of one tile
     // share the node block of the gather array and the deposit sums, which
@@ -255,15 +275,16 @@ __global__ void __launch_bounds__(kNT, SIPF_STEP_MIN_BLOCKS)
         if (tile != cur || tile < 0) {
             if (cur >= 0 && do_deposit) {
                 // flush the finished tile's node block into the grid accumulator
-                for (int j = threadIdx.x; j < kBlock; j += kNT) {
-                    const unsigned long long v = dep64[j];
+                // (two's complement sums)
+                for (int j = threadIdx.x; j < DB::N; j += kNT) {
+                    const long long v = dep64[j];
                     if (v) {
-                        const int lx = j % 9, ly = (j / 9) % 9, lz = j / 81;
-                        const int nx = cx0 + lx < H ? cx0 + lx : cx0 + lx - H;
-                        const int ny = cy0 + ly < H ? cy0 + ly : cy0 + ly - H;
-                        const int nz = cz0 + lz < H ? cz0 + lz : cz0 + lz - H;
-                        atomicAdd(acc + (nz * H + ny) * H + nx, v);
-                        dep64[j] = 0ull;
+                        const int lx = j % DB::B - DB::DO, ly = (j / DB::B) % DB::B - DB::DO;
+                        const int lz = j / (DB::B * DB::B) - DB::DO;
+                        const int nx = wrap_index(cx0 + lx, H), ny = wrap_index(cy0 + ly, H);
+                        const int nz = wrap_index(cz0 + lz, H);
+                        atomicAdd(acc + (nz * H + ny) * H + nx, static_cast<unsigned long long>(v));
+                        dep64[j] = 0;
                     }
                 }
             }
@@ -313,44 +334,88 @@ __global__ void __launch_bounds__(kNT, SIPF_STEP_MIN_BLOCKS)
             const Cell c = locate(px, py, pz, H);
 
             if (do_deposit && valid) {
-                // a_p R_h(X_p, node) h^3 in units of exp(logref) 2^-S, as uint32 (< 2^21)
-                // (below 2^20 by the choice of S; the clamp keeps a non-finite
-                // mass inside round_small's range)
-                const float ea = fminf(__fmul_rn(expf(d2f_bits(pl)), d.scale), 4194304.0f);
+                // a_p R_h(X_p, node) h^3 in units of exp(logref) 2^-S as integers
+                // (below 2^20 in magnitude by the choice of S; the clamp keeps a
+                // non-finite mass inside the rounding's range)
+                const float ea = fminf(__fmul_rn(expf(d2f_bits(pl)), d.scale), 2097152.0f);
                 const float wx0 = __fsub_rn(1.0f, c.fx), wy0 = __fsub_rn(1.0f, c.fy);
-                const float e0 = __fmul_rn(ea, __fsub_rn(1.0f, c.fz)), e1 = __fmul_rn(ea, c.fz);
-                const float xy[4] = {__fmul_rn(wx0, wy0), __fmul_rn(c.fx, wy0),
-                                     __fmul_rn(wx0, c.fy), __fmul_rn(c.fx, c.fy)};
-                uint32_t q[8];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    q[k] = round_small(__fmul_rn(e0, xy[k]));
-                    q[4 + k] = round_small(__fmul_rn(e1, xy[k]));
-                }
+                const float wz0 = __fsub_rn(1.0f, c.fz);
                 const int lx = c.cx - tx0, ly = c.cy - ty0, lz = c.cz - tz0;
                 const bool in_tile = tile >= 0 && ((lx | ly | lz) & ~7) == 0;
                 if (tile >= 0 && !in_tile) bad |= 2;   // bucket does not match position
-                if (in_tile) {
-                    // particles of a bucket are in random cells of the tile, so lanes
-                    // rarely collide: one shared 32-bit atomic per corner (an item has at
-                    // most kItem particles and each value is < 2^21, so sums are exact)
-                    const int nbase = (lz * 9 + ly) * 9 + lx;
+                if constexpr (ORDER == 2) {
+                    const float e0 = __fmul_rn(ea, wz0), e1 = __fmul_rn(ea, c.fz);
+                    const float xy[4] = {__fmul_rn(wx0, wy0), __fmul_rn(c.fx, wy0),
+                                         __fmul_rn(wx0, c.fy), __fmul_rn(c.fx, c.fy)};
+                    uint32_t q[8];
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        const int node = nbase + (k & 1) + ((k >> 1) & 1) * 9 + (k >> 2) * 81;
-                        if (q[k]) atomicAdd(dep + node, q[k]);
+                    for (int k = 0; k < 4; ++k) {
+                        q[k] = round_small(__fmul_rn(e0, xy[k]));
+                        q[4 + k] = round_small(__fmul_rn(e1, xy[k]));
+                    }
+                    if (in_tile) {
+                        // particles of a bucket are in random cells of the tile, so lanes
+                        // rarely collide: one shared 32-bit atomic per corner (an item has
+                        // at most kItem particles and each value is < 2^21, so sums are exact)
+                        const int nbase = DB::idx(lx, ly, lz);
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const int node = nbase + (k & 1) + ((k >> 1) & 1) * 9 + (k >> 2) * 81;
+                            if (q[k]) atomicAdd(dep + node, static_cast<int>(q[k]));
+                        }
+                    } else {
+                        const int x1 = c.cx + 1 < H ? c.cx + 1 : 0;
+                        const int y1 = c.cy + 1 < H ? c.cy + 1 : 0;
+                        const int z1 = c.cz + 1 < H ? c.cz + 1 : 0;
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const int nx = (k & 1) ? x1 : c.cx, ny = ((k >> 1) & 1) ? y1 : c.cy;
+                            const int nz = (k >> 2) ? z1 : c.cz;
+                            if (q[k])
+                                atomicAdd(acc + (nz * H + ny) * H + nx,
+                                          static_cast<unsigned long long>(q[k]));
+                        }
                     }
                 } else {
-                    const int x1 = c.cx + 1 < H ? c.cx + 1 : 0;
-                    const int y1 = c.cy + 1 < H ? c.cy + 1 : 0;
-                    const int z1 = c.cz + 1 < H ? c.cz + 1 : 0;
+                    // R^(4): the 8 corners carry the trilinear weight times
+                    // g = 1 + sum_j f_j (1 - f_j) / 2; along axis j the nodes c_j - 1 and
+                    // c_j + 2 carry -f (1 - f)(2 - f) / 6 and -f (1 - f)(1 + f) / 6 times
+                    // the bilinear weight of the other two axes (cases of R_h^(4))
+                    const float fx = c.fx, fy = c.fy, fz = c.fz;
+                    const float bx = __fmul_rn(fx, wx0), by = __fmul_rn(fy, wy0), bz = __fmul_rn(fz, wz0);
+                    const float g = __fadd_rn(1.0f, __fmul_rn(0.5f, __fadd_rn(__fadd_rn(bx, by), bz)));
+                    const float sx[2] = {__fmul_rn(__fmul_rn(bx, __fsub_rn(2.0f, fx)), -1.0f / 6.0f),
+                                         __fmul_rn(__fmul_rn(bx, __fadd_rn(1.0f, fx)), -1.0f / 6.0f)};
+                    const float sy[2] = {__fmul_rn(__fmul_rn(by, __fsub_rn(2.0f, fy)), -1.0f / 6.0f),
+                                         __fmul_rn(__fmul_rn(by, __fadd_rn(1.0f, fy)), -1.0f / 6.0f)};
+                    const float sz[2] = {__fmul_rn(__fmul_rn(bz, __fsub_rn(2.0f, fz)), -1.0f / 6.0f),
+                                         __fmul_rn(__fmul_rn(bz, __fadd_rn(1.0f, fz)), -1.0f / 6.0f)};
+                    const float wx[2] = {wx0, fx}, wy[2] = {wy0, fy}, wz[2] = {wz0, fz};
+                    const float eg = __fmul_rn(ea, g);
+                    auto emit = [&](int ox, int oy, int oz, float value) {
+                        const int q = round_signed_small(value);
+                        if (!q) return;
+                        if (in_tile) {
+                            atomicAdd(dep + DB::idx(lx + ox, ly + oy, lz + oz), q);
+                        } else {
+                            const int nx = wrap_index(c.cx + ox, H), ny = wrap_index(c.cy + oy, H);
+                            const int nz = wrap_index(c.cz + oz, H);
+                            atomicAdd(acc + (nz * H + ny) * H + nx,
+                                      static_cast<unsigned long long>(static_cast<long long>(q)));
+                        }
+                    };
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
-                        const int nx = (k & 1) ? x1 : c.cx, ny = ((k >> 1) & 1) ? y1 : c.cy;
-                        const int nz = (k >> 2) ? z1 : c.cz;
-                        if (q[k])
-                            atomicAdd(acc + (nz * H + ny) * H + nx,
-                                      static_cast<unsigned long long>(q[k]));
+                        const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+                        emit(dx, dy, dz, __fmul_rn(eg, __fmul_rn(__fmul_rn(wx[dx], wy[dy]), wz[dz])));
+                    }
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int side = k & 1, u = (k >> 1) & 1, v = k >> 2;
+                        const int o = side ? 2 : -1;
+                        emit(o, u, v, __fmul_rn(ea, __fmul_rn(sx[side], __fmul_rn(wy[u], wz[v]))));
+                        emit(u, o, v, __fmul_rn(ea, __fmul_rn(sy[side], __fmul_rn(wx[u], wz[v]))));
+                        emit(u, v, o, __fmul_rn(ea, __fmul_rn(sz[side], __fmul_rn(wx[u], wy[v]))));
                     }
                 }
             }
@@ -404,11 +469,11 @@ __global__ void __launch_bounds__(kNT, SIPF_STEP_MIN_BLOCKS)
         __syncthreads();
         if (do_deposit && tile >= 0) {
             // the item's exact 32-bit sums into the tile's 64-bit sums
-            for (int j = threadIdx.x; j < kBlock; j += kNT) {
-                const unsigned v = dep[j];
+            for (int j = threadIdx.x; j < DB::N; j += kNT) {
+                const int v = dep[j];
                 if (v) {
                     dep64[j] += v;
-                    dep[j] = 0u;
+                    dep[j] = 0;
                 }
             }
         }
@@ -731,8 +796,9 @@ __global__ void k_acc_to_float(unsigned long long* __restrict__ acc, int n, floa
     if (i >= n) return;
     const unsigned long long q = acc[i];
     acc[i] = 0ull;
-    const float f = fmaf(__uint2float_rn(static_cast<unsigned>(q >> 32)), 4294967296.0f,
-                         __uint2float_rn(static_cast<unsigned>(q)));
+    // two's complement: signed high half, unsigned low half
+    const float f = fmaf(__int2float_rn(static_cast<int>(static_cast<unsigned>(q >> 32))),
+                         4294967296.0f, __uint2float_rn(static_cast<unsigned>(q)));
     out[i] = f * scale;
 }
 
@@ -888,7 +954,10 @@ inline Layout layout_of(sipf_ctx* c, int b) {
 int step_grid(sipf_ctx* c) {
     int dev = c->device, nsm = 0, per_sm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step, kNT, 0);
+    if (c->p.p2g_order == 4)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<4>, kNT, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<2>, kNT, 0);
     const int g = nsm * (per_sm > 0 ? per_sm : 1);
     return g > 0 ? g : 1;
 }
@@ -896,7 +965,8 @@ int step_grid(sipf_ctx* c) {
 cudaError_t launch_step_kernel(sipf_ctx* c, const PushArgs& a, const DepositArgs& d,
                                int do_deposit, int do_move) {
     const int b = c->cur;
-    k_step<<<c->step_blocks, kNT, 0, c->stream>>>(
+    auto kernel = c->p.p2g_order == 4 ? k_step<4> : k_step<2>;
+    kernel<<<c->step_blocks, kNT, 0, c->stream>>>(
         a, d, reinterpret_cast<const float4*>(c->G), buf_of(c, b), buf_of(c, b ^ 1),
         layout_of(c, b ^ 1), c->items, c->n_items,
         reinterpret_cast<unsigned long long*>(c->acc), do_deposit, do_move, c->status);

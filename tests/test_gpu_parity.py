@@ -21,6 +21,7 @@ Tolerances (float32 path against float64 oracle):
   tau |rho - 1| <= tau, summed in float64).
 """
 
+import dataclasses
 import math
 
 import numpy as np
@@ -205,6 +206,34 @@ def test_deposit_matches_oracle_and_conserves_mass(name, H, N):
     assert abs(d["mass_particles"] - wl.mass.sum()) <= 1e-12 * wl.mass.sum()
 
 
+@pytest.mark.parametrize("name,H,N", [("small", 32, 1 << 15), ("headline", 64, 1 << 18),
+                                      ("small", 48, 20000)])
+def test_fourth_order_deposit_matches_oracle(name, H, N):
+    """R^(4) (Sec. 2.2.1): 32 nodes per particle, signed integer sums.
+
+    Bound: the trilinear case's 1e-6 times 1.75 (sum_q |R^(4)| = 1 +
+    sum_j f_j (1 - f_j) <= 1.75 times sum_q R^(4): the negative star weights
+    cancel part of the corners) times sqrt(8/3) (about eight float32 roundings
+    per contribution instead of three): 2.9e-6 (6e-6 for the largest node
+    error, against 2e-6 trilinear)."""
+    wl = workload(name, H=H, N=N)
+    p = dataclasses.replace(wl.params, p2g_order=4)
+    sim = run_gpu(wl, 0, p=p)
+    u = sim.fields(sipf.FIELD_U)["u"]
+    d = sim.diagnostics()
+    sim.close()
+    st = oracle_state(wl, p=p)
+    ref = O.density(st)
+    tol = 2.9e-6 if N >= H ** 3 else max(2.9e-6, u_tolerance(st, N))
+    assert rel_l2(u, ref) <= tol
+    assert np.max(np.abs(u - ref)) <= 6e-6 * np.abs(ref).max()
+    h3 = (wl.L / wl.H) ** 3
+    assert abs(u.astype(np.float64).sum() * h3 - wl.mass.sum()) <= 1e-6 * wl.mass.sum()
+    assert abs(d["mass_grid"] - wl.mass.sum()) <= 2e-5 / np.sqrt(wl.N) * wl.mass.sum()
+    if ref.min() < 0:
+        assert u.min() < 0       # the negative star weights survive the integer path
+
+
 @pytest.mark.parametrize("H", [8, 16, 24, 32, 48, 64, 72, 96, 128, 144, 192, 256])
 def test_initial_spectral_gradient(H):
     wl = workload("small", H=H, N=1024)
@@ -337,6 +366,26 @@ def test_steps_match_oracle_radix3_grids(H):
     wl = workload("small", H=H, N=1 << 15)
     sim = run_gpu(wl, 10)
     st = O.run(oracle_state(wl), wl.dt, 10)
+    _compare(sim, st, wl)
+    sim.close()
+
+
+def test_steps_match_oracle_fourth_order_assignment():
+    """Ten steps with fourth-order P2G and trilinear G2P (Theorem overall)
+    and the low-pass filter H0 = H^(8/13)."""
+    wl = workload("small", H=32, N=1 << 15)
+    p = dataclasses.replace(wl.params, p2g_order=4, H0=32 ** (8 / 13))
+    sim = run_gpu(wl, 10, p=p)
+    st = O.run(oracle_state(wl, p=p), wl.dt, 10)
+    _compare(sim, st, wl)
+    sim.close()
+
+
+def test_headline_size_one_step_fourth_order():
+    wl = workload("headline")
+    p = dataclasses.replace(wl.params, p2g_order=4)
+    sim = run_gpu(wl, 1, p=p)
+    st = O.run(oracle_state(wl, p=p), wl.dt, 1)
     _compare(sim, st, wl)
     sim.close()
 
