@@ -145,22 +145,27 @@ def _peaks():
 # DRAM bytes (read + write) of one launch from an ncu capture of the same
 # workload (profiles/k_step_and_spectral_passes_headline_128cube_4M.md),
 # valid only while the kernel's source is the one captured.
-NCU_TRAFFIC = {"particle_step": ("paper_2605_20140_gb300/csrc/particles.cu", "1d92c60773379c0a",
-                                 161.1e6)}
+NCU_TRAFFIC = {"particle_step": (("paper_2605_20140_gb300/csrc/particles.cu",
+                                  "paper_2605_20140_gb300/csrc/sipf_internal.cuh"),
+                                 "802fdee422500cb2", 161.3e6)}
 
 
 def _ncu_traffic(group):
+    """DRAM bytes per launch from the committed ncu capture, or None when the
+    kernel's sources changed since (sha256 over the files, first 16 hex)."""
     import hashlib
     entry = NCU_TRAFFIC.get(group)
     if not entry:
         return None
-    path, digest, traffic = entry
+    paths, digest, traffic = entry
+    h = hashlib.sha256()
     try:
-        with open(os.path.join(ROOT, path), "rb") as f:
-            cur = hashlib.sha256(f.read()).hexdigest()[:16]
+        for path in paths:
+            with open(os.path.join(ROOT, path), "rb") as f:
+                h.update(f.read())
     except OSError:
         return None
-    return traffic if cur == digest else None
+    return traffic if h.hexdigest()[:16] == digest else None
 
 
 def _cpu_baseline(wl_fn, n_sample_steps=1):
