@@ -2,6 +2,7 @@
 """Throughput of the SIPF-W step on the 128^3-grid / 2^22-particle workload.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sipf|reference]
+                    [--workload headline|ensemble]
 
 One step = one pass of the whole hot path (the particle step: deposit,
 gather, push, mass update and binning; the bucket plan; three spectral
@@ -10,6 +11,9 @@ tumour seeds at seeded centres, sigma 0.04, unit periodic cube, dt 5e-4).
 Prints one JSON line on rank 0.  Under torchrun (N > 1) every rank runs an
 independent replica on its own GPU (no data-path collective); the timed
 region is bracketed by a barrier and the slowest rank's time is used.
+
+--workload ensemble instead times 64 uneven independent runs advanced
+together (one stream each) against the same runs one at a time (runs/s).
 
 --impl reference times the FP64 oracle on the host cores (the paper ships
 no code; the oracle is the reference arm), each step on a bounded sample of
@@ -333,21 +337,90 @@ def run_sipf(args, rank, world, local):
     return 0
 
 
+def run_ensemble(args, rank, world, local):
+    """64 uneven independent runs (H in {32, 48, 64, 96}, N = 2^U[14, 20],
+    chi, alpha, Du drawn per run, one Philox key each) advanced together, one
+    stream per run, against the same runs stepped one at a time."""
+    import torch
+    from paper_2605_20140_gb300 import sipf
+    from sipf_inputs import ensemble_workloads
+
+    torch.cuda.set_device(local)
+    count, K, W = 64, args.steps, args.warmup
+    runs = ensemble_workloads(count, seed=rank)
+    dts = np.array([w.dt for w in runs])
+    ens = sipf.Ensemble([(w.H, w.L, w.origin, w.N, w.params) for w in runs])
+    try:
+        for sim, w in zip(ens.members, runs):
+            sim.set_state(w.x, w.mass, w.ids, w.v, w.m, w.w)
+        ens.step(dts, W)
+        ens.sync()
+        clocks = ClockSampler(local)
+        _barrier(world)
+        torch.cuda.synchronize()
+        clocks.start()
+        t0 = time.perf_counter()
+        ens.step(dts, K)
+        ens.sync()
+        t_together = time.perf_counter() - t0
+        clk = clocks.stop()
+        t0 = time.perf_counter()
+        for sim, dt in zip(ens.members, dts):
+            sim.step(dt, K)
+            sipf.sipf_sync(sim.ctx)
+        t_alone = time.perf_counter() - t0
+        _barrier(world)
+        t_together = _max_over_ranks(t_together, world)
+        t_alone = _max_over_ranks(t_alone, world)
+    finally:
+        ens.close()
+    member_steps = count * K * world
+    particle_steps = sum(w.N for w in runs) * K * world
+    if rank == 0:
+        line = {
+            "metric": f"runs/s, {count} uneven runs of {K} steps (H in 32..96, N in 2^14..2^20)",
+            "value": count * world / t_together,
+            "unit": "runs/s",
+            "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": 1e3 * t_together / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (f64 log-mass and reductions)", "data": "synthetic",
+            "config": {"workload": f"ensemble: {count} runs, H in {{32, 48, 64, 96}}, "
+                                   "N = 2^U[14, 20], chi ~ U[0.005, 0.03], alpha ~ U[5, 20], "
+                                   "Du ~ U[5e-4, 2e-3], dt 1e-3",
+                       "parallelism": f"one stream per run, replicas x{world}",
+                       "timing": "host wall clock around enqueue + sync of all runs"},
+            "one_at_a_time": {"value": count * world / t_alone, "unit": "runs/s",
+                              "speedup": t_alone / t_together},
+            "member_steps_per_s": member_steps / t_together,
+            "particle_steps_per_s": particle_steps / t_together,
+            "gpu_launches": 5 * member_steps,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--workload", choices=["headline", "ensemble"], default="headline")
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["sipf", "reference"], default="sipf")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 200 if args.workload == "ensemble" else 1000
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     rank, world, local = _dist_init(args.gpus)
     try:
         if args.impl == "reference":
             return run_reference(args, rank, world)
+        if args.workload == "ensemble":
+            return run_ensemble(args, rank, world, local)
         return run_sipf(args, rank, world, local)
     finally:
         if world > 1:

@@ -193,6 +193,33 @@ int sipf_sync(sipf_ctx* ctx);
  * (a mass is not finite), SIPF_ENOMEM, SIPF_ECUDA. */
 int sipf_resample(sipf_ctx* ctx, double ratio, int32_t* resampled);
 
+/* Ensembles: many independent runs (different grids, particle counts,
+ * parameters and seeds) advanced together.  The paper's method is one run;
+ * an ensemble is replicas of it with no shared state: each member is an
+ * ordinary context on a stream of its own, so the kernels of small members
+ * run concurrently on the GPU, and each member's results are bit for bit
+ * those of the same run alone.
+ *
+ * sipf_ensemble_create: count members, member i created as
+ * sipf_create(&grids[i], N[i], &params[i]) on a new non-blocking stream owned
+ * by the ensemble.  Errors: those of sipf_create (nothing is kept on error).
+ * sipf_ensemble_member: member i (for sipf_set_state, sipf_fields, ...;
+ * owned by the ensemble; NULL if i is out of range).
+ * sipf_ensemble_step: k steps of every member, dt[i] for member i (host
+ * array of count doubles); enqueues only.  Errors: SIPF_EINVAL (a member
+ * without state, a dt outside (0, 0.5]).
+ * sipf_ensemble_sync: waits for all members; returns the first deferred
+ * device error.  sipf_ensemble_last_error: message of the last failed call
+ * ("" if none).  sipf_ensemble_destroy frees everything (NULL: no-op). */
+typedef struct sipf_ensemble sipf_ensemble;
+int sipf_ensemble_create(int32_t count, const sipf_grid* grids, const int64_t* N,
+                         const sipf_params* params, sipf_ensemble** out);
+sipf_ctx* sipf_ensemble_member(sipf_ensemble* ens, int32_t i);
+int sipf_ensemble_step(sipf_ensemble* ens, const double* dt, int64_t k);
+int sipf_ensemble_sync(sipf_ensemble* ens);
+const char* sipf_ensemble_last_error(const sipf_ensemble* ens);
+void sipf_ensemble_destroy(sipf_ensemble* ens);
+
 /* Checkpoint / resume.  The paper has no checkpoint; what is saved is the
  * state of the scheme after step n of Alg. 3: the particles X^n (grid units)
  * with log a^n and ids, the grids v^n, m^n, w^n and the gather array

@@ -882,6 +882,107 @@ int sipf_describe(const sipf_ctx* c, sipf_grid* grid, int64_t* N, sipf_params* p
     return SIPF_OK;
 }
 
+// ---------------------------------------------------------------- ensembles
+}  // extern "C"
+
+struct sipf_ensemble {
+    std::vector<sipf_ctx*> members;
+    std::vector<cudaStream_t> streams;   // one per member, owned here
+    std::string last_error;
+};
+
+namespace {
+void ensemble_free(sipf_ensemble* e) {
+    for (sipf_ctx* c : e->members)
+        if (c) sipf_destroy(c);
+    for (cudaStream_t s : e->streams)
+        if (s) cudaStreamDestroy(s);
+    delete e;
+}
+}  // namespace
+
+extern "C" {
+
+int sipf_ensemble_create(int32_t count, const sipf_grid* grids, const int64_t* N,
+                         const sipf_params* params, sipf_ensemble** out) {
+    if (!out) return SIPF_EINVAL;
+    *out = nullptr;
+    if (count < 1 || !grids || !N || !params) return SIPF_EINVAL;
+    sipf_ensemble* e = new (std::nothrow) sipf_ensemble();
+    if (!e) return SIPF_ENOMEM;
+    for (int32_t i = 0; i < count; ++i) {
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            ensemble_free(e);
+            return SIPF_ECUDA;
+        }
+        e->streams.push_back(s);
+        sipf_ctx* c = nullptr;
+        const int r = sipf_create(&grids[i], N[i], &params[i], s, &c);
+        if (r != SIPF_OK) {
+            ensemble_free(e);
+            return r;
+        }
+        e->members.push_back(c);
+    }
+    *out = e;
+    return SIPF_OK;
+}
+
+sipf_ctx* sipf_ensemble_member(sipf_ensemble* e, int32_t i) {
+    if (!e || i < 0 || i >= static_cast<int32_t>(e->members.size())) return nullptr;
+    return e->members[i];
+}
+
+int sipf_ensemble_step(sipf_ensemble* e, const double* dt, int64_t k) {
+    if (!e || !dt || k < 0) return SIPF_EINVAL;
+    for (size_t i = 0; i < e->members.size(); ++i) {
+        sipf_ctx* c = e->members[i];
+        if (!c->state_set) {
+            e->last_error = "member " + std::to_string(i) + ": sipf_set_state has not been called";
+            return SIPF_EINVAL;
+        }
+        if (!(isfinite(dt[i]) && dt[i] > 0.0 && dt[i] <= 0.5)) {
+            e->last_error = "member " + std::to_string(i) + ": dt must satisfy 0 < dt <= 0.5";
+            return SIPF_EINVAL;
+        }
+    }
+    // step by step, member after member: every member's work goes to its own
+    // stream, so the kernels of different members run concurrently
+    for (int64_t n = 0; n < k; ++n) {
+        for (size_t i = 0; i < e->members.size(); ++i) {
+            const int r = enqueue_step(e->members[i], dt[i]);
+            if (r != SIPF_OK) {
+                e->last_error = "member " + std::to_string(i) + ": " + e->members[i]->last_error;
+                return r;
+            }
+        }
+    }
+    return SIPF_OK;
+}
+
+int sipf_ensemble_sync(sipf_ensemble* e) {
+    if (!e) return SIPF_EINVAL;
+    int first = SIPF_OK;
+    for (size_t i = 0; i < e->members.size(); ++i) {
+        const int r = sipf_sync(e->members[i]);
+        if (r != SIPF_OK && first == SIPF_OK) {
+            first = r;
+            e->last_error = "member " + std::to_string(i) + ": " + e->members[i]->last_error;
+        }
+    }
+    return first;
+}
+
+const char* sipf_ensemble_last_error(const sipf_ensemble* e) {
+    return e ? e->last_error.c_str() : "";
+}
+
+void sipf_ensemble_destroy(sipf_ensemble* e) {
+    if (e) ensemble_free(e);
+}
+
 int sipf_profile(sipf_ctx* c, int enable) {
     if (!c) return SIPF_EINVAL;
     if (enable && !c->prof_on) c->prof_steps = 0;

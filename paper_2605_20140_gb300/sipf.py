@@ -36,7 +36,9 @@ EXPORTED = (
     "sipf_destroy", "sipf_strerror", "sipf_last_error", "sipf_brownian_normals",
     "sipf_profile", "sipf_profile_read", "sipf_profile_name", "sipf_check_conversions",
     "sipf_deposit_noalloc", "sipf_save", "sipf_load",
-    "sipf_describe", "sipf_resample",
+    "sipf_describe", "sipf_resample", "sipf_ensemble_create", "sipf_ensemble_member",
+    "sipf_ensemble_step", "sipf_ensemble_sync", "sipf_ensemble_last_error",
+    "sipf_ensemble_destroy",
 )
 PROFILE_GROUPS = 4
 
@@ -102,6 +104,12 @@ def load() -> ctypes.CDLL:
         "sipf_deposit_noalloc": ([ctypes.POINTER(sipf_grid), P, P, I64, P, P], I32),
         "sipf_save": ([P, ctypes.c_char_p], I32),
         "sipf_resample": ([P, ctypes.c_double, ctypes.POINTER(ctypes.c_int32)], I32),
+        "sipf_ensemble_create": ([I32, P, P, P, ctypes.POINTER(P)], I32),
+        "sipf_ensemble_member": ([P, I32], P),
+        "sipf_ensemble_step": ([P, P, I64], I32),
+        "sipf_ensemble_sync": ([P], I32),
+        "sipf_ensemble_last_error": ([P], ctypes.c_char_p),
+        "sipf_ensemble_destroy": ([P], None),
         "sipf_describe": ([P, ctypes.POINTER(sipf_grid), ctypes.POINTER(I64),
                            ctypes.POINTER(sipf_params), ctypes.POINTER(I64),
                            ctypes.POINTER(ctypes.c_double)], I32),
@@ -207,6 +215,45 @@ def sipf_resample(ctx, ratio: float = 0.0) -> bool:
     done = ctypes.c_int32(0)
     _check(load().sipf_resample(ctx, float(ratio), ctypes.byref(done)), ctx)
     return bool(done.value)
+
+
+def _check_ens(code: int, ens):
+    if code != SIPF_OK:
+        lib = load()
+        msg = lib.sipf_strerror(code).decode()
+        extra = lib.sipf_ensemble_last_error(ens).decode() if ens else ""
+        raise SipfError(code, f"{msg}: {extra}" if extra else msg)
+
+
+def sipf_ensemble_create(grids, Ns, params) -> int:
+    n = len(grids)
+    ga = (sipf_grid * n)(*grids)
+    na = (ctypes.c_int64 * n)(*[int(x) for x in Ns])
+    pa = (sipf_params * n)(*params)
+    out = ctypes.c_void_p()
+    _check(load().sipf_ensemble_create(n, ga, na, pa, ctypes.byref(out)))
+    return out.value
+
+
+def sipf_ensemble_member(ens, i: int) -> int:
+    c = load().sipf_ensemble_member(ens, int(i))
+    if not c:
+        raise IndexError(i)
+    return c
+
+
+def sipf_ensemble_step(ens, dts, k: int = 1):
+    d = np.ascontiguousarray(dts, dtype=np.float64)
+    _check_ens(load().sipf_ensemble_step(ens, d.ctypes.data, int(k)), ens)
+
+
+def sipf_ensemble_sync(ens):
+    _check_ens(load().sipf_ensemble_sync(ens), ens)
+
+
+def sipf_ensemble_destroy(ens):
+    if ens:
+        load().sipf_ensemble_destroy(ens)
 
 
 def sipf_describe(ctx) -> dict:
@@ -353,3 +400,35 @@ class Simulation:
 
     def diagnostics(self) -> dict:
         return sipf_diagnostics(self.ctx)
+
+
+class Ensemble:
+    """Independent runs advanced together, one stream each; members are
+    Simulation views (owned by the ensemble)."""
+
+    def __init__(self, specs):
+        """specs: sequence of (H, L, origin, N, params)."""
+        grids = [make_grid(H, L, origin) for H, L, origin, _, _ in specs]
+        self.ens = sipf_ensemble_create(grids, [N for _, _, _, N, _ in specs],
+                                        [make_params(p) for *_, p in specs])
+        self.members = [Simulation(H, L, origin, N, None, _ctx=sipf_ensemble_member(self.ens, i))
+                        for i, (H, L, origin, N, _) in enumerate(specs)]
+
+    def step(self, dts, k=1):
+        sipf_ensemble_step(self.ens, dts, k)
+
+    def sync(self):
+        sipf_ensemble_sync(self.ens)
+
+    def close(self):
+        if self.ens:
+            for m in self.members:
+                m.ctx = None          # owned by the ensemble
+            sipf_ensemble_destroy(self.ens)
+            self.ens = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -41,6 +41,7 @@ import numpy as np
 __all__ = [
     "Params",
     "Workload",
+    "ensemble_workloads",
     "gaussian_mixture_positions",
     "node_coordinates",
     "periodic_sq_distance",
@@ -202,3 +203,27 @@ def workload(name: str, seed: int = 0, H: int | None = None, N: int | None = Non
     mass = np.full(N, 1.0 / N)
     return Workload(name, H, L, origin, N, dt, steps, p, x, mass,
                     np.arange(N, dtype=np.uint32), v, m, w)
+
+
+def ensemble_workloads(count: int = 64, seed: int = 0, max_log2_N: int = 20,
+                       sizes=(32, 48, 64, 96)) -> list:
+    """Uneven ensemble of independent runs: grid side H uniform over ``sizes``,
+    particle count N = round(2^U[14, max_log2_N]), chi ~ U[0.005, 0.03],
+    alpha ~ U[5, 20], Du ~ U[5e-4, 2e-3], one Philox key per run, 200 steps of
+    dt 1e-3; initial data as in ``small`` (one Gaussian cloud of sigma 0.05 at
+    the box centre, equal masses of total 1)."""
+    rng = np.random.default_rng(np.random.PCG64(7000 + seed))
+    runs = []
+    for r in range(count):
+        H = int(rng.choice(sizes))
+        N = int(round(2.0 ** rng.uniform(14.0, max_log2_N)))
+        chi = float(rng.uniform(0.005, 0.03))
+        alpha = float(rng.uniform(5.0, 20.0))
+        Du = float(rng.uniform(5e-4, 2e-3))
+        wl = workload("small", seed=1000 * seed + r, H=H, N=N)
+        wl.name = f"ensemble[{r}]"
+        wl.params = dataclasses.replace(wl.params, chi=chi, alpha=alpha, Du=Du,
+                                        seed=(seed << 32) | r)
+        wl.steps = 200
+        runs.append(wl)
+    return runs

@@ -118,3 +118,19 @@ def test_load_rejects_missing_and_foreign_files_without_touching_the_gpu(lib, tm
     assert lib.sipf_load(None, None, ctypes.byref(out)) == sipf.SIPF_EINVAL
     assert lib.sipf_save(None, b"x") == sipf.SIPF_EINVAL
     assert lib.sipf_describe(None, None, None, None, None, None) == sipf.SIPF_EINVAL
+
+
+def test_ensemble_calls_reject_bad_arguments_without_touching_the_gpu(lib):
+    out = ctypes.c_void_p()
+    g = sipf.make_grid(32, 1.0)
+    p = sipf.sipf_params()
+    n = ctypes.c_int64(100)
+    assert lib.sipf_ensemble_create(0, ctypes.byref(g), ctypes.byref(n), ctypes.byref(p),
+                                    ctypes.byref(out)) == sipf.SIPF_EINVAL
+    assert lib.sipf_ensemble_create(1, None, None, None, ctypes.byref(out)) == sipf.SIPF_EINVAL
+    assert out.value is None
+    assert lib.sipf_ensemble_step(None, None, 1) == sipf.SIPF_EINVAL
+    assert lib.sipf_ensemble_sync(None) == sipf.SIPF_EINVAL
+    assert lib.sipf_ensemble_member(None, 0) is None
+    assert lib.sipf_ensemble_last_error(None) == b""
+    lib.sipf_ensemble_destroy(None)

@@ -1,0 +1,71 @@
+"""Ensembles of independent runs through the C ABI: every member, advanced
+together with the others on its own stream, ends bit for bit where the same
+run advanced alone ends (same kernels, deterministic integer deposit)."""
+
+import os
+
+import numpy as np
+import pytest
+
+from paper_2605_20140_gb300 import sipf
+from sipf_inputs import ensemble_workloads
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    if not os.path.exists(sipf.LIB_PATH):
+        from paper_2605_20140_gb300 import build
+        build.build()
+    sipf.load()
+
+
+def snapshot(sim):
+    f = sim.fields()
+    s, loga, ids = sim.particle_state()
+    o = np.argsort(ids, kind="stable")
+    return f, s[o], loga[o]
+
+
+def test_members_equal_their_solo_runs():
+    runs = ensemble_workloads(6, seed=3, max_log2_N=16)
+    assert len({w.H for w in runs}) > 1          # uneven grids
+    dts = np.array([w.dt * (1.0 + 0.1 * i) for i, w in enumerate(runs)])
+    steps = 12
+    with sipf.Ensemble([(w.H, w.L, w.origin, w.N, w.params) for w in runs]) as ens:
+        for sim, w in zip(ens.members, runs):
+            sim.set_state(w.x, w.mass, w.ids, w.v, w.m, w.w)
+        ens.step(dts, steps)
+        ens.sync()
+        got = [snapshot(sim) for sim in ens.members]
+        assert all(sim.diagnostics()["step"] == steps for sim in ens.members)
+    for w, dt, (f, s, l) in zip(runs, dts, got):
+        with sipf.Simulation(w.H, w.L, w.origin, w.N, w.params) as solo:
+            solo.set_state(w.x, w.mass, w.ids, w.v, w.m, w.w)
+            solo.step(dt, steps)
+            f0, s0, l0 = snapshot(solo)
+        for k in f0:
+            np.testing.assert_array_equal(f[k], f0[k], err_msg=f"{w.name} {k}")
+        np.testing.assert_array_equal(s, s0)
+        np.testing.assert_array_equal(l, l0)
+
+
+def test_step_checks_every_member():
+    runs = ensemble_workloads(2, seed=1, max_log2_N=14)
+    with sipf.Ensemble([(w.H, w.L, w.origin, w.N, w.params) for w in runs]) as ens:
+        ens.members[0].set_state(runs[0].x, runs[0].mass, runs[0].ids, runs[0].v, runs[0].m,
+                                 runs[0].w)
+        with pytest.raises(sipf.SipfError) as e:
+            ens.step([1e-3, 1e-3], 1)      # member 1 has no state
+        assert e.value.code == sipf.SIPF_EINVAL
+        ens.members[1].set_state(runs[1].x, runs[1].mass, runs[1].ids, runs[1].v, runs[1].m,
+                                 runs[1].w)
+        with pytest.raises(sipf.SipfError):
+            ens.step([1e-3, 0.0], 1)
+        ens.step([1e-3, 1e-3], 2)
+        ens.sync()
