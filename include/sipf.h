@@ -137,9 +137,13 @@ int sipf_set_state(sipf_ctx* ctx, const float* x, const double* mass, const uint
 /* Enqueue k steps of size dt (paper Alg. 3 loop body, Jacobi ordering:
  * deposit, gather, push and field update all read the state at step n-1).
  * Asynchronous: returns after enqueueing; device-side failures are reported
- * by the next synchronising call.  Errors: SIPF_EINVAL (state not set,
- * dt <= 0, dt > 0.5 -- the positivity lemma's bound -- or k < 0),
- * SIPF_ECUDA. */
+ * by the next synchronising call.  With k >= 2 on a stream other than the
+ * legacy default one and tracing off, pairs of steps are launched as a CUDA
+ * graph captured from the context's own launches on the first such call for
+ * this dt (kept per context, at most four); the kernels and their arguments
+ * are the same, so the results are identical to k single steps.  Errors:
+ * SIPF_EINVAL (state not set, dt <= 0, dt > 0.5 -- the positivity lemma's
+ * bound -- or k < 0), SIPF_ECUDA. */
 int sipf_step(sipf_ctx* ctx, double dt, int64_t k);
 
 /* Copy the fields selected by `mask` (SIPF_FIELD_* bits) into dst, one H^3

@@ -79,7 +79,8 @@ void free_all(sipf_ctx* c) {
                     c->work, c->count, c->cell_start, c->scan_tmp, c->acc, c->v, c->m, c->w,
                     c->G, c->specM, c->specW, c->specV, c->specB, c->specA, c->specDx,
                     c->specDy, c->twiddle,
-                    c->status, c->diag_tmp, c->diag_out, c->diag_ll, c->voff, c->rs_scratch};
+                    c->status, c->diag_tmp, c->diag_out, c->diag_ll, c->voff, c->rs_scratch,
+                    c->dsc};
     for (void* q : ptrs)
         if (q) cudaFree(q);
 }
@@ -113,39 +114,40 @@ int check_status(sipf_ctx* c) {
     return SIPF_OK;
 }
 
-// Fixed-point scale 2^S of the deposit: one contribution is at most
-// max_p a_p / exp(logref) <= maxrel e^t (Lemma mass: a grows by at most
-// 1 + tau <= e^tau per step), and must stay below 2^21 after scaling, so
-// that the sums of one 1024-particle item fit exactly in 32 bits; node sums
-// over the whole grid are accumulated in 64-bit integers.
-int deposit_shift(const sipf_ctx* c) {
-    const double bound = log2(c->maxrel) + c->time * 1.4426950408889634 + 0.5;
-    int S = static_cast<int>(floor(20.0 - bound));
-    if (S > 40) S = 40;
-    if (S < -60) S = -60;
-    return S;
-}
-
-DepositArgs deposit_args(const sipf_ctx* c) {
-    DepositArgs d;
-    d.scale = static_cast<float>(ldexp(1.0, deposit_shift(c)));
-    return d;
-}
+// Fixed-point scale 2^S of the deposit at the context's current time (the
+// same expression the plan kernel evaluates for the device-side scalars).
+int deposit_shift(const sipf_ctx* c) { return deposit_shift_at(c->log2_maxrel, c->time); }
 
 // Converts the integer accumulator to u_bar = a R_h summed: 2^-S e^logref / h^3.
-double acc_to_u_d(const sipf_ctx* c) {
-    return ldexp(exp(c->logref), -deposit_shift(c)) / (c->h * c->h * c->h);
-}
+double acc_to_u_d(const sipf_ctx* c) { return ldexp(c->exp_logref, -deposit_shift(c)) / c->h3; }
 
 float acc_to_u(const sipf_ctx* c) { return static_cast<float>(acc_to_u_d(c)); }
 
-PushArgs push_args(const sipf_ctx* c, double dt, uint32_t n, int push) {
+// The device scalars of the next step (slot of the current buffer) from the
+// host's step count and time; after set-up operations that do not advance a
+// step (set_state, load, resample).
+int write_scalars(sipf_ctx* c) {
+    StepScalars hs;
+    fill_step_scalars(&hs, static_cast<uint32_t>(c->step + 1), c->time, c->log2_maxrel,
+                      c->exp_logref, c->h3);
+    SIPF_CUDA(c, cudaMemcpyAsync(c->dsc + c->cur, &hs, sizeof(hs), cudaMemcpyHostToDevice,
+                                 c->stream));
+    SIPF_CUDA(c, cudaStreamSynchronize(c->stream));
+    return SIPF_OK;
+}
+
+// Constants of the scalars from logref and maxrel.
+void set_mass_reference(sipf_ctx* c) {
+    c->log2_maxrel = log2(c->maxrel);
+    c->exp_logref = exp(c->logref);
+}
+
+PushArgs push_args(const sipf_ctx* c, double dt, int push) {
     PushArgs a;
     a.H = c->H;
     a.drift = static_cast<float>(c->p.chi * dt / c->h);
     a.noise = static_cast<float>(sqrt(2.0 * c->p.Du * dt) / c->h);
     a.tau = static_cast<float>(dt);
-    a.n = n;
     a.k0 = static_cast<uint32_t>(c->p.seed);
     a.k1 = static_cast<uint32_t>(c->p.seed >> 32);
     for (int r = 0; r < 10; ++r) {
@@ -156,10 +158,9 @@ PushArgs push_args(const sipf_ctx* c, double dt, uint32_t n, int push) {
     return a;
 }
 
-SpectralArgs spectral_args(const sipf_ctx* c, double dt, float react_scale, int full) {
+SpectralArgs spectral_args(const sipf_ctx* c, double dt, int full) {
     SpectralArgs s;
     s.tau = static_cast<float>(dt);
-    s.react_scale = react_scale;
     s.gamma = static_cast<float>(c->p.gamma);
     s.alpha = static_cast<float>(c->p.alpha);
     s.v_update = c->p.v_update;
@@ -195,13 +196,13 @@ int bin_from(sipf_ctx* c, int b) {
     SIPF_CUDA(c, cudaMemsetAsync(c->cnt[b], 0, sizeof(int) * c->ntiles, c->stream));
     SIPF_CUDA(c, cudaMemsetAsync(c->ovf[b], 0, sizeof(int), c->stream));
     SIPF_CUDA(c, launch_tile_count(c, b, c->cnt[b]));
-    SIPF_CUDA(c, launch_plan(c, b, 1, c->stream));   // layout of buffer b ^ 1 from the tile counts
+    SIPF_CUDA(c, launch_plan(c, b, 1, c->stream, 0.0));   // layout of buffer b ^ 1 from the tile counts
     SIPF_CUDA(c, launch_plan_flat(c));           // items: the raw input array
     c->cur = b;
-    const PushArgs a = push_args(c, 0.0, 0, 0);
-    SIPF_CUDA(c, launch_step_kernel(c, a, deposit_args(c), 0, 1));
+    const PushArgs a = push_args(c, 0.0, 0);
+    SIPF_CUDA(c, launch_step_kernel(c, a, 0, 1));
     c->cur = b ^ 1;
-    SIPF_CUDA(c, launch_plan(c, b ^ 1, 1, c->stream));
+    SIPF_CUDA(c, launch_plan(c, b ^ 1, 1, c->stream, 0.0));
     return SIPF_OK;
 }
 
@@ -209,8 +210,8 @@ int bin_initial(sipf_ctx* c) { return bin_from(c, 1); }
 
 // Deposit the current particles into the accumulator (Alg. 1).
 int deposit_current(sipf_ctx* c) {
-    const PushArgs a = push_args(c, 0.0, 0, 0);
-    SIPF_CUDA(c, launch_step_kernel(c, a, deposit_args(c), 1, 0));
+    const PushArgs a = push_args(c, 0.0, 0);
+    SIPF_CUDA(c, launch_step_kernel(c, a, 1, 0));
     return SIPF_OK;
 }
 
@@ -238,20 +239,25 @@ cudaError_t prof_mark(sipf_ctx* c, int k) {
     return e ? cudaEventRecord(e, c->stream) : cudaSuccess;
 }
 
+// Host bookkeeping of one step (the device side advances its scalars in the
+// plan kernel).
+void advance_host(sipf_ctx* c, double dt) {
+    c->cur ^= 1;
+    c->step += 1;
+    c->time += dt;
+}
+
 int enqueue_step(sipf_ctx* c, double dt) {
-    const uint32_t n = static_cast<uint32_t>(c->step + 1);
-    const PushArgs a = push_args(c, dt, n, 1);
-    const DepositArgs d = deposit_args(c);
-    const float u_scale = acc_to_u(c);
-    const SpectralArgs sa = spectral_args(c, dt, u_scale, 1);
+    const PushArgs a = push_args(c, dt, 1);
+    const SpectralArgs sa = spectral_args(c, dt, 1);
     SIPF_CUDA(c, prof_mark(c, 0));
-    SIPF_CUDA(c, launch_step_kernel(c, a, d, 1, 1));
+    SIPF_CUDA(c, launch_step_kernel(c, a, 1, 1));
     SIPF_CUDA(c, prof_mark(c, 1));
-    // the plan of the next step's items and layout needs only the counts: it
-    // runs on the side stream while the spectral passes run on the main one
+    // the plan of the next step's items, layout and scalars needs only the
+    // counts: it runs on the side stream while the spectral passes run on the main one
     SIPF_CUDA(c, cudaEventRecord(c->ev_fork, c->stream));
     SIPF_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-    SIPF_CUDA(c, launch_plan(c, c->cur ^ 1, 1, c->side));
+    SIPF_CUDA(c, launch_plan(c, c->cur ^ 1, 1, c->side, dt));
     SIPF_CUDA(c, cudaEventRecord(c->ev_join, c->side));
     for (int pass = 0; pass < 3; ++pass) {
         SIPF_CUDA(c, launch_spectral_pass(c, sa, pass));
@@ -259,9 +265,71 @@ int enqueue_step(sipf_ctx* c, double dt) {
     }
     SIPF_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     if (c->prof_on && c->prof_steps < kProfMaxSteps) c->prof_steps += 1;
-    c->cur ^= 1;
-    c->step += 1;
-    c->time += dt;
+    advance_host(c, dt);
+    return SIPF_OK;
+}
+
+// Two steps of size dt captured once (per dt and buffer parity) as a CUDA
+// graph; *out = nullptr when the stream cannot capture (the legacy default
+// stream) or capture fails, in which case the caller enqueues the steps.
+int step_pair_graph(sipf_ctx* c, double dt, cudaGraphExec_t* out) {
+    *out = nullptr;
+    if (!c->stream) return SIPF_OK;
+    for (const auto& g : c->graphs)
+        if (g.dt == dt && g.parity == c->cur) {
+            *out = g.exec;
+            return SIPF_OK;
+        }
+    const int cur0 = c->cur;
+    const int64_t step0 = c->step;
+    const double time0 = c->time;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return SIPF_OK;
+    }
+    int r = enqueue_step(c, dt);
+    if (r == SIPF_OK) r = enqueue_step(c, dt);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    c->cur = cur0;
+    c->step = step0;
+    c->time = time0;
+    cudaGraphExec_t exec = nullptr;
+    const bool ok = r == SIPF_OK && e == cudaSuccess && graph &&
+                    cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+        cudaGetLastError();
+        return SIPF_OK;
+    }
+    if (c->graphs.size() >= 4) {
+        cudaGraphExecDestroy(c->graphs.front().exec);
+        c->graphs.erase(c->graphs.begin());
+    }
+    c->graphs.push_back({dt, cur0, exec});
+    *out = exec;
+    return SIPF_OK;
+}
+
+// k steps: pairs replay the captured two-step graph (not while tracing),
+// the rest is enqueued launch by launch; both run the same kernels with the
+// same arguments.
+int run_steps(sipf_ctx* c, double dt, int64_t k) {
+    int64_t done = 0;
+    if (k >= 2 && !c->prof_on) {
+        cudaGraphExec_t exec = nullptr;
+        const int r = step_pair_graph(c, dt, &exec);
+        if (r != SIPF_OK) return r;
+        for (; exec && done + 2 <= k; done += 2) {
+            SIPF_CUDA(c, cudaGraphLaunch(exec, c->stream));
+            advance_host(c, dt);
+            advance_host(c, dt);
+        }
+    }
+    for (; done < k; ++done) {
+        const int r = enqueue_step(c, dt);
+        if (r != SIPF_OK) return r;
+    }
     return SIPF_OK;
 }
 
@@ -350,6 +418,7 @@ int sipf_create(const sipf_grid* grid, int64_t N, const sipf_params* params, voi
     c->H = grid->H;
     c->L = grid->L;
     c->h = grid->L / grid->H;
+    c->h3 = c->h * c->h * c->h;
     for (int k = 0; k < 3; ++k) c->origin[k] = grid->origin[k];
     c->N = N;
     c->p = *params;
@@ -390,6 +459,7 @@ int sipf_create(const sipf_grid* grid, int64_t N, const sipf_params* params, voi
          dalloc(&c->specW, spec) == cudaSuccess && dalloc(&c->specV, spec) == cudaSuccess &&
          dalloc(&c->specB, spec) == cudaSuccess && dalloc(&c->twiddle, c->H) == cudaSuccess &&
          dalloc(&c->status, 1) == cudaSuccess && dalloc(&c->voff, 1) == cudaSuccess &&
+         dalloc(&c->dsc, 2) == cudaSuccess &&
          dalloc(&c->diag_tmp, diag_scratch_doubles()) == cudaSuccess &&
          dalloc(&c->diag_ll, diag_scratch_ll()) == cudaSuccess &&
          dalloc(&c->diag_out, 8) == cudaSuccess;
@@ -415,6 +485,7 @@ int sipf_create(const sipf_grid* grid, int64_t N, const sipf_params* params, voi
     if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, H3 * sizeof(long long), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->G, 0, 4 * H3 * sizeof(float), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->dsc, 0, 2 * sizeof(StepScalars), c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         free_all(c);
@@ -459,6 +530,7 @@ int sipf_set_state(sipf_ctx* c, const float* x, const double* mass, const uint32
     }
     c->logref = M0 > 0.0 ? log(M0 / static_cast<double>(N)) : 0.0;
     c->maxrel = M0 > 0.0 ? amax / exp(c->logref) : 1.0;
+    set_mass_reference(c);
     c->step = 0;
     c->time = 0.0;
     // upload into buffer 1 (unordered), then bin into buffer 0
@@ -514,7 +586,7 @@ int sipf_set_state(sipf_ctx* c, const float* x, const double* mass, const uint32
         // w^(0) into the gather array; grad v^(0) from the DFT of v^(0) (tau = 0)
         e = cudaMemcpy2DAsync(c->G + 3, 4 * sizeof(float), c->w, sizeof(float), sizeof(float), H3,
                               cudaMemcpyDeviceToDevice, c->stream);
-        if (e == cudaSuccess) e = launch_spectral_step(c, spectral_args(c, 0.0, 0.0f, 0));
+        if (e == cudaSuccess) e = launch_spectral_step(c, spectral_args(c, 0.0, 0));
     }
     if (e == cudaSuccess && r == SIPF_OK) e = cudaStreamSynchronize(c->stream);
     if (xin) cudaFree(xin);
@@ -522,6 +594,8 @@ int sipf_set_state(sipf_ctx* c, const float* x, const double* mass, const uint32
     if (e != cudaSuccess) return cuda_fail(c, e, "sipf_set_state");
     if (r != SIPF_OK) return r;
     r = check_status(c);
+    if (r != SIPF_OK) return r;
+    r = write_scalars(c);
     if (r != SIPF_OK) return r;
     c->state_set = true;
     return SIPF_OK;
@@ -533,11 +607,7 @@ int sipf_step(sipf_ctx* c, double dt, int64_t k) {
     if (!(isfinite(dt) && dt > 0.0 && dt <= 0.5))
         return fail(c, SIPF_EINVAL, "dt must satisfy 0 < dt <= 0.5");
     if (k < 0) return fail(c, SIPF_EINVAL, "k must be >= 0");
-    for (int64_t i = 0; i < k; ++i) {
-        const int r = enqueue_step(c, dt);
-        if (r != SIPF_OK) return r;
-    }
-    return SIPF_OK;
+    return run_steps(c, dt, k);
 }
 
 int sipf_fields(sipf_ctx* c, uint32_t mask, float* dst, int where) {
@@ -705,6 +775,8 @@ void sipf_destroy(sipf_ctx* c) {
         cudaStreamSynchronize(c->side);
         cudaStreamDestroy(c->side);
     }
+    for (const auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     free_all(c);
@@ -830,8 +902,10 @@ int sipf_load(const char* path, void* stream, sipf_ctx** out) {
     c->time = hd.time;
     c->logref = hd.logref;
     c->maxrel = hd.maxrel;
+    set_mass_reference(c);
     if (e == cudaSuccess) {
         r = bin_initial(c);
+        if (r == SIPF_OK) r = write_scalars(c);
         if (r == SIPF_OK) e = cudaStreamSynchronize(c->stream);
     }
     if (e != cudaSuccess || r != SIPF_OK || check_status(c) != SIPF_OK) {
@@ -858,6 +932,7 @@ int sipf_resample(sipf_ctx* c, double ratio, int32_t* resampled) {
     if (r != SIPF_OK) return fail(c, r, "sipf_resample: " + why);
     if (done) {
         r = bin_from(c, dst);
+        if (r == SIPF_OK) r = write_scalars(c);
         if (r != SIPF_OK) return r;
         SIPF_CUDA(c, cudaStreamSynchronize(c->stream));
         r = check_status(c);
@@ -948,10 +1023,45 @@ int sipf_ensemble_step(sipf_ensemble* e, const double* dt, int64_t k) {
             return SIPF_EINVAL;
         }
     }
-    // step by step, member after member: every member's work goes to its own
-    // stream, so the kernels of different members run concurrently
-    for (int64_t n = 0; n < k; ++n) {
-        for (size_t i = 0; i < e->members.size(); ++i) {
+    // every member's work goes to its own stream, so the kernels of different
+    // members run concurrently; pairs of steps replay each member's captured
+    // two-step graph, interleaved member after member
+    const size_t M = e->members.size();
+    std::vector<cudaGraphExec_t> exec(M, nullptr);
+    for (size_t i = 0; i < M && k >= 2; ++i) {
+        sipf_ctx* c = e->members[i];
+        if (c->prof_on) continue;
+        const int r = step_pair_graph(c, dt[i], &exec[i]);
+        if (r != SIPF_OK) {
+            e->last_error = "member " + std::to_string(i) + ": " + c->last_error;
+            return r;
+        }
+    }
+    int64_t n = 0;
+    for (; n + 2 <= k; n += 2) {
+        for (size_t i = 0; i < M; ++i) {
+            sipf_ctx* c = e->members[i];
+            int r = SIPF_OK;
+            if (exec[i]) {
+                const cudaError_t ce = cudaGraphLaunch(exec[i], c->stream);
+                if (ce == cudaSuccess) {
+                    advance_host(c, dt[i]);
+                    advance_host(c, dt[i]);
+                } else {
+                    r = cuda_fail(c, ce, "cudaGraphLaunch");
+                }
+            } else {
+                r = enqueue_step(c, dt[i]);
+                if (r == SIPF_OK) r = enqueue_step(c, dt[i]);
+            }
+            if (r != SIPF_OK) {
+                e->last_error = "member " + std::to_string(i) + ": " + c->last_error;
+                return r;
+            }
+        }
+    }
+    for (; n < k; ++n) {
+        for (size_t i = 0; i < M; ++i) {
             const int r = enqueue_step(e->members[i], dt[i]);
             if (r != SIPF_OK) {
                 e->last_error = "member " + std::to_string(i) + ": " + e->members[i]->last_error;

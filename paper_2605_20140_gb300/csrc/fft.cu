@@ -297,8 +297,9 @@ __global__ void __launch_bounds__(Cfg<H>::NT1)
                  const float* __restrict__ w, unsigned long long* __restrict__ acc,
                  float* v_out, float2* __restrict__ gM, float2* __restrict__ gW,
                  float2* __restrict__ gV, const float2* __restrict__ twg,
-                 const float* __restrict__ voff) {
+                 const float* __restrict__ voff, const StepScalars* __restrict__ sc) {
     constexpr int NT = Cfg<H>::NT1, KXP = kxp<H>(), HK = H / 2 + 1, RP = rowp<H>();
+    const float u_scale = sc->u_scale;   // u_bar per accumulator unit
     extern __shared__ float2 sm[];
     float2* Z = sm;               // [H][RP]: m* + i w*
     float2* Vb = Z + H * RP;      // v^n: [H/2][RP] row pairs, then [H][KXP] half rows
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT1)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     float ms, ws;
-                    react(a, vv[e], mm[e], ww[e], acc_to_float(qq[e]) * a.react_scale, ms, ws,
+                    react(a, vv[e], mm[e], ww[e], acc_to_float(qq[e]) * u_scale, ms, ws,
                           vn[e]);
                     Z[y * RP + x0 + e] = make_float2(ms, ws);
                     vrow[2 * (x0 + e) + (y & 1)] = vn[e] - c0;
@@ -667,8 +668,10 @@ __global__ void __launch_bounds__(kSxNT)
     k_sx_forward(SpectralArgs a, const float* v, const float* __restrict__ m,
                  const float* __restrict__ w, unsigned long long* __restrict__ acc, float* v_out,
                  float2* __restrict__ gM, float2* __restrict__ gW, float2* __restrict__ gV,
-                 const float2* __restrict__ twg, const float* __restrict__ voff) {
+                 const float2* __restrict__ twg, const float* __restrict__ voff,
+                 const StepScalars* __restrict__ sc) {
     constexpr int RB = kSxRows, NT = kSxNT, KXP = kxp<H>(), HK = H / 2 + 1, RP = rowp<H>();
+    const float u_scale = sc->u_scale;   // u_bar per accumulator unit
     static_assert((RB / 2) * RP <= RB * KXP, "row pairs fit in the half-row space");
     extern __shared__ float2 sm[];
     float2* buf = sm;              // 3 fields: [RB/2][RP] row pairs, then [RB][KXP] half rows
@@ -694,7 +697,7 @@ __global__ void __launch_bounds__(kSxNT)
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             float ms, ws;
-            react(a, vv[e], mm[e], ww[e], acc_to_float(qq[e]) * a.react_scale, ms, ws, vn[e]);
+            react(a, vv[e], mm[e], ww[e], acc_to_float(qq[e]) * u_scale, ms, ws, vn[e]);
             const float val[3] = {ms, ws, vn[e] - c0};
 #pragma unroll
             for (int f = 0; f < 3; ++f)
@@ -875,7 +878,7 @@ cudaError_t spectral_pass_split(sipf_ctx* c, const SpectralArgs& a, int pass) {
     if (pass == 0) {
         k_sx_forward<H><<<dim3(H / RB, H), kSxNT, smx1, c->stream>>>(
             a, c->v, c->m, c->w, reinterpret_cast<unsigned long long*>(c->acc), c->v, c->specM,
-            c->specW, c->specV, c->twiddle, c->voff);
+            c->specW, c->specV, c->twiddle, c->voff, c->dsc + c->cur);
         k_sx_columns<H, -1><<<gy, kSxNT, smy, c->stream>>>(a, c->specM, c->specW, c->specV,
                                                              nullptr, nullptr, c->twiddle, 0);
     } else if (pass == 1) {
@@ -914,7 +917,7 @@ cudaError_t spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass) {
     if (pass == 0) {
         k_forward_xy<H><<<H, Cfg<H>::NT1, sm1, c->stream>>>(
             a, c->v, c->m, c->w, reinterpret_cast<unsigned long long*>(c->acc), c->v, c->specM,
-            c->specW, c->specV, c->twiddle, c->voff);
+            c->specW, c->specV, c->twiddle, c->voff, c->dsc + c->cur);
     } else if (pass == 1) {
         k_z_multiply<H><<<dim3(H, 4, (KXP + zcols<H>() - 1) / zcols<H>()), Cfg<H>::NT2, sm2,
                             c->stream>>>(a, c->specM, c->specW, c->specV,

@@ -241,8 +241,8 @@ __device__ __forceinline__ int round_signed_small(float v) {
 
 template <int ORDER>
 __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
-    k_step(PushArgs a, DepositArgs d, const float4* __restrict__ G, Buf src, Buf dst, Layout L,
-           const Item* __restrict__ items, const int* __restrict__ n_items,
+    k_step(PushArgs a, const StepScalars* __restrict__ sc, const float4* __restrict__ G, Buf src,
+           Buf dst, Layout L, const Item* __restrict__ items, const int* __restrict__ n_items,
            unsigned long long* __restrict__ acc, int do_deposit, int do_move,
            int* __restrict__ status) {
     using DB = DepBlock<ORDER>;
@@ -259,6 +259,8 @@ __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
     const int lane = threadIdx.x & 31;
     const float Hf = __int2float_rn(H);
     const int total = *n_items;
+    const uint32_t step_n = sc->n;                 // Philox counter word 0 of this step
+    const float dscale = sc->deposit_scale;        // 2^S of the fixed-point deposit
     for (int i = threadIdx.x; i < DB::N; i += kNT) {
         dep[i] = 0;
         dep64[i] = 0;
@@ -337,7 +339,7 @@ __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
                 // a_p R_h(X_p, node) h^3 in units of exp(logref) 2^-S as integers
                 // (below 2^20 in magnitude by the choice of S; the clamp keeps a
                 // non-finite mass inside the rounding's range)
-                const float ea = fminf(__fmul_rn(expf(d2f_bits(pl)), d.scale), 2097152.0f);
+                const float ea = fminf(__fmul_rn(expf(d2f_bits(pl)), dscale), 2097152.0f);
                 const float wx0 = __fsub_rn(1.0f, c.fx), wy0 = __fsub_rn(1.0f, c.fy);
                 const float wz0 = __fsub_rn(1.0f, c.fz);
                 const int lx = c.cx - tx0, ly = c.cy - ty0, lz = c.cz - tz0;
@@ -431,7 +433,7 @@ __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
                     const float inc = log1pf(__fmul_rn(a.tau, __fsub_rn(rho, 1.0f)));
                     pl = pl + f2d_bits(inc);
                     // Euler-Maruyama push in grid units
-                    const float3 nz = box_muller(philox4x32_10(make_uint4(a.n, 0u, pid, 0u), a.rk));
+                    const float3 nz = box_muller(philox4x32_10(make_uint4(step_n, 0u, pid, 0u), a.rk));
                     px = wrap(__fmaf_rn(a.noise, nz.x, __fmaf_rn(a.drift, g.x, px)), Hf, &bad);
                     py = wrap(__fmaf_rn(a.noise, nz.y, __fmaf_rn(a.drift, g.y, py)), Hf, &bad);
                     pz = wrap(__fmaf_rn(a.noise, nz.z, __fmaf_rn(a.drift, g.z, pz)), Hf, &bad);
@@ -561,12 +563,14 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* smem, int* total
 // their offsets in the compacted particle order; and, when next_cnt is not
 // null, the bucket layout of the other buffer for the next step (capacity
 // count + count/8 + 32, rounded up to a multiple of 4) with its counters
-// reset.
+// reset; with next_sc, the next step's scalars from those of this step.
 __global__ void __launch_bounds__(kPlanNT)
     k_plan(int ntiles, int T, const int* __restrict__ cnt, const int* __restrict__ cap,
            const int* __restrict__ bstart, const int* __restrict__ ovf, int ovf_base, Item* items,
            int* n_items, int* next_bstart, int* next_cap, int* next_cnt, int* next_ovf,
-           int* __restrict__ status) {
+           int* __restrict__ status, const StepScalars* __restrict__ cur_sc,
+           StepScalars* __restrict__ next_sc, double dt, double log2_maxrel, double exp_logref,
+           double h3) {
     __shared__ int smem[33];
     const int per = (ntiles + kPlanNT - 1) / kPlanNT;
     const int t0 = threadIdx.x * per;
@@ -625,6 +629,10 @@ __global__ void __launch_bounds__(kPlanNT)
         *n_items = n;
         if (next_ovf) *next_ovf = 0;
         if (tot_fill + no < 0) atomicOr(status, kStatusTotal);
+        // scalars of the next step: n + 1 at time t_n = t_{n-1} + dt
+        if (next_sc)
+            fill_step_scalars(next_sc, cur_sc->n + 1u, cur_sc->time + dt, log2_maxrel, exp_logref,
+                              h3);
     }
 }
 
@@ -962,25 +970,26 @@ int step_grid(sipf_ctx* c) {
     return g > 0 ? g : 1;
 }
 
-cudaError_t launch_step_kernel(sipf_ctx* c, const PushArgs& a, const DepositArgs& d,
-                               int do_deposit, int do_move) {
+cudaError_t launch_step_kernel(sipf_ctx* c, const PushArgs& a, int do_deposit, int do_move) {
     const int b = c->cur;
     auto kernel = c->p.p2g_order == 4 ? k_step<4> : k_step<2>;
     kernel<<<c->step_blocks, kNT, 0, c->stream>>>(
-        a, d, reinterpret_cast<const float4*>(c->G), buf_of(c, b), buf_of(c, b ^ 1),
+        a, c->dsc + b, reinterpret_cast<const float4*>(c->G), buf_of(c, b), buf_of(c, b ^ 1),
         layout_of(c, b ^ 1), c->items, c->n_items,
         reinterpret_cast<unsigned long long*>(c->acc), do_deposit, do_move, c->status);
     return cudaGetLastError();
 }
 
 // Items of buffer `b` and, with next_layout, the layout of b ^ 1.
-cudaError_t launch_plan(sipf_ctx* c, int b, int next_layout, cudaStream_t s) {
+cudaError_t launch_plan(sipf_ctx* c, int b, int next_layout, cudaStream_t s, double dt) {
     const int o = b ^ 1;
     k_plan<<<1, kPlanNT, 0, s>>>(
         c->ntiles, c->H / 8, c->cnt[b], c->cap[b], c->bstart[b], c->ovf[b], c->ovf_base, c->items,
         c->n_items, next_layout ? c->bstart[o] : nullptr,
         next_layout ? c->cap[o] : nullptr, next_layout ? c->cnt[o] : nullptr,
-        next_layout ? c->ovf[o] : nullptr, c->status);
+        next_layout ? c->ovf[o] : nullptr, c->status,
+        // b is the buffer the step just wrote: its slot is the next step's, o's the current one
+        c->dsc + o, dt > 0.0 ? c->dsc + b : nullptr, dt, c->log2_maxrel, c->exp_logref, c->h3);
     return cudaGetLastError();
 }
 

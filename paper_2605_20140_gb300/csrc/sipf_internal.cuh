@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <string>
@@ -60,17 +61,47 @@ struct PushArgs {
     float drift;      // chi * tau / h      (grid units per unit grad v)
     float noise;      // sqrt(2 Du tau) / h (grid units per standard normal)
     float tau;
-    uint32_t n;       // step index (Philox counter word 0)
     uint32_t k0, k1;  // Philox key
     uint32_t rk[20];  // Philox round keys (k0 + r 0x9E3779B9, k1 + r 0xBB67AE85), r = 0..9
     int push;         // 0: positions unchanged (pure binning)
 };
 
-// Deposit scaling: contribution of a particle to a corner node is
-// exp(log a - logref) * weight, stored as the integer round(value * 2^S) < 2^31.
-struct DepositArgs {
-    float scale;      // 2^S
+// Per-step scalars, kept in device memory (one slot per buffer parity) so
+// that the kernels of a step read them there rather than as launch
+// arguments: the plan kernel of step n writes step n + 1's slot, and a
+// captured sequence of steps can be replayed.
+struct StepScalars {
+    uint32_t n;            // the step being taken (Philox counter word 0), from 1
+    uint32_t pad;
+    double time;           // t_{n-1}
+    float deposit_scale;   // 2^S: contribution of a particle to a node is
+                           // exp(log a - logref) * weight * 2^S, rounded to an integer
+    float u_scale;         // u_bar per accumulator unit: 2^-S exp(logref) / h^3
 };
+
+// S for the deposit at time t: one contribution is at most
+// max_p a_p / exp(logref) <= maxrel e^t (Lemma mass: a grows by at most
+// 1 + tau <= e^tau per step) and must stay below 2^20 after scaling, so the
+// sums of one 1024-particle item fit exactly in 32 bits.  Host and device
+// evaluate the same expression (an explicit fma), so they agree bit for bit.
+__host__ __device__ inline int deposit_shift_at(double log2_maxrel, double t) {
+    const double bound = fma(t, 1.4426950408889634, log2_maxrel) + 0.5;
+    int S = static_cast<int>(floor(20.0 - bound));
+    if (S > 40) S = 40;
+    if (S < -60) S = -60;
+    return S;
+}
+
+__host__ __device__ inline void fill_step_scalars(StepScalars* s, uint32_t n, double t,
+                                                  double log2_maxrel, double exp_logref,
+                                                  double h3) {
+    const int S = deposit_shift_at(log2_maxrel, t);
+    s->n = n;
+    s->pad = 0;
+    s->time = t;
+    s->deposit_scale = static_cast<float>(ldexp(1.0, S));
+    s->u_scale = static_cast<float>(ldexp(exp_logref, -S) / h3);
+}
 
 // A run of particles read by one block of the step kernel: [beg, end) of a
 // buffer, all in bucket `tile` (or tile = -1 for the overflow region / an
@@ -87,7 +118,6 @@ struct Item {
 // Spectral-step scalars.
 struct SpectralArgs {
     float tau;
-    float react_scale;     // converts the integer deposit accumulator to u_bar
     float gamma, alpha;
     int v_update;          // SIPF_V_*
     int diffusion;         // SIPF_DIFFUSION_*
@@ -167,6 +197,17 @@ struct sipf_ctx {
     void* rs_scratch = nullptr;      // residual resampling work space (allocated on first use)
     size_t rs_bytes = 0;
 
+    sipf::StepScalars* dsc = nullptr;      // [2] per-step scalars, slot = parity of the source buffer
+    double log2_maxrel = 0;          // log2(maxrel), exp(logref), h^3: constants of the scalars
+    double exp_logref = 1;
+    double h3 = 1;
+    struct StepGraph {
+        double dt;
+        int parity;
+        cudaGraphExec_t exec;
+    };
+    std::vector<StepGraph> graphs;   // captured two-step sequences, by (dt, parity)
+
     int* status = nullptr;           // device status word
     double* diag_tmp = nullptr;      // diagnostics partials
     double* diag_out = nullptr;      // 8 doubles
@@ -195,9 +236,10 @@ int item_size();
 size_t diag_scratch_doubles();
 size_t diag_scratch_ll();
 int scan_tiles(int n);
-cudaError_t launch_step_kernel(sipf_ctx* c, const PushArgs& a, const DepositArgs& d,
-                               int do_deposit, int do_move);
-cudaError_t launch_plan(sipf_ctx* c, int b, int next_layout, cudaStream_t s);
+cudaError_t launch_step_kernel(sipf_ctx* c, const PushArgs& a, int do_deposit, int do_move);
+// Items of buffer b and, with next_layout, the layout of b ^ 1; with dt > 0
+// also the scalars of the next step (slot b ^ 1) from those of slot b.
+cudaError_t launch_plan(sipf_ctx* c, int b, int next_layout, cudaStream_t s, double dt);
 cudaError_t launch_tile_count(sipf_ctx* c, int b, int* cnt);
 cudaError_t launch_plan_flat(sipf_ctx* c);
 cudaError_t launch_compact(sipf_ctx* c, int b, int out);

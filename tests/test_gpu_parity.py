@@ -594,3 +594,36 @@ def test_largest_configuration_sampled():
     assert abs(d["mass_grid"] - d["mass_particles"]) <= tol * M0
     assert M0 * (1 - wl.dt) <= d["mass_particles"] <= M0 * (1 + wl.dt)
     assert d["nonfinite"] == 0 and d["min_u"] >= 0 and d["min_v"] > 0
+
+
+def test_graph_replayed_steps_equal_single_steps():
+    """k >= 2 steps replay a captured two-step graph; single steps are
+    enqueued one launch at a time: same kernels, same bits, across a change
+    of dt, an odd count and a resampling in between (which flips the buffer
+    parity the graphs were captured for)."""
+    wl = workload("small", H=32, N=1 << 14)
+    outs = []
+    for graphs in (True, False):
+        stream = torch.cuda.Stream()
+        sim = sipf.Simulation(wl.H, wl.L, wl.origin, wl.N, wl.params, stream=stream.cuda_stream)
+        sim.set_state(wl.x, wl.mass, wl.ids, wl.v, wl.m, wl.w)
+        plan = [(wl.dt, 6), (0.5 * wl.dt, 3), (wl.dt, 5)]
+        for i, (dt, k) in enumerate(plan):
+            if graphs:
+                sim.step(dt, k)
+            else:
+                for _ in range(k):
+                    sim.step(dt, 1)
+            if i == 1:
+                sim.resample(0.0)
+        f = sim.fields()
+        s, l, ids = by_id(*sim.particle_state())
+        d = sim.diagnostics()
+        outs.append((f, s, l, d))
+        sim.close()
+    for k in outs[0][0]:
+        np.testing.assert_array_equal(outs[0][0][k], outs[1][0][k], err_msg=k)
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    np.testing.assert_array_equal(outs[0][2], outs[1][2])
+    assert outs[0][3]["step"] == outs[1][3]["step"] == 14
+    assert outs[0][3]["time"] == outs[1][3]["time"]
