@@ -2,7 +2,7 @@
 """Throughput of the SIPF-W step on the 128^3-grid / 2^22-particle workload.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sipf|reference]
-                    [--workload headline|ensemble]
+                    [--workload headline|ensemble|serve [--rate R]]
 
 One step = one pass of the whole hot path (the particle step: deposit,
 gather, push, mass update and binning; the bucket plan; three spectral
@@ -13,7 +13,9 @@ independent replica on its own GPU (no data-path collective); the timed
 region is bracketed by a barrier and the slowest rank's time is used.
 
 --workload ensemble instead times 64 uneven independent runs advanced
-together (one stream each) against the same runs one at a time (runs/s).
+together (one stream each) against the same runs one at a time (runs/s);
+--workload serve times continuous batching of Poisson-arriving requests
+(p50/p99 time-to-result).
 
 --impl reference times the FP64 oracle on the host cores (the paper ships
 no code; the oracle is the reference arm), each step on a bounded sample of
@@ -409,10 +411,97 @@ def run_ensemble(args, rank, world, local):
     return 0
 
 
+def run_serve(args, rank, world, local):
+    """Continuous batching: requests drawn like the ensemble's runs plus a
+    simulated time T ~ U[0.05, 0.5] (T/dt steps), arriving as a Poisson
+    process of rate --rate per second, served from one GPU under a 150 GB
+    device-memory budget; time-to-result = collection time - arrival time."""
+    import torch
+    from paper_2605_20140_gb300 import sipf
+    from sipf_inputs import ensemble_workloads
+
+    torch.cuda.set_device(local)
+    R, rate = args.requests, args.rate
+    rng = np.random.default_rng(np.random.PCG64(9000 + rank))
+    runs = ensemble_workloads(R, seed=100 + rank)
+    steps = [max(1, int(round(rng.uniform(0.05, 0.5) / w.dt))) for w in runs]
+    arrival = np.cumsum(rng.exponential(1.0 / rate, R))
+    budget = 150 * 10 ** 9
+    # warm-up: one request per grid size (graph capture, kernel attributes)
+    with sipf.Server(budget) as warm:
+        seen = {}
+        for w in runs:
+            if w.H not in seen:
+                seen[w.H] = warm.submit(w.H, w.L, w.origin, w.N, w.params, w.x, w.mass, w.v,
+                                        w.m, w.w, w.dt, 4)
+        while warm.advance(2):
+            pass
+        for rid in warm.poll():
+            warm.collect(rid, 0)
+    mask = sipf.FIELD_U | sipf.FIELD_V | sipf.FIELD_M | sipf.FIELD_W
+    ttr, rid_of = {}, {}
+    clocks = ClockSampler(local)
+    _barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    srv = sipf.Server(budget)
+    try:
+        t0 = time.perf_counter()
+        nxt = 0
+        while len(ttr) < R:
+            now = time.perf_counter() - t0
+            while nxt < R and arrival[nxt] <= now:
+                w = runs[nxt]
+                rid_of[srv.submit(w.H, w.L, w.origin, w.N, w.params, w.x, w.mass, w.v, w.m,
+                                  w.w, w.dt, steps[nxt])] = nxt
+                nxt += 1
+            pending = srv.advance(args.quantum)
+            for rid in srv.poll():
+                srv.collect(rid, mask)
+                i = rid_of[rid]
+                ttr[i] = time.perf_counter() - t0 - arrival[i]
+            if pending == 0 and nxt < R:
+                time.sleep(max(0.0, arrival[nxt] - (time.perf_counter() - t0)))
+        makespan = time.perf_counter() - t0
+        st = srv.stats()
+    finally:
+        srv.close()
+    clk = clocks.stop()
+    lat = np.array([ttr[i] for i in range(R)])
+    p50, p99 = float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
+    p99 = _max_over_ranks(p99, world)
+    total_steps = sum(steps)
+    h2d = sum(w.x.nbytes + w.mass.nbytes + 3 * w.v.nbytes for w in runs)
+    d2h = sum(4 * w.v.nbytes for w in runs)
+    if rank == 0:
+        line = {
+            "metric": f"p99 time-to-result, Poisson arrivals at {rate:g} requests/s",
+            "value": p99, "unit": "s", "n_gpus": world, "steps": total_steps,
+            "warmup": len(seen), "ms_per_step": 1e3 * makespan / total_steps,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (f64 log-mass and reductions)", "data": "synthetic",
+            "config": {"workload": f"serve: {R} requests drawn as the ensemble's runs "
+                                   "(H in {32, 48, 64, 96}, N = 2^U[14, 20]) with "
+                                   "T ~ U[0.05, 0.5], dt 1e-3; 150 GB budget",
+                       "quantum_steps": args.quantum, "parallelism": f"replicas x{world}"},
+            "p50_s": p50, "p99_s": p99, "mean_s": float(lat.mean()),
+            "requests_per_s": R / makespan, "makespan_s": makespan,
+            "peak_device_bytes": st["peak"],
+            "e2e": {"value": p99, "unit": "s", "h2d_bytes_per_step": h2d / total_steps,
+                    "d2h_bytes_per_step": d2h / total_steps},
+            "gpu_launches": 5 * total_steps, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--workload", choices=["headline", "ensemble"], default="headline")
+    ap.add_argument("--workload", choices=["headline", "ensemble", "serve"], default="headline")
+    ap.add_argument("--rate", type=float, default=100.0, help="serve: arrivals per second")
+    ap.add_argument("--requests", type=int, default=128, help="serve: number of requests")
+    ap.add_argument("--quantum", type=int, default=2, help="serve: steps per round")
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["sipf", "reference"], default="sipf")
@@ -429,6 +518,8 @@ def main():
             return run_reference(args, rank, world)
         if args.workload == "ensemble":
             return run_ensemble(args, rank, world, local)
+        if args.workload == "serve":
+            return run_serve(args, rank, world, local)
         return run_sipf(args, rank, world, local)
     finally:
         if world > 1:

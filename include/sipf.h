@@ -224,6 +224,52 @@ int sipf_ensemble_sync(sipf_ensemble* ens);
 const char* sipf_ensemble_last_error(const sipf_ensemble* ens);
 void sipf_ensemble_destroy(sipf_ensemble* ens);
 
+/* Device memory of a context: sipf_context_bytes gives the bytes
+ * sipf_create(grid, N, params) will allocate (a negative SIPF_E* code for
+ * arguments sipf_create would reject), without touching the GPU;
+ * sipf_device_bytes the bytes a context did allocate (the two agree).  Not
+ * included: the work space of sipf_resample, allocated on its first call. */
+int64_t sipf_context_bytes(const sipf_grid* grid, int64_t N, const sipf_params* params);
+int64_t sipf_device_bytes(const sipf_ctx* ctx);
+
+/* Serving with continuous batching: independent runs (requests) submitted at
+ * any time, admitted first come first served while their device memory
+ * (sipf_context_bytes) fits the budget, advanced together a few steps per
+ * scheduling round (each on a stream of its own, pairs of steps replayed as
+ * graphs), and released as soon as their results are collected.  A
+ * request's results are bit for bit those of the same run alone.  All calls
+ * are host calls of one thread.
+ *
+ * sipf_server_create: budget_bytes > 0.  sipf_server_submit: the run's grid,
+ * N, parameters, initial state (host buffers, copied during the call: x
+ * 3*N physical coordinates SoA, mass N, v, m, w H^3 each; ids 0..N-1) and its
+ * length (steps of dt); *id receives the request id.  Errors: SIPF_EINVAL
+ * (NULL, bad dt or steps, arguments sipf_create would reject, a request
+ * larger than the whole budget).  sipf_server_advance: admits what fits,
+ * enqueues up to `quantum` steps of every running request, marks finished
+ * the requests whose last step has completed on the device; *pending (may
+ * be NULL) = queued + unfinished requests.  sipf_server_poll: up to
+ * `capacity` ids of newly finished requests into ids[]; *count = how many.
+ * sipf_server_collect: copies the fields of a finished request (mask and
+ * layout as sipf_fields, host buffer) and releases its device memory; mask
+ * 0 only releases.  sipf_server_stats: device bytes in use and at most in
+ * use so far, queued and admitted-but-uncollected requests.  Errors of a
+ * request's own calls are returned by the call that made them, with
+ * sipf_server_last_error describing them. */
+typedef struct sipf_server sipf_server;
+int sipf_server_create(int64_t budget_bytes, sipf_server** out);
+int sipf_server_submit(sipf_server* srv, const sipf_grid* grid, int64_t N,
+                       const sipf_params* params, const float* x, const double* mass,
+                       const float* v, const float* m, const float* w, double dt,
+                       int64_t steps, int64_t* id);
+int sipf_server_advance(sipf_server* srv, int64_t quantum, int32_t* pending);
+int sipf_server_poll(sipf_server* srv, int64_t* ids, int32_t capacity, int32_t* count);
+int sipf_server_collect(sipf_server* srv, int64_t id, uint32_t mask, float* dst);
+int sipf_server_stats(const sipf_server* srv, int64_t* in_use, int64_t* peak, int32_t* queued,
+                      int32_t* live);
+const char* sipf_server_last_error(const sipf_server* srv);
+void sipf_server_destroy(sipf_server* srv);
+
 /* Checkpoint / resume.  The paper has no checkpoint; what is saved is the
  * state of the scheme after step n of Alg. 3: the particles X^n (grid units)
  * with log a^n and ids, the grids v^n, m^n, w^n and the gather array

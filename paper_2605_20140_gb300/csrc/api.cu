@@ -72,6 +72,48 @@ cudaError_t dalloc(T** p, size_t n) {
     return cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
 }
 
+// Sizes of a context's device arrays (shared by sipf_create and the memory
+// estimate sipf_context_bytes).
+struct CtxSizes {
+    size_t H3, spec;
+    int ntiles, ovf_base, max_items;
+    int64_t buf_slots;
+};
+
+CtxSizes ctx_sizes(int H, int64_t N) {
+    CtxSizes z;
+    z.H3 = static_cast<size_t>(H) * H * H;
+    z.spec = static_cast<size_t>(H) * H * (H / 2 + 2);
+    const int T = H / 8;
+    z.ntiles = T * T * T;
+    const int64_t bucket_slots = N + N / 8 + 36 * static_cast<int64_t>(z.ntiles) + 64;
+    z.ovf_base = static_cast<int>((bucket_slots + 3) & ~int64_t{3});
+    z.buf_slots = z.ovf_base + N + 8;
+    const int K = item_size();
+    z.max_items = static_cast<int>(2 * ((N + K - 1) / K) + z.ntiles + 2);
+    return z;
+}
+
+// Device bytes sipf_create allocates (the resampling work space, allocated
+// on first use, is not included).
+size_t ctx_device_bytes(int H, int64_t N, bool filter) {
+    const CtxSizes z = ctx_sizes(H, N);
+    const size_t S = static_cast<size_t>(z.buf_slots);
+    size_t b = 2 * (S * (3 * sizeof(float) + sizeof(double) + sizeof(uint32_t)) +
+                    3 * static_cast<size_t>(z.ntiles) * sizeof(int) + sizeof(int));
+    b += static_cast<size_t>(z.max_items) * sizeof(Item) + 2 * sizeof(int);
+    b += z.H3 * sizeof(int32_t) + (z.H3 + 1) * sizeof(int32_t) +
+         (static_cast<size_t>(scan_tiles(static_cast<int>(z.H3))) + 1) * sizeof(int32_t);
+    b += z.H3 * sizeof(long long) + 3 * z.H3 * sizeof(float) + 4 * z.H3 * sizeof(float);
+    b += 4 * z.spec * sizeof(float2) + static_cast<size_t>(H) * sizeof(float2);
+    b += sizeof(int) + sizeof(float) + 2 * sizeof(StepScalars);
+    b += diag_scratch_doubles() * sizeof(double) + diag_scratch_ll() * sizeof(long long) +
+         8 * sizeof(double);
+    if (filter) b += z.spec * sizeof(float2);
+    if (H > 128) b += 2 * z.spec * sizeof(float2);
+    return b;
+}
+
 void free_all(sipf_ctx* c) {
     void* ptrs[] = {c->sx[0], c->sx[1], c->sy[0], c->sy[1], c->sz[0], c->sz[1], c->dl[0],
                     c->dl[1], c->id[0], c->id[1], c->bstart[0], c->bstart[1], c->cap[0],
@@ -384,6 +426,12 @@ struct CkptArray {
 
 }  // namespace
 
+namespace sipf {
+// k steps of a context with the same launch path as sipf_step (graph pairs
+// when possible), for the request scheduler.
+int run_steps_for(sipf_ctx* c, double dt, int64_t k) { return run_steps(c, dt, k); }
+}  // namespace sipf
+
 extern "C" {
 
 const char* sipf_strerror(int code) {
@@ -425,48 +473,50 @@ int sipf_create(const sipf_grid* grid, int64_t N, const sipf_params* params, voi
     if (c->p.p2g_order == 0) c->p.p2g_order = 2;
     c->stream = static_cast<cudaStream_t>(stream);
     cudaGetDevice(&c->device);
-    const size_t H3 = static_cast<size_t>(c->H) * c->H * c->H;
+    const CtxSizes z = ctx_sizes(c->H, N);
+    const size_t H3 = z.H3, spec = z.spec;
     c->kxp = c->H / 2 + 2;
-    const size_t spec = static_cast<size_t>(c->H) * c->H * c->kxp;
-    const int T = c->H / 8;
-    c->ntiles = T * T * T;
-    const int64_t bucket_slots = N + N / 8 + 36 * static_cast<int64_t>(c->ntiles) + 64;
-    c->ovf_base = static_cast<int>((bucket_slots + 3) & ~int64_t{3});
-    c->buf_slots = c->ovf_base + N + 8;
+    c->ntiles = z.ntiles;
+    c->ovf_base = z.ovf_base;
+    c->buf_slots = z.buf_slots;
     if (c->buf_slots >= (int64_t{1} << 31)) {
         delete c;
         return SIPF_EINVAL;
     }
-    const int K = item_size();
-    c->max_items = static_cast<int>(2 * ((N + K - 1) / K) + c->ntiles + 2);
+    c->max_items = z.max_items;
     const size_t S = static_cast<size_t>(c->buf_slots);
+    // every allocation of the context is counted in dev_bytes
+    auto da = [c](auto** p, size_t n) {
+        c->dev_bytes += n * sizeof(**p);
+        return dalloc(p, n);
+    };
     bool ok = true;
     for (int b = 0; b < 2; ++b) {
-        ok = ok && dalloc(&c->sx[b], S) == cudaSuccess && dalloc(&c->sy[b], S) == cudaSuccess &&
-             dalloc(&c->sz[b], S) == cudaSuccess && dalloc(&c->dl[b], S) == cudaSuccess &&
-             dalloc(&c->id[b], S) == cudaSuccess &&
-             dalloc(&c->bstart[b], c->ntiles) == cudaSuccess &&
-             dalloc(&c->cap[b], c->ntiles) == cudaSuccess &&
-             dalloc(&c->cnt[b], c->ntiles) == cudaSuccess && dalloc(&c->ovf[b], 1) == cudaSuccess;
+        ok = ok && da(&c->sx[b], S) == cudaSuccess && da(&c->sy[b], S) == cudaSuccess &&
+             da(&c->sz[b], S) == cudaSuccess && da(&c->dl[b], S) == cudaSuccess &&
+             da(&c->id[b], S) == cudaSuccess &&
+             da(&c->bstart[b], c->ntiles) == cudaSuccess &&
+             da(&c->cap[b], c->ntiles) == cudaSuccess &&
+             da(&c->cnt[b], c->ntiles) == cudaSuccess && da(&c->ovf[b], 1) == cudaSuccess;
     }
-    ok = ok && dalloc(&c->items, static_cast<size_t>(c->max_items)) == cudaSuccess &&
-         dalloc(&c->n_items, 1) == cudaSuccess && dalloc(&c->work, 1) == cudaSuccess &&
-         dalloc(&c->count, H3) == cudaSuccess && dalloc(&c->cell_start, H3 + 1) == cudaSuccess &&
-         dalloc(&c->scan_tmp, static_cast<size_t>(scan_tiles(static_cast<int>(H3))) + 1) == cudaSuccess &&
-         dalloc(&c->acc, H3) == cudaSuccess && dalloc(&c->v, H3) == cudaSuccess &&
-         dalloc(&c->m, H3) == cudaSuccess && dalloc(&c->w, H3) == cudaSuccess &&
-         dalloc(&c->G, 4 * H3) == cudaSuccess && dalloc(&c->specM, spec) == cudaSuccess &&
-         dalloc(&c->specW, spec) == cudaSuccess && dalloc(&c->specV, spec) == cudaSuccess &&
-         dalloc(&c->specB, spec) == cudaSuccess && dalloc(&c->twiddle, c->H) == cudaSuccess &&
-         dalloc(&c->status, 1) == cudaSuccess && dalloc(&c->voff, 1) == cudaSuccess &&
-         dalloc(&c->dsc, 2) == cudaSuccess &&
-         dalloc(&c->diag_tmp, diag_scratch_doubles()) == cudaSuccess &&
-         dalloc(&c->diag_ll, diag_scratch_ll()) == cudaSuccess &&
-         dalloc(&c->diag_out, 8) == cudaSuccess;
+    ok = ok && da(&c->items, static_cast<size_t>(c->max_items)) == cudaSuccess &&
+         da(&c->n_items, 1) == cudaSuccess && da(&c->work, 1) == cudaSuccess &&
+         da(&c->count, H3) == cudaSuccess && da(&c->cell_start, H3 + 1) == cudaSuccess &&
+         da(&c->scan_tmp, static_cast<size_t>(scan_tiles(static_cast<int>(H3))) + 1) == cudaSuccess &&
+         da(&c->acc, H3) == cudaSuccess && da(&c->v, H3) == cudaSuccess &&
+         da(&c->m, H3) == cudaSuccess && da(&c->w, H3) == cudaSuccess &&
+         da(&c->G, 4 * H3) == cudaSuccess && da(&c->specM, spec) == cudaSuccess &&
+         da(&c->specW, spec) == cudaSuccess && da(&c->specV, spec) == cudaSuccess &&
+         da(&c->specB, spec) == cudaSuccess && da(&c->twiddle, c->H) == cudaSuccess &&
+         da(&c->status, 1) == cudaSuccess && da(&c->voff, 1) == cudaSuccess &&
+         da(&c->dsc, 2) == cudaSuccess &&
+         da(&c->diag_tmp, diag_scratch_doubles()) == cudaSuccess &&
+         da(&c->diag_ll, diag_scratch_ll()) == cudaSuccess &&
+         da(&c->diag_out, 8) == cudaSuccess;
     const bool filter = params->H0 > 0.0 && params->H0 < grid->H;
-    if (ok && filter) ok = dalloc(&c->specA, spec) == cudaSuccess;
+    if (ok && filter) ok = da(&c->specA, spec) == cudaSuccess;
     if (ok && c->H > 128)
-        ok = dalloc(&c->specDx, spec) == cudaSuccess && dalloc(&c->specDy, spec) == cudaSuccess;
+        ok = da(&c->specDx, spec) == cudaSuccess && da(&c->specDy, spec) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_all(c);
@@ -940,6 +990,20 @@ int sipf_resample(sipf_ctx* c, double ratio, int32_t* resampled) {
     }
     if (resampled) *resampled = done;
     return SIPF_OK;
+}
+
+int64_t sipf_context_bytes(const sipf_grid* grid, int64_t N, const sipf_params* params) {
+    std::string why;
+    if (!grid || !params || N < 1 || N >= (int64_t{1} << 31) || !supported_H(grid->H) ||
+        check_params(params, &why) != SIPF_OK)
+        return SIPF_EINVAL;
+    if (ctx_sizes(grid->H, N).buf_slots >= (int64_t{1} << 31)) return SIPF_EINVAL;
+    const bool filter = params->H0 > 0.0 && params->H0 < grid->H;
+    return static_cast<int64_t>(ctx_device_bytes(grid->H, N, filter));
+}
+
+int64_t sipf_device_bytes(const sipf_ctx* c) {
+    return c ? static_cast<int64_t>(c->dev_bytes) : SIPF_EINVAL;
 }
 
 int sipf_describe(const sipf_ctx* c, sipf_grid* grid, int64_t* N, sipf_params* params,

@@ -162,6 +162,7 @@ struct sipf_ctx {
     int ntiles = 0;                      // (H/8)^3
     int ovf_base = 0;                    // first slot of the overflow region
     int64_t buf_slots = 0;               // slots per buffer
+    size_t dev_bytes = 0;                // device memory allocated by sipf_create
     int* bstart[2] = {nullptr, nullptr}; // bucket layout per buffer
     int* cap[2] = {nullptr, nullptr};
     int* cnt[2] = {nullptr, nullptr};    // arrivals per bucket (incl. overflowed)
@@ -256,6 +257,8 @@ cudaError_t launch_normals(const uint32_t* ids, int64_t N, uint32_t n, uint64_t 
                            uint32_t* bits, cudaStream_t s);
 cudaError_t launch_conv_check(const float* f, const double* d, int n, int* mismatches,
                               cudaStream_t s);
+// api.cu
+int run_steps_for(sipf_ctx* c, double dt, int64_t k);
 // resample.cu
 int resample_device(sipf_ctx* c, int src, int dst, double ratio, int* done, std::string* err);
 // fft.cu

@@ -38,7 +38,9 @@ EXPORTED = (
     "sipf_deposit_noalloc", "sipf_save", "sipf_load",
     "sipf_describe", "sipf_resample", "sipf_ensemble_create", "sipf_ensemble_member",
     "sipf_ensemble_step", "sipf_ensemble_sync", "sipf_ensemble_last_error",
-    "sipf_ensemble_destroy",
+    "sipf_ensemble_destroy", "sipf_context_bytes", "sipf_device_bytes", "sipf_server_create",
+    "sipf_server_submit", "sipf_server_advance", "sipf_server_poll", "sipf_server_collect",
+    "sipf_server_stats", "sipf_server_last_error", "sipf_server_destroy",
 )
 PROFILE_GROUPS = 4
 
@@ -110,6 +112,18 @@ def load() -> ctypes.CDLL:
         "sipf_ensemble_sync": ([P], I32),
         "sipf_ensemble_last_error": ([P], ctypes.c_char_p),
         "sipf_ensemble_destroy": ([P], None),
+        "sipf_context_bytes": ([ctypes.POINTER(sipf_grid), I64, ctypes.POINTER(sipf_params)], I64),
+        "sipf_device_bytes": ([P], I64),
+        "sipf_server_create": ([I64, ctypes.POINTER(P)], I32),
+        "sipf_server_submit": ([P, ctypes.POINTER(sipf_grid), I64, ctypes.POINTER(sipf_params),
+                                P, P, P, P, P, ctypes.c_double, I64, ctypes.POINTER(I64)], I32),
+        "sipf_server_advance": ([P, I64, ctypes.POINTER(I32)], I32),
+        "sipf_server_poll": ([P, P, I32, ctypes.POINTER(I32)], I32),
+        "sipf_server_collect": ([P, I64, U32, P], I32),
+        "sipf_server_stats": ([P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I32),
+                               ctypes.POINTER(I32)], I32),
+        "sipf_server_last_error": ([P], ctypes.c_char_p),
+        "sipf_server_destroy": ([P], None),
         "sipf_describe": ([P, ctypes.POINTER(sipf_grid), ctypes.POINTER(I64),
                            ctypes.POINTER(sipf_params), ctypes.POINTER(I64),
                            ctypes.POINTER(ctypes.c_double)], I32),
@@ -426,6 +440,84 @@ class Ensemble:
                 m.ctx = None          # owned by the ensemble
             sipf_ensemble_destroy(self.ens)
             self.ens = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def sipf_context_bytes(grid: sipf_grid, N: int, params: sipf_params) -> int:
+    return int(load().sipf_context_bytes(ctypes.byref(grid), int(N), ctypes.byref(params)))
+
+
+def _check_srv(code: int, srv):
+    if code != SIPF_OK:
+        lib = load()
+        msg = lib.sipf_strerror(code).decode()
+        extra = lib.sipf_server_last_error(srv).decode() if srv else ""
+        raise SipfError(code, f"{msg}: {extra}" if extra else msg)
+
+
+class Server:
+    """Continuous-batching request scheduler (host calls of one thread)."""
+
+    def __init__(self, budget_bytes: int):
+        out = ctypes.c_void_p()
+        _check(load().sipf_server_create(int(budget_bytes), ctypes.byref(out)))
+        self.srv = out.value
+        self.H = {}
+
+    def submit(self, H, L, origin, N, params, x, mass, v, m, w, dt, steps) -> int:
+        xs = np.ascontiguousarray(np.asarray(x, dtype=np.float32).T)
+        mass = np.ascontiguousarray(mass, dtype=np.float64)
+        v, m, w = (np.ascontiguousarray(a, dtype=np.float32) for a in (v, m, w))
+        rid = ctypes.c_int64()
+        _check_srv(load().sipf_server_submit(
+            self.srv, ctypes.byref(make_grid(H, L, origin)), int(N),
+            ctypes.byref(make_params(params)), xs.ctypes.data, mass.ctypes.data, v.ctypes.data,
+            m.ctypes.data, w.ctypes.data, float(dt), int(steps), ctypes.byref(rid)), self.srv)
+        self.H[rid.value] = H
+        return rid.value
+
+    def advance(self, quantum: int = 2) -> int:
+        pending = ctypes.c_int32()
+        _check_srv(load().sipf_server_advance(self.srv, int(quantum), ctypes.byref(pending)),
+                   self.srv)
+        return pending.value
+
+    def poll(self, capacity: int = 256) -> list:
+        ids = np.zeros(capacity, dtype=np.int64)
+        n = ctypes.c_int32()
+        _check_srv(load().sipf_server_poll(self.srv, ids.ctypes.data, capacity, ctypes.byref(n)),
+                   self.srv)
+        return [int(i) for i in ids[:n.value]]
+
+    def collect(self, rid: int, mask: int = 127) -> dict:
+        H = self.H.pop(rid)
+        nsel = bin(mask).count("1")
+        buf = np.empty(max(nsel, 1) * H ** 3, dtype=np.float32)
+        _check_srv(load().sipf_server_collect(self.srv, int(rid), mask, buf.ctypes.data),
+                   self.srv)
+        out, off = {}, 0
+        for b, name in enumerate(FIELD_NAMES):
+            if mask & (1 << b):
+                out[name] = buf[off * H ** 3:(off + 1) * H ** 3].reshape(H, H, H)
+                off += 1
+        return out
+
+    def stats(self) -> dict:
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        q, l = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().sipf_server_stats(self.srv, ctypes.byref(a), ctypes.byref(b),
+                                        ctypes.byref(q), ctypes.byref(l)))
+        return {"in_use": a.value, "peak": b.value, "queued": q.value, "live": l.value}
+
+    def close(self):
+        if self.srv:
+            load().sipf_server_destroy(self.srv)
+            self.srv = None
 
     def __enter__(self):
         return self

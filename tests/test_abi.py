@@ -134,3 +134,47 @@ def test_ensemble_calls_reject_bad_arguments_without_touching_the_gpu(lib):
     assert lib.sipf_ensemble_member(None, 0) is None
     assert lib.sipf_ensemble_last_error(None) == b""
     lib.sipf_ensemble_destroy(None)
+
+
+def test_context_bytes_without_touching_the_gpu(lib):
+    p = sipf.sipf_params()
+    p.chi, p.Du, p.Dm, p.Dw, p.alpha, p.beta, p.gamma = 0.01, 1e-3, 1e-3, 1e-2, 10, 0.1, 0.5
+    b = lambda H, N: sipf.sipf_context_bytes(sipf.make_grid(H, 1.0), N, p)
+    assert b(32, 1000) > 0 and b(32, 2000) > b(32, 1000) and b(64, 1000) > b(32, 1000)
+    spec = 64 * 64 * (64 // 2 + 2) * 8
+    p.H0 = 10.0                                   # the filtered v spectrum adds one spectrum
+    assert b(64, 1000) == sipf.sipf_context_bytes(sipf.make_grid(64, 1.0), 1000, p)
+    filt = b(64, 1000)
+    p.H0 = 0.0
+    assert filt - b(64, 1000) == spec
+    assert b(40, 1000) == sipf.SIPF_EINVAL and b(32, 0) == sipf.SIPF_EINVAL
+    assert lib.sipf_device_bytes(None) == sipf.SIPF_EINVAL
+
+
+def test_server_queues_and_validates_without_touching_the_gpu(lib):
+    out = ctypes.c_void_p()
+    assert lib.sipf_server_create(0, ctypes.byref(out)) == sipf.SIPF_EINVAL
+    assert lib.sipf_server_advance(None, 1, None) == sipf.SIPF_EINVAL
+    assert lib.sipf_server_last_error(None) == b""
+    lib.sipf_server_destroy(None)
+    from sipf_inputs import workload
+    wl = workload("small", H=32, N=2048)
+    need = sipf.sipf_context_bytes(sipf.make_grid(32, 1.0), 2048, sipf.make_params(wl.params))
+    srv = sipf.Server(10 * need)
+    try:
+        rid = srv.submit(wl.H, wl.L, wl.origin, wl.N, wl.params, wl.x, wl.mass, wl.v, wl.m, wl.w,
+                         wl.dt, 4)
+        assert rid == 1 and srv.stats() == {"in_use": 0, "peak": 0, "queued": 1, "live": 0}
+        with pytest.raises(sipf.SipfError):
+            srv.submit(wl.H, wl.L, wl.origin, wl.N, wl.params, wl.x, wl.mass, wl.v, wl.m, wl.w,
+                       0.0, 4)
+    finally:
+        srv.close()
+    small = sipf.Server(need - 1)                 # larger than the whole budget
+    try:
+        with pytest.raises(sipf.SipfError) as e:
+            small.submit(wl.H, wl.L, wl.origin, wl.N, wl.params, wl.x, wl.mass, wl.v, wl.m,
+                         wl.w, wl.dt, 4)
+        assert e.value.code == sipf.SIPF_EINVAL
+    finally:
+        small.close()
