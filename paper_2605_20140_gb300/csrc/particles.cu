@@ -18,9 +18,10 @@
 // integers, summed exactly, so the density does not depend on particle order
 // and needs no float atomics), gathers grad v and w at X^(n-1), draws the Philox normals,
 // pushes, updates the log-mass, and writes the particle into its new tile's
-// bucket.  Slots are reserved per (item, neighbour tile) with one global
-// atomic; a one-block plan kernel then builds the next step's items and the
-// next bucket layout from the counts.
+// bucket straight from registers: the lanes of a warp bound for the same
+// tile reserve consecutive slots with one global atomic.  A one-block plan
+// kernel then builds the next step's items and the next bucket layout from
+// the counts.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -211,23 +212,15 @@ constexpr int kPT = 4;                    // particles per thread and item
 constexpr int kItem = kNT * kPT;          // particles per item
 constexpr int kBlock = 9 * 9 * 9;         // nodes of a tile's gather block
 
-// Per-item staging of the pushed particles between the two phases.
-struct Staged {
-    float x[kItem], y[kItem], z[kItem];
-    double l[kItem];
-    uint32_t id[kItem];
-    int tile[kItem];      // destination tile
-    int slot[kItem];      // neighbour index (< 27) << 22 | rank, or -1 (far / overflow item)
-};
-
 // Deposit node block of a tile for assignment order ORDER: local node
 // coordinates [-DO, 8 + DO] per axis (trilinear: the cells' corners 0..8;
-// R^(4): one more node on each side for the star arms).
+// R^(4): one more node on each side for the star arms).  MIN_BLOCKS: blocks
+// per SM the register budget is set for (48 and 60 registers per thread).
 template <int ORDER> struct DepBlock {
     static constexpr int DO = ORDER == 4 ? 1 : 0;
     static constexpr int B = 9 + 2 * DO;
     static constexpr int N = B * B * B;
-    static constexpr int MIN_BLOCKS = ORDER == 4 ? 3 : 4;
+    static constexpr int MIN_BLOCKS = ORDER == 4 ? 4 : 5;
     static __device__ __forceinline__ int idx(int lx, int ly, int lz) {
         return ((lz + DO) * B + (ly + DO)) * B + (lx + DO);
     }
@@ -249,12 +242,6 @@ __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
     __shared__ int dep[DB::N];              // node sums of the item (exact: |sum| < 2^31)
     __shared__ long long dep64[DB::N];      // node sums of the tile's items so far
     __shared__ float4 gblk[kBlock];         // (dv/dx, dv/dy, dv/dz, w) on the tile's 9^3 nodes
-    __shared__ Staged st;
-    __shared__ int nb_cnt[27];
-    __shared__ int nb_base[27];
-    __shared__ int nb_tile[27];     // tile index, bucket start and capacity of the
-    __shared__ int nb_start[27];    // 27 tiles around the item's tile
-    __shared__ int nb_cap[27];
     const int H = a.H, T = H >> 3;
     const int lane = threadIdx.x & 31;
     const float Hf = __int2float_rn(H);
@@ -305,18 +292,8 @@ __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
                     gblk[q] = __ldg(G + (nz * H + ny) * H + nx);
                 }
             }
-            if (threadIdx.x < 27 && do_move && tile >= 0) {
-                const int k = threadIdx.x;
-                const int nx = it.tx + k % 3 - 1, ny = it.ty + (k / 3) % 3 - 1, nz = it.tz + k / 9 - 1;
-                const int nt = (((nz + T) % T) * T + (ny + T) % T) * T + (nx + T) % T;
-                nb_tile[k] = nt;
-                nb_start[k] = L.bstart[nt];
-                nb_cap[k] = L.cap[nt];
-            }
         }
-        const int ttx = it.tx, tty = it.ty, ttz = it.tz;
         const int tx0 = cx0, ty0 = cy0, tz0 = cz0;
-        if (threadIdx.x < 27) nb_cnt[threadIdx.x] = 0;
         __syncthreads();
         int bad = 0;
         for (int j = 0; j < kPT; ++j) {
@@ -439,31 +416,36 @@ __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
                     pz = wrap(__fmaf_rn(a.noise, nz.z, __fmaf_rn(a.drift, g.z, pz)), Hf, &bad);
                 }
                 const Cell cn = locate(px, py, pz, H);
-                const int ntx = cn.cx >> 3, nty = cn.cy >> 3, ntz = cn.cz >> 3;
-                const int nt = (ntz * T + nty) * T + ntx;
-                int nb = -1;
-                if (tile >= 0) {
-                    int ddx = ntx - ttx, ddy = nty - tty, ddz = ntz - ttz;
-                    ddx = ddx == T - 1 ? -1 : ddx == 1 - T ? 1 : ddx;
-                    ddy = ddy == T - 1 ? -1 : ddy == 1 - T ? 1 : ddy;
-                    ddz = ddz == T - 1 ? -1 : ddz == 1 - T ? 1 : ddz;
-                    if (ddx >= -1 && ddx <= 1 && ddy >= -1 && ddy <= 1 && ddz >= -1 && ddz <= 1)
-                        nb = ((ddz + 1) * 3 + (ddy + 1)) * 3 + (ddx + 1);
-                }
-                // rank within this item among particles bound for the same neighbour tile
-                const int nkey = valid && nb >= 0 ? nb : -1;
-                const unsigned peers = __match_any_sync(kFull, nkey);
+                const int nt = valid ? (((cn.cz >> 3) * T + (cn.cy >> 3)) * T + (cn.cx >> 3)) : -1;
+                // slots in the destination bucket: one atomic per warp and tile (the
+                // lanes bound for the same tile take consecutive slots), then the
+                // particle is written straight from registers; a full bucket sends
+                // it to the overflow region
+                const unsigned peers = __match_any_sync(kFull, nt);
                 const int leader = __ffs(peers) - 1;
-                int old = 0;
-                if (nkey >= 0 && lane == leader) old = atomicAdd(nb_cnt + nb, __popc(peers));
-                old = __shfl_sync(kFull, old, leader);
-                st.x[e] = px;
-                st.y[e] = py;
-                st.z[e] = pz;
-                st.l[e] = pl;
-                st.id[e] = pid;
-                st.tile[e] = valid ? nt : -2;
-                st.slot[e] = nb >= 0 ? (nb << 22) | (old + __popc(peers & ((1u << lane) - 1u))) : -1;
+                int base = 0;
+                if (nt >= 0 && lane == leader) base = atomicAdd(L.cnt + nt, __popc(peers));
+                base = __shfl_sync(kFull, base, leader);
+                if (nt >= 0) {
+                    const int slot = base + __popc(peers & ((1u << lane) - 1u));
+                    int dest = -1;
+                    if (slot < __ldg(L.cap + nt)) {
+                        dest = __ldg(L.bstart + nt) + slot;
+                    } else {
+                        const int o = atomicAdd(L.ovf, 1);
+                        if (o < L.ovf_cap)
+                            dest = L.ovf_base + o;
+                        else
+                            atomicOr(status, kStatusSlot);
+                    }
+                    if (dest >= 0) {
+                        dst.sx[dest] = px;
+                        dst.sy[dest] = py;
+                        dst.sz[dest] = pz;
+                        dst.dl[dest] = pl;
+                        dst.id[dest] = pid;
+                    }
+                }
             }
         }
         if (bad & 1) atomicOr(status, kStatusNonfinite);
@@ -476,49 +458,6 @@ __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
                 if (v) {
                     dep64[j] += v;
                     dep[j] = 0;
-                }
-            }
-        }
-        if (do_move) {
-            if (threadIdx.x < 27 && nb_cnt[threadIdx.x] > 0)
-                nb_base[threadIdx.x] = atomicAdd(L.cnt + nb_tile[threadIdx.x], nb_cnt[threadIdx.x]);
-            __syncthreads();
-            for (int j = 0; j < kPT; ++j) {
-                const int e = j * kNT + threadIdx.x;
-                const int nt = st.tile[e];
-                const int code = st.slot[e];
-                // far moves and overflow items: per-warp aggregated reservation
-                // (every lane takes part in the warp-collective calls)
-                const int fkey = (nt >= 0 && code < 0) ? nt : -1;
-                unsigned peers = 0u;
-                int old = 0;
-                if (__any_sync(kFull, fkey >= 0)) {
-                    peers = __match_any_sync(kFull, fkey);
-                    const int leader = __ffs(peers) - 1;
-                    if (fkey >= 0 && lane == leader) old = atomicAdd(L.cnt + nt, __popc(peers));
-                    old = __shfl_sync(kFull, old, leader);
-                }
-                if (nt < 0) continue;
-                const int nb = code >= 0 ? (code >> 22) : -1;
-                const int slot = nb >= 0 ? nb_base[nb] + (code & 0x3FFFFF)
-                                         : old + __popc(peers & ((1u << lane) - 1u));
-                const int cp = nb >= 0 ? nb_cap[nb] : L.cap[nt];
-                int dest = -1;
-                if (slot < cp) {
-                    dest = (nb >= 0 ? nb_start[nb] : L.bstart[nt]) + slot;
-                } else {
-                    const int o = atomicAdd(L.ovf, 1);
-                    if (o < L.ovf_cap)
-                        dest = L.ovf_base + o;
-                    else
-                        atomicOr(status, kStatusSlot);
-                }
-                if (dest >= 0) {
-                    dst.sx[dest] = st.x[e];
-                    dst.sy[dest] = st.y[e];
-                    dst.sz[dest] = st.z[e];
-                    dst.dl[dest] = st.l[e];
-                    dst.id[dest] = st.id[e];
                 }
             }
         }
