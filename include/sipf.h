@@ -75,8 +75,8 @@ typedef struct sipf_ctx sipf_ctx;
 
 /* Periodic box [origin, origin + L)^3 with H nodes per axis (paper Sec. 2.1;
  * Omega = [-L/2, L/2]^3 there, origin = -L/2).  H must be a multiple of 8
- * of the form 2^a 3^b up to 256: 8, 16, 24, 32, 48, 64, 72, 96, 128, 144,
- * 192 or 256. */
+ * of the form 2^a 3^b up to 512: 8, 16, 24, 32, 48, 64, 72, 96, 128, 144,
+ * 192, 216, 256, 288, 384, 432 or 512. */
 typedef struct {
     int32_t H;
     double L;

@@ -35,7 +35,7 @@ int cuda_fail(sipf_ctx* c, cudaError_t e, const char* where) {
 bool supported_H(int H) {
     switch (H) {
         case 8: case 16: case 24: case 32: case 48: case 64: case 72: case 96: case 128:
-        case 144: case 192: case 256:
+        case 144: case 192: case 216: case 256: case 288: case 384: case 432: case 512:
             return true;
         default:
             return false;

@@ -198,29 +198,37 @@ __device__ __forceinline__ void stage1_from(float2* out, Load load) {
     __syncthreads();
 }
 
-// Radix plan of a length-L transform: two or three Stockham stages
-// (R3 = 1: two).  Lengths are 2^a 3^b with 8 <= L <= 256.
+// Radix plan of a length-L transform: two to four Stockham stages (R3, R4 =
+// 1: fewer).  Lengths are 2^a 3^b with 8 <= L <= 512.
 template <int L> struct Radix;
-template <> struct Radix<8> { static constexpr int R1 = 4, R2 = 2, R3 = 1; };
-template <> struct Radix<16> { static constexpr int R1 = 4, R2 = 4, R3 = 1; };
-template <> struct Radix<24> { static constexpr int R1 = 8, R2 = 3, R3 = 1; };
-template <> struct Radix<32> { static constexpr int R1 = 8, R2 = 4, R3 = 1; };
-template <> struct Radix<48> { static constexpr int R1 = 16, R2 = 3, R3 = 1; };
-template <> struct Radix<64> { static constexpr int R1 = 8, R2 = 8, R3 = 1; };
-template <> struct Radix<72> { static constexpr int R1 = 8, R2 = 3, R3 = 3; };
-template <> struct Radix<96> { static constexpr int R1 = 8, R2 = 4, R3 = 3; };
-template <> struct Radix<128> { static constexpr int R1 = 16, R2 = 8, R3 = 1; };
-template <> struct Radix<144> { static constexpr int R1 = 16, R2 = 3, R3 = 3; };
-template <> struct Radix<192> { static constexpr int R1 = 16, R2 = 4, R3 = 3; };
-template <> struct Radix<256> { static constexpr int R1 = 16, R2 = 16, R3 = 1; };
+template <int A, int B, int C = 1, int D = 1>
+struct RadixPlan { static constexpr int R1 = A, R2 = B, R3 = C, R4 = D; };
+template <> struct Radix<8> : RadixPlan<4, 2> {};
+template <> struct Radix<16> : RadixPlan<4, 4> {};
+template <> struct Radix<24> : RadixPlan<8, 3> {};
+template <> struct Radix<32> : RadixPlan<8, 4> {};
+template <> struct Radix<48> : RadixPlan<16, 3> {};
+template <> struct Radix<64> : RadixPlan<8, 8> {};
+template <> struct Radix<72> : RadixPlan<8, 3, 3> {};
+template <> struct Radix<96> : RadixPlan<8, 4, 3> {};
+template <> struct Radix<128> : RadixPlan<16, 8> {};
+template <> struct Radix<144> : RadixPlan<16, 3, 3> {};
+template <> struct Radix<192> : RadixPlan<16, 4, 3> {};
+template <> struct Radix<216> : RadixPlan<8, 3, 3, 3> {};
+template <> struct Radix<256> : RadixPlan<16, 16> {};
+template <> struct Radix<288> : RadixPlan<16, 3, 3, 2> {};
+template <> struct Radix<384> : RadixPlan<16, 8, 3> {};
+template <> struct Radix<432> : RadixPlan<16, 3, 3, 3> {};
+template <> struct Radix<512> : RadixPlan<8, 8, 8> {};
 
 // The stages after the first of a batched length-L FFT.
 template <int L, int NTRANS, int ES, int TS, int NT, int SIGN>
 __device__ __forceinline__ void fft_rest(float2* buf, const float2* tw) {
-    constexpr int R1 = Radix<L>::R1, R2 = Radix<L>::R2, R3 = Radix<L>::R3;
-    static_assert(R1 * R2 * R3 == L, "radix plan");
+    constexpr int R1 = Radix<L>::R1, R2 = Radix<L>::R2, R3 = Radix<L>::R3, R4 = Radix<L>::R4;
+    static_assert(R1 * R2 * R3 * R4 == L, "radix plan");
     stage<L, R2, R1, NTRANS, ES, TS, NT, SIGN>(buf, tw);
     if constexpr (R3 > 1) stage<L, R3, R1 * R2, NTRANS, ES, TS, NT, SIGN>(buf, tw);
+    if constexpr (R4 > 1) stage<L, R4, R1 * R2 * R3, NTRANS, ES, TS, NT, SIGN>(buf, tw);
 }
 
 // Batched length-L FFT along one axis of a shared-memory array.
@@ -254,7 +262,12 @@ template <> struct Cfg<128> { static constexpr int NT1 = 1024, NT2 = 544, NT3 = 
 // H > 128 runs the per-axis pipeline; NT2 is the z pass over 32-column tiles
 template <> struct Cfg<144> { static constexpr int NT1 = 256, NT2 = 288, NT3 = 256; };
 template <> struct Cfg<192> { static constexpr int NT1 = 256, NT2 = 384, NT3 = 256; };
+template <> struct Cfg<216> { static constexpr int NT1 = 256, NT2 = 896, NT3 = 256; };
 template <> struct Cfg<256> { static constexpr int NT1 = 256, NT2 = 512, NT3 = 256; };
+template <> struct Cfg<288> { static constexpr int NT1 = 256, NT2 = 576, NT3 = 256; };
+template <> struct Cfg<384> { static constexpr int NT1 = 256, NT2 = 768, NT3 = 256; };
+template <> struct Cfg<432> { static constexpr int NT1 = 256, NT2 = 896, NT3 = 256; };
+template <> struct Cfg<512> { static constexpr int NT1 = 256, NT2 = 1024, NT3 = 256; };
 
 // kx columns per block of the z pass: the whole padded row up to H = 128
 template <int H> constexpr int zcols() { return H <= 128 ? H / 2 + 2 : 32; }
@@ -652,7 +665,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT3)
 }
 
 // ---------------------------------------------------------------- per-axis passes (H > 128)
-// A 256^2 complex plane does not fit in shared memory, so for H > 128 each
+// A plane above 128^2 does not fit in shared memory, so for H > 128 each
 // axis is transformed by its own kernel over small blocks of lines:
 //   sx_forward: rows of RB lines: reaction, x DFT (row pairs) -> half spectra
 //   sx_columns: columns (KB kx at a time) of one plane: y DFT, forward or
@@ -946,7 +959,12 @@ cudaError_t launch_spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass) {
         case 128: return spectral_pass<128>(c, a, pass);
         case 144: return spectral_pass_split<144>(c, a, pass);
         case 192: return spectral_pass_split<192>(c, a, pass);
+        case 216: return spectral_pass_split<216>(c, a, pass);
         case 256: return spectral_pass_split<256>(c, a, pass);
+        case 288: return spectral_pass_split<288>(c, a, pass);
+        case 384: return spectral_pass_split<384>(c, a, pass);
+        case 432: return spectral_pass_split<432>(c, a, pass);
+        case 512: return spectral_pass_split<512>(c, a, pass);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -14,7 +14,7 @@
 namespace sipf {
 
 constexpr int kTile = 8;            // cells per tile edge of the tile-major cell key
-constexpr int kMaxH = 256;          // largest grid of this build
+constexpr int kMaxH = 512;          // largest grid of this build
 
 // Device status bits (ORed into ctx->status by kernels, read by sipf_sync).
 constexpr int kStatusNonfinite = 1;   // a pushed position was NaN/inf (reset to 0)

@@ -83,7 +83,8 @@ def _create(lib, H=32, L=1.0, N=100, **kw):
     (dict(H=40), sipf.SIPF_EINVAL),
     (dict(H=36), sipf.SIPF_EINVAL),
     (dict(H=12), sipf.SIPF_EINVAL),
-    (dict(H=512), sipf.SIPF_EINVAL),
+    (dict(H=1024), sipf.SIPF_EINVAL),
+    (dict(H=40 * 8), sipf.SIPF_EINVAL),
     (dict(L=0.0), sipf.SIPF_EINVAL),
     (dict(L=float("nan")), sipf.SIPF_EINVAL),
     (dict(chi=-1.0), sipf.SIPF_EINVAL),

@@ -234,7 +234,7 @@ def test_fourth_order_deposit_matches_oracle(name, H, N):
         assert u.min() < 0       # the negative star weights survive the integer path
 
 
-@pytest.mark.parametrize("H", [8, 16, 24, 32, 48, 64, 72, 96, 128, 144, 192, 256])
+@pytest.mark.parametrize("H", [8, 16, 24, 32, 48, 64, 72, 96, 128, 144, 192, 216, 256])
 def test_initial_spectral_gradient(H):
     wl = workload("small", H=H, N=1024)
     sim = run_gpu(wl, 0)
@@ -627,3 +627,66 @@ def test_graph_replayed_steps_equal_single_steps():
     np.testing.assert_array_equal(outs[0][2], outs[1][2])
     assert outs[0][3]["step"] == outs[1][3]["step"] == 14
     assert outs[0][3]["time"] == outs[1][3]["time"]
+
+
+def _plane_wave(H, L, qv):
+    """cos(2 pi q.x / L) on the nodes, float32, built axis by axis."""
+    q = (np.arange(H) * (L / H)).astype(np.float64)
+    ax = [2 * np.pi * qv[k] * q / L for k in range(3)]
+    ph = ax[2][:, None, None] + ax[1][None, :, None] + ax[0][None, None, :]
+    return np.cos(ph).astype(np.float32), np.sin(ph).astype(np.float32)
+
+
+@pytest.mark.parametrize("H,mode", [(216, 0), (288, 1), (384, 0), (432, 1), (512, 0)])
+def test_large_grids_single_mode_decay_and_gradient(H, mode):
+    """Grids above 256 (four-stage radix plans, per-axis pipeline): the
+    spectral gradient of a plane wave and its decay over two steps against
+    the closed forms (massless particles, gamma = alpha = 0).
+
+    v is rounded to float32 on input (white noise of rms 2^-23/sqrt(12) per
+    node), and differentiation multiplies white noise by the rms wave number
+    (2 pi / L) H / sqrt(12), about 930 at H = 512; so the gradient is checked
+    by its projection on the wave (amplitude to 1e-5) and by the rms of the
+    rest (at most 4x that noise)."""
+    L, tau = 1.0, 0.01
+    qv = np.array([3, -2, 5])
+    cw, sw = _plane_wave(H, L, qv)
+    p = Params(chi=0.0, Du=0.0, Dm=0.03, Dw=0.07, alpha=0.0, beta=0.4, gamma=0.0, diffusion=mode)
+    rng = np.random.default_rng(H)
+    x = rng.random((256, 3)).astype(np.float32)
+    v = (1.0 + 0.3 * sw).astype(np.float32)
+    sim = sipf.Simulation(H, L, (0.0, 0.0, 0.0), 256, p)
+    sim.set_state(x, np.zeros(256), None, v, (1.5 * cw).astype(np.float32),
+                  (0.25 * cw).astype(np.float32))
+    g = sim.fields(sipf.FIELD_GX | sipf.FIELD_GY | sipf.FIELD_GZ)
+    c64 = cw.astype(np.float64)
+    cc = float(np.sum(c64 * c64))
+    noise = 4.0 * (2.0 ** -23 / math.sqrt(12.0)) * (2 * np.pi / L) * H / math.sqrt(12.0)
+    for k, name in enumerate(("gx", "gy", "gz")):
+        amp_ref = 0.3 * 2 * np.pi * qv[k] / L
+        gk = g[name].astype(np.float64)
+        amp = float(np.sum(gk * c64)) / cc
+        assert abs(amp - amp_ref) <= 1e-5 * abs(amp_ref), (name, amp, amp_ref)
+        rest = float(np.sqrt(np.mean((gk - amp * c64) ** 2)))
+        assert rest <= noise, (name, rest, noise)
+    del g
+    sim.step(tau, 2)
+    f = sim.fields(sipf.FIELD_M | sipf.FIELD_W)
+    sim.close()
+    k2 = (2 * np.pi / L) ** 2 * np.sum(qv ** 2)
+    if mode == 0:
+        fm, fw = 1 / (1 + tau * 0.4 + tau * 0.03 * k2), 1 / (1 + tau + tau * 0.07 * k2)
+    else:
+        fm, fw = math.exp(-tau * 0.03 * k2 - tau * 0.4), math.exp(-tau * 0.07 * k2 - tau)
+    assert np.max(np.abs(f["m"] - 1.5 * cw * fm ** 2)) <= 2e-6 * 1.5
+    assert np.max(np.abs(f["w"] - 0.25 * cw * fw ** 2)) <= 2e-6 * 0.25
+
+
+def test_steps_match_oracle_216_grid():
+    """A four-stage radix plan (216 = 8 * 3 * 3 * 3) in the per-axis pipeline:
+    two whole steps against the oracle."""
+    wl = workload("small", H=216, N=1 << 17)
+    sim = run_gpu(wl, 2)
+    st = O.run(oracle_state(wl), wl.dt, 2)
+    _compare(sim, st, wl)
+    sim.close()
