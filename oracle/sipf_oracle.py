@@ -32,6 +32,10 @@ Readings of the paper taken here (where it is silent or inconsistent):
 * Low-pass filter exp(-2 pi^2 |q|^2 / H0^2) (Alg. 3): off unless 0 < H0 < H;
   when on it multiplies the m and w spectra and the v spectrum used for
   grad v, never the stored v.
+* Regularised m source (Eq. m_reg): with sigma > 0 the source of m is
+  K_sigma * u_bar, K_sigma the density of N(0, sigma I_3) (sigma a variance,
+  in units of L^2), applied spectrally; the w source keeps u_bar.  Off by
+  default (sigma = 0), like the paper's experiments.
 * Deposit: u_bar(qh) = sum_p a_p R_h(X_p, qh) (Alg. 1; the extra factor
   u_hat(X_p) printed in Eq. def_u_overline is read as a typo).  R_h is the
   trilinear function, or (p2g_order = 4) the fourth-order R_h^(4) of
@@ -315,10 +319,25 @@ def eta(u):
     return 2.0 * u / (1.0 + u)
 
 
-def react(v, m, w, ubar, p, tau):
+def gaussian_smooth(f: np.ndarray, L: float, sigma: float) -> np.ndarray:
+    """K_sigma * f on the periodic grid, K_sigma the density of N(0, sigma I_3)
+    (Eq. m_reg): the DFT of f times the characteristic function
+    exp(-sigma |k|^2 / 2), k = 2 pi q / L."""
+    if sigma <= 0.0:
+        return np.asarray(f, dtype=np.float64).copy()
+    H = f.shape[0]
+    q = wavenumbers(H)
+    k2 = (2 * np.pi / L) ** 2 * (q[:, None, None] ** 2 + q[None, :, None] ** 2 +
+                                  q[None, None, :] ** 2)
+    return np.fft.ifftn(np.fft.fftn(f) * np.exp(-0.5 * sigma * k2)).real
+
+
+def react(v, m, w, ubar, p, tau, L=1.0):
     """R_tau: explicit Euler of S(u, g) = (-alpha m v; u; gamma v - eta(u) w),
-    with v taken implicitly as v/(1 + alpha tau m) (or explicitly)."""
-    m_star = m + tau * ubar
+    with v taken implicitly as v/(1 + alpha tau m) (or explicitly).  With
+    p.sigma > 0 the m source is the regularised K_sigma * u (Eq. m_reg); the
+    w source keeps u itself."""
+    m_star = m + tau * gaussian_smooth(ubar, L, getattr(p, "sigma", 0.0))
     w_star = w + tau * (p.gamma * v - eta(ubar) * w)
     if p.v_update == 0:
         v_new = v / (1.0 + p.alpha * tau * m)
@@ -402,7 +421,7 @@ def step(st: State, tau: float, normals: np.ndarray | None = None) -> State:
     s_new = wrap(s_new, H)
     loga_new = st.loga + np.log1p(tau * (rho(w_H) - 1.0))
     # Eq. g_hat_phy / k_q_update: reaction at n-1, then the diffusion solve.
-    v_new, m_star, w_star = react(st.v, st.m, st.w, ubar, p, tau)
+    v_new, m_star, w_star = react(st.v, st.m, st.w, ubar, p, tau, L)
     m_new = diffuse(m_star, L, p.Dm, p.beta, tau, p.diffusion, p.H0)
     w_new = diffuse(w_star, L, p.Dw, 1.0, tau, p.diffusion, p.H0)
     grad_new = spectral_gradient(v_new, L, p.H0)

@@ -66,6 +66,7 @@ class Params:
     H0: float = 0.0         # low-pass filter cut-off; 0 (or >= H) means off
     seed: int = 0           # Philox key for the Brownian increments
     p2g_order: int = 2      # particle-to-grid assignment: 2 trilinear, 4 the star stencil R^(4)
+    sigma: float = 0.0      # variance of the Gaussian K_sigma regularising the m source; 0 = off
 
 
 @dataclasses.dataclass

@@ -484,3 +484,40 @@ def test_r4_deposit_conserves_mass():
     a = rng.uniform(0.5, 2.0, 500)
     u = O.deposit4(s, a, H, 0.25)
     assert abs(u.sum() * 0.25 ** 3 - a.sum()) <= 1e-12 * a.sum()
+
+
+# ---------------------------------------------------------------- K_sigma-regularised m source
+
+def test_gaussian_smoothing_of_a_plane_wave_and_the_mean():
+    H, L, sigma = 16, 2.0, 0.003
+    q = np.arange(H) * (L / H)
+    Z, Y, X = np.meshgrid(q, q, q, indexing="ij")
+    qv = np.array([2, -3, 1])
+    f = 0.7 + np.cos(2 * np.pi * (qv[0] * X + qv[1] * Y + qv[2] * Z) / L)
+    g = O.gaussian_smooth(f, L, sigma)
+    k2 = (2 * np.pi / L) ** 2 * np.sum(qv ** 2)
+    want = 0.7 + np.exp(-0.5 * sigma * k2) * (f - 0.7)
+    assert np.max(np.abs(g - want)) <= 1e-13
+    np.testing.assert_array_equal(O.gaussian_smooth(f, L, 0.0), f)
+
+
+def test_gaussian_smoothing_equals_the_periodised_kernel_in_real_space():
+    """Brute force: u_s(x_i) = sum_j h^3 G(x_i - x_j) u(x_j) with G the density of
+    N(0, sigma I_3) summed over periodic images; sigma = 4 h^2 keeps the
+    aliasing of the sampled kernel below e^-19."""
+    H, L = 8, 1.0
+    h = L / H
+    sigma = 4 * h * h
+    rng = np.random.default_rng(0)
+    u = rng.random((H, H, H))
+    idx = np.arange(H)
+    d1 = (idx[:, None] - idx[None, :]) * h                      # x_i - x_j per axis
+    img = np.arange(-3, 4) * L
+    g1 = np.exp(-((d1[:, :, None] + img) ** 2) / (2 * sigma)).sum(axis=2)
+    g1 /= np.sqrt(2 * np.pi * sigma)                             # 1D factor of the density
+    # separable 3D kernel h^3 G = prod_axes (h g1)
+    K = h * g1
+    want = np.einsum("ia,jb,kc,abc->ijk", K, K, K, u)
+    got = O.gaussian_smooth(u, L, sigma)
+    assert np.max(np.abs(got - want)) <= 1e-9 * np.abs(want).max()
+    assert abs(got.mean() - u.mean()) <= 1e-14
