@@ -91,7 +91,10 @@ typedef struct {
  * particle-to-grid transfer, 2 (or 0) the trilinear R_h, 4 the fourth-order
  * star stencil R_h^(4) of Sec. 2.2.1 (32 nodes; negative weights, so u_bar
  * may be negative); the grid-to-particle interpolation is trilinear either
- * way.  reserved must be 0. */
+ * way.  reserved must be 0.  sigma >= 0: variance (units of L^2) of the
+ * Gaussian kernel K_sigma = N(0, sigma I_3) of Eq. m_reg, which replaces the
+ * m source u by K_sigma * u (applied spectrally, exp(-sigma |k|^2 / 2)); the
+ * w source keeps u; 0 (the default, as in the paper's experiments) is off. */
 typedef struct {
     double chi, Du, Dm, Dw, alpha, beta, gamma;
     int32_t diffusion;   /* SIPF_DIFFUSION_*  */
@@ -100,6 +103,7 @@ typedef struct {
     uint64_t seed;       /* Philox key        */
     int32_t p2g_order;   /* 0 or 2: trilinear, 4: R^(4) */
     int32_t reserved;
+    double sigma;        /* K_sigma regularisation of the m source; 0 = off */
 } sipf_params;
 
 /* FP64 diagnostics of the current state (Lemma mass, Corollary mass and the

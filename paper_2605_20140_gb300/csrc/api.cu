@@ -45,9 +45,9 @@ bool supported_H(int H) {
 bool finite_nonneg(double x) { return isfinite(x) && x >= 0.0; }
 
 int check_params(const sipf_params* p, std::string* why) {
-    const double v[] = {p->chi, p->Du, p->Dm, p->Dw, p->alpha, p->beta, p->gamma, p->H0};
-    const char* n[] = {"chi", "Du", "Dm", "Dw", "alpha", "beta", "gamma", "H0"};
-    for (int i = 0; i < 8; ++i)
+    const double v[] = {p->chi, p->Du, p->Dm, p->Dw, p->alpha, p->beta, p->gamma, p->H0, p->sigma};
+    const char* n[] = {"chi", "Du", "Dm", "Dw", "alpha", "beta", "gamma", "H0", "sigma"};
+    for (int i = 0; i < 9; ++i)
         if (!finite_nonneg(v[i])) {
             *why = std::string("parameter ") + n[i] + " must be finite and >= 0";
             return SIPF_EINVAL;
@@ -96,7 +96,7 @@ CtxSizes ctx_sizes(int H, int64_t N) {
 
 // Device bytes sipf_create allocates (the resampling work space, allocated
 // on first use, is not included).
-size_t ctx_device_bytes(int H, int64_t N, bool filter) {
+size_t ctx_device_bytes(int H, int64_t N, bool filter, bool smoothing) {
     const CtxSizes z = ctx_sizes(H, N);
     const size_t S = static_cast<size_t>(z.buf_slots);
     size_t b = 2 * (S * (3 * sizeof(float) + sizeof(double) + sizeof(uint32_t)) +
@@ -111,6 +111,7 @@ size_t ctx_device_bytes(int H, int64_t N, bool filter) {
          8 * sizeof(double);
     if (filter) b += z.spec * sizeof(float2);
     if (H > 128) b += 2 * z.spec * sizeof(float2);
+    if (smoothing) b += z.H3 * sizeof(float) + static_cast<size_t>(H) * sizeof(float);
     return b;
 }
 
@@ -122,7 +123,7 @@ void free_all(sipf_ctx* c) {
                     c->G, c->specM, c->specW, c->specV, c->specB, c->specA, c->specDx,
                     c->specDy, c->twiddle,
                     c->status, c->diag_tmp, c->diag_out, c->diag_ll, c->voff, c->rs_scratch,
-                    c->dsc};
+                    c->dsc, c->us, c->ksig};
     for (void* q : ptrs)
         if (q) cudaFree(q);
 }
@@ -301,6 +302,8 @@ int enqueue_step(sipf_ctx* c, double dt) {
     SIPF_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
     SIPF_CUDA(c, launch_plan(c, c->cur ^ 1, 1, c->side, dt));
     SIPF_CUDA(c, cudaEventRecord(c->ev_join, c->side));
+    // K_sigma * u_bar for the m source (Eq. m_reg), when sigma > 0
+    if (c->us) SIPF_CUDA(c, launch_smooth(c, c->us, c->stream));
     for (int pass = 0; pass < 3; ++pass) {
         SIPF_CUDA(c, launch_spectral_pass(c, sa, pass));
         SIPF_CUDA(c, prof_mark(c, 2 + pass));
@@ -517,6 +520,8 @@ int sipf_create(const sipf_grid* grid, int64_t N, const sipf_params* params, voi
     if (ok && filter) ok = da(&c->specA, spec) == cudaSuccess;
     if (ok && c->H > 128)
         ok = da(&c->specDx, spec) == cudaSuccess && da(&c->specDy, spec) == cudaSuccess;
+    if (ok && params->sigma > 0.0)
+        ok = da(&c->us, H3) == cudaSuccess && da(&c->ksig, static_cast<size_t>(c->H)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_all(c);
@@ -526,6 +531,11 @@ int sipf_create(const sipf_grid* grid, int64_t N, const sipf_params* params, voi
     std::vector<float2> tw(c->H);
     fill_twiddles(c->H, tw.data());
     cudaError_t e = cudaMemcpy(c->twiddle, tw.data(), c->H * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && c->ksig) {
+        std::vector<float> ks(c->H);
+        fill_smoothing(c->H, c->L, params->sigma, ks.data());
+        e = cudaMemcpy(c->ksig, ks.data(), c->H * sizeof(float), cudaMemcpyHostToDevice);
+    }
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
         e = cudaMemsetAsync(c->bstart[b], 0, sizeof(int) * c->ntiles, c->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->cap[b], 0, sizeof(int) * c->ntiles, c->stream);
@@ -999,7 +1009,7 @@ int64_t sipf_context_bytes(const sipf_grid* grid, int64_t N, const sipf_params* 
         return SIPF_EINVAL;
     if (ctx_sizes(grid->H, N).buf_slots >= (int64_t{1} << 31)) return SIPF_EINVAL;
     const bool filter = params->H0 > 0.0 && params->H0 < grid->H;
-    return static_cast<int64_t>(ctx_device_bytes(grid->H, N, filter));
+    return static_cast<int64_t>(ctx_device_bytes(grid->H, N, filter, params->sigma > 0.0));
 }
 
 int64_t sipf_device_bytes(const sipf_ctx* c) {

@@ -23,220 +23,13 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "fft_stages.cuh"
 #include "sipf_internal.cuh"
 
 namespace sipf {
 namespace {
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
-
-// exp(-2 pi i t / 16) for t < 8.
-__device__ __forceinline__ float2 root16(int t) {
-    constexpr float c1 = 0.92387953251128674f, s1 = 0.38268343236508978f, r2 = 0.70710678118654752f;
-    switch (t) {
-        case 0: return make_float2(1.f, 0.f);
-        case 1: return make_float2(c1, -s1);
-        case 2: return make_float2(r2, -r2);
-        case 3: return make_float2(s1, -c1);
-        case 4: return make_float2(0.f, -1.f);
-        case 5: return make_float2(-s1, -c1);
-        case 6: return make_float2(-r2, -r2);
-        default: return make_float2(-c1, -s1);
-    }
-}
-
-template <int R>
-__host__ __device__ constexpr int bitrev(int i) {
-    return R == 1 ? 0 : ((i & 1) * (R / 2) + bitrev<(R > 1 ? R / 2 : 1)>(i >> 1));
-}
-
-// Bit-reversal permutation of a register array, resolved at compile time.
-template <int R, int I>
-struct BitRevSwap {
-    static __device__ __forceinline__ void run(float2 (&v)[R]) {
-        constexpr int J = bitrev<R>(I);
-        if constexpr (J > I) {
-            const float2 t = v[I];
-            v[I] = v[J];
-            v[J] = t;
-        }
-        BitRevSwap<R, I + 1>::run(v);
-    }
-};
-template <int R>
-struct BitRevSwap<R, R> {
-    static __device__ __forceinline__ void run(float2 (&)[R]) {}
-};
-
-// One radix-2 level of the in-register DFT: butterflies of span LEN/2.
-template <int R, int LEN, int SIGN>
-struct DftLevel {
-    static __device__ __forceinline__ void run(float2 (&v)[R]) {
-#pragma unroll
-        for (int i = 0; i < R; i += LEN) {
-#pragma unroll
-            for (int k = 0; k < LEN / 2; ++k) {
-                constexpr int step = 16 / LEN;
-                const int t = k * step;
-                float2 b = v[i + k + LEN / 2];
-                if (t == 4) {
-                    b = SIGN < 0 ? make_float2(b.y, -b.x) : make_float2(-b.y, b.x);
-                } else if (t != 0) {
-                    float2 wv = root16(t);
-                    if (SIGN > 0) wv.y = -wv.y;
-                    b = cmul(b, wv);
-                }
-                const float2 a = v[i + k];
-                v[i + k] = cadd(a, b);
-                v[i + k + LEN / 2] = csub(a, b);
-            }
-        }
-        if constexpr (2 * LEN <= R) DftLevel<R, 2 * LEN, SIGN>::run(v);
-    }
-};
-
-// In-register R-point DFT, sign -1 forward, +1 inverse.  R = 2, 4, 8, 16:
-// bit-reversal permutation, then log2 R radix-2 levels (decimation in time).
-// R = 3: X0 = a + b + c, X1 = a - (b + c)/2 + SIGN i (sqrt 3 / 2)(b - c),
-// X2 = a - (b + c)/2 - SIGN i (sqrt 3 / 2)(b - c).
-template <int R, int SIGN>
-__device__ __forceinline__ void dft(float2 (&v)[R]) {
-    if constexpr (R == 3) {
-        constexpr float s3 = 0.86602540378443865f;
-        const float2 sum = cadd(v[1], v[2]), dif = csub(v[1], v[2]);
-        const float2 mid = make_float2(v[0].x - 0.5f * sum.x, v[0].y - 0.5f * sum.y);
-        // rot = SIGN i s3 (b - c)
-        const float2 rot = SIGN < 0 ? make_float2(s3 * dif.y, -s3 * dif.x)
-                                    : make_float2(-s3 * dif.y, s3 * dif.x);
-        v[0] = cadd(v[0], sum);
-        v[1] = cadd(mid, rot);
-        v[2] = csub(mid, rot);
-    } else {
-        BitRevSwap<R, 0>::run(v);
-        DftLevel<R, 2, SIGN>::run(v);
-    }
-}
-
-// One Stockham stage of radix R after NS points have been combined.
-// Transform t, element j lives at buf[t * TS + j * ES].  Consecutive lanes
-// take consecutive transforms (same butterfly), so a warp's accesses are
-// contiguous when TS == 1 and spread over all banks when TS is odd.
-template <int L, int R, int NS, int NTRANS, int ES, int TS, int NT, int SIGN>
-__device__ __forceinline__ void stage(float2* buf, const float2* tw) {
-    constexpr int NB = NTRANS * (L / R);
-    constexpr int BPT = (NB + NT - 1) / NT;
-    float2 v[BPT][R];
-#pragma unroll
-    for (int i = 0; i < BPT; ++i) {
-        const int b = threadIdx.x + i * NT;
-        if (b < NB) {
-            const int t = b % NTRANS;
-            const int j = b / NTRANS;
-            const int k = j % NS;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                float2 x = buf[t * TS + (j + r * (L / R)) * ES];
-                if (NS > 1 && r > 0) {
-                    float2 wv = tw[r * k * (L / (NS * R))];
-                    if (SIGN > 0) wv.y = -wv.y;
-                    x = cmul(x, wv);
-                }
-                v[i][r] = x;
-            }
-            dft<R, SIGN>(v[i]);
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < BPT; ++i) {
-        const int b = threadIdx.x + i * NT;
-        if (b < NB) {
-            const int t = b % NTRANS;
-            const int j = b / NTRANS;
-            const int k = j % NS;
-            const int base = (j - k) * R + k;
-#pragma unroll
-            for (int r = 0; r < R; ++r) buf[t * TS + (base + r * NS) * ES] = v[i][r];
-        }
-    }
-    __syncthreads();
-}
-
-// First Stockham stage (NS = 1) with inputs from a loader: element j of
-// transform t is load(t, j).  All loads precede all writes (a block barrier
-// in between), so the loader may read the memory `out` overwrites.
-template <int L, int R, int NTRANS, int ES, int TS, int NT, int SIGN, class Load>
-__device__ __forceinline__ void stage1_from(float2* out, Load load) {
-    constexpr int NB = NTRANS * (L / R);
-    constexpr int BPT = (NB + NT - 1) / NT;
-    float2 v[BPT][R];
-#pragma unroll
-    for (int i = 0; i < BPT; ++i) {
-        const int b = threadIdx.x + i * NT;
-        if (b < NB) {
-            const int t = b % NTRANS, j = b / NTRANS;
-#pragma unroll
-            for (int r = 0; r < R; ++r) v[i][r] = load(t, j + r * (L / R));
-            dft<R, SIGN>(v[i]);
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < BPT; ++i) {
-        const int b = threadIdx.x + i * NT;
-        if (b < NB) {
-            const int t = b % NTRANS, j = b / NTRANS;
-#pragma unroll
-            for (int r = 0; r < R; ++r) out[t * TS + (j * R + r) * ES] = v[i][r];
-        }
-    }
-    __syncthreads();
-}
-
-// Radix plan of a length-L transform: two to four Stockham stages (R3, R4 =
-// 1: fewer).  Lengths are 2^a 3^b with 8 <= L <= 512.
-template <int L> struct Radix;
-template <int A, int B, int C = 1, int D = 1>
-struct RadixPlan { static constexpr int R1 = A, R2 = B, R3 = C, R4 = D; };
-template <> struct Radix<8> : RadixPlan<4, 2> {};
-template <> struct Radix<16> : RadixPlan<4, 4> {};
-template <> struct Radix<24> : RadixPlan<8, 3> {};
-template <> struct Radix<32> : RadixPlan<8, 4> {};
-template <> struct Radix<48> : RadixPlan<16, 3> {};
-template <> struct Radix<64> : RadixPlan<8, 8> {};
-template <> struct Radix<72> : RadixPlan<8, 3, 3> {};
-template <> struct Radix<96> : RadixPlan<8, 4, 3> {};
-template <> struct Radix<128> : RadixPlan<16, 8> {};
-template <> struct Radix<144> : RadixPlan<16, 3, 3> {};
-template <> struct Radix<192> : RadixPlan<16, 4, 3> {};
-template <> struct Radix<216> : RadixPlan<8, 3, 3, 3> {};
-template <> struct Radix<256> : RadixPlan<16, 16> {};
-template <> struct Radix<288> : RadixPlan<16, 3, 3, 2> {};
-template <> struct Radix<384> : RadixPlan<16, 8, 3> {};
-template <> struct Radix<432> : RadixPlan<16, 3, 3, 3> {};
-template <> struct Radix<512> : RadixPlan<8, 8, 8> {};
-
-// The stages after the first of a batched length-L FFT.
-template <int L, int NTRANS, int ES, int TS, int NT, int SIGN>
-__device__ __forceinline__ void fft_rest(float2* buf, const float2* tw) {
-    constexpr int R1 = Radix<L>::R1, R2 = Radix<L>::R2, R3 = Radix<L>::R3, R4 = Radix<L>::R4;
-    static_assert(R1 * R2 * R3 * R4 == L, "radix plan");
-    stage<L, R2, R1, NTRANS, ES, TS, NT, SIGN>(buf, tw);
-    if constexpr (R3 > 1) stage<L, R3, R1 * R2, NTRANS, ES, TS, NT, SIGN>(buf, tw);
-    if constexpr (R4 > 1) stage<L, R4, R1 * R2 * R3, NTRANS, ES, TS, NT, SIGN>(buf, tw);
-}
-
-// Batched length-L FFT along one axis of a shared-memory array.
-template <int L, int NTRANS, int ES, int TS, int NT, int SIGN>
-__device__ __forceinline__ void fft_axis(float2* buf, const float2* tw) {
-    stage<L, Radix<L>::R1, 1, NTRANS, ES, TS, NT, SIGN>(buf, tw);
-    fft_rest<L, NTRANS, ES, TS, NT, SIGN>(buf, tw);
-}
+using namespace fftk;
 
 // (H - k) mod H for 0 <= k <= H: the index of the mode -k.
 template <int H>
@@ -289,14 +82,15 @@ __device__ __forceinline__ float acc_to_float(unsigned long long q) {
 }
 
 // R_tau at one node: (m*, w*) and v^n.
+// um is the u of the m source: u itself, or K_sigma * u (Eq. m_reg).
 __device__ __forceinline__ void react(const SpectralArgs& a, float vv, float mm, float ww, float u,
-                                      float& ms, float& ws, float& vn) {
+                                      float um, float& ms, float& ws, float& vn) {
     ms = mm;
     ws = ww;
     if (a.do_mw) {
         // explicit Euler of S = (-alpha m v; u; gamma v - eta(u) w), eta(u) = 2u/(1+u)
         const float eta = 2.0f * u / (1.0f + u);
-        ms = mm + a.tau * u;
+        ms = mm + a.tau * um;
         ws = ww + a.tau * (a.gamma * vv - eta * ww);
     }
     vn = (a.v_update == SIPF_V_IMPLICIT) ? vv / (1.0f + a.alpha * a.tau * mm)
@@ -310,7 +104,8 @@ __global__ void __launch_bounds__(Cfg<H>::NT1)
                  const float* __restrict__ w, unsigned long long* __restrict__ acc,
                  float* v_out, float2* __restrict__ gM, float2* __restrict__ gW,
                  float2* __restrict__ gV, const float2* __restrict__ twg,
-                 const float* __restrict__ voff, const StepScalars* __restrict__ sc) {
+                 const float* __restrict__ voff, const StepScalars* __restrict__ sc,
+                 const float* __restrict__ us) {
     constexpr int NT = Cfg<H>::NT1, KXP = kxp<H>(), HK = H / 2 + 1, RP = rowp<H>();
     const float u_scale = sc->u_scale;   // u_bar per accumulator unit
     extern __shared__ float2 sm[];
@@ -357,11 +152,14 @@ __global__ void __launch_bounds__(Cfg<H>::NT1)
                 float vn[4];
                 const int y = (4 * g) / H, x0 = (4 * g) % H;
                 float* vrow = reinterpret_cast<float*>(Vb + (y >> 1) * RP);
+                float4 ru = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (us) ru = reinterpret_cast<const float4*>(us + plane)[g];
+                const float uu[4] = {ru.x, ru.y, ru.z, ru.w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     float ms, ws;
-                    react(a, vv[e], mm[e], ww[e], acc_to_float(qq[e]) * u_scale, ms, ws,
-                          vn[e]);
+                    const float u = acc_to_float(qq[e]) * u_scale;
+                    react(a, vv[e], mm[e], ww[e], u, us ? uu[e] : u, ms, ws, vn[e]);
                     Z[y * RP + x0 + e] = make_float2(ms, ws);
                     vrow[2 * (x0 + e) + (y & 1)] = vn[e] - c0;
                 }
@@ -682,7 +480,7 @@ __global__ void __launch_bounds__(kSxNT)
                  const float* __restrict__ w, unsigned long long* __restrict__ acc, float* v_out,
                  float2* __restrict__ gM, float2* __restrict__ gW, float2* __restrict__ gV,
                  const float2* __restrict__ twg, const float* __restrict__ voff,
-                 const StepScalars* __restrict__ sc) {
+                 const StepScalars* __restrict__ sc, const float* __restrict__ us) {
     constexpr int RB = kSxRows, NT = kSxNT, KXP = kxp<H>(), HK = H / 2 + 1, RP = rowp<H>();
     const float u_scale = sc->u_scale;   // u_bar per accumulator unit
     static_assert((RB / 2) * RP <= RB * KXP, "row pairs fit in the half-row space");
@@ -707,10 +505,14 @@ __global__ void __launch_bounds__(kSxNT)
         const unsigned long long qq[4] = {q0.x, q0.y, q1.x, q1.y};
         const int r = (4 * g) / H, x0 = (4 * g) % H;
         float vn[4];
+        float4 ru = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (us) ru = *reinterpret_cast<const float4*>(us + o);
+        const float uu[4] = {ru.x, ru.y, ru.z, ru.w};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             float ms, ws;
-            react(a, vv[e], mm[e], ww[e], acc_to_float(qq[e]) * u_scale, ms, ws, vn[e]);
+            const float u = acc_to_float(qq[e]) * u_scale;
+            react(a, vv[e], mm[e], ww[e], u, us ? uu[e] : u, ms, ws, vn[e]);
             const float val[3] = {ms, ws, vn[e] - c0};
 #pragma unroll
             for (int f = 0; f < 3; ++f)
@@ -891,7 +693,7 @@ cudaError_t spectral_pass_split(sipf_ctx* c, const SpectralArgs& a, int pass) {
     if (pass == 0) {
         k_sx_forward<H><<<dim3(H / RB, H), kSxNT, smx1, c->stream>>>(
             a, c->v, c->m, c->w, reinterpret_cast<unsigned long long*>(c->acc), c->v, c->specM,
-            c->specW, c->specV, c->twiddle, c->voff, c->dsc + c->cur);
+            c->specW, c->specV, c->twiddle, c->voff, c->dsc + c->cur, c->us);
         k_sx_columns<H, -1><<<gy, kSxNT, smy, c->stream>>>(a, c->specM, c->specW, c->specV,
                                                              nullptr, nullptr, c->twiddle, 0);
     } else if (pass == 1) {
@@ -930,7 +732,7 @@ cudaError_t spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass) {
     if (pass == 0) {
         k_forward_xy<H><<<H, Cfg<H>::NT1, sm1, c->stream>>>(
             a, c->v, c->m, c->w, reinterpret_cast<unsigned long long*>(c->acc), c->v, c->specM,
-            c->specW, c->specV, c->twiddle, c->voff, c->dsc + c->cur);
+            c->specW, c->specV, c->twiddle, c->voff, c->dsc + c->cur, c->us);
     } else if (pass == 1) {
         k_z_multiply<H><<<dim3(H, 4, (KXP + zcols<H>() - 1) / zcols<H>()), Cfg<H>::NT2, sm2,
                             c->stream>>>(a, c->specM, c->specW, c->specV,

@@ -180,6 +180,8 @@ struct sipf_ctx {
 
     // grid
     long long* acc = nullptr;        // H^3 fixed-point deposit accumulator, zero between steps
+    float* us = nullptr;             // K_sigma * u_bar, the m source (sigma > 0 only)
+    float* ksig = nullptr;           // [H] 1D smoothing multiplier exp(-sigma k_j^2 / 2) / H
     float* v = nullptr;
     float* m = nullptr;
     float* w = nullptr;
@@ -259,6 +261,9 @@ cudaError_t launch_conv_check(const float* f, const double* d, int n, int* misma
                               cudaStream_t s);
 // api.cu
 int run_steps_for(sipf_ctx* c, double dt, int64_t k);
+// smooth.cu
+cudaError_t launch_smooth(sipf_ctx* c, float* us, cudaStream_t s);
+void fill_smoothing(int H, double L, double sigma, float* host_out);
 // resample.cu
 int resample_device(sipf_ctx* c, int src, int dst, double ratio, int* done, std::string* err);
 // fft.cu

@@ -54,7 +54,8 @@ class sipf_params(ctypes.Structure):
                 ("Dw", ctypes.c_double), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("diffusion", ctypes.c_int32),
                 ("v_update", ctypes.c_int32), ("H0", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("p2g_order", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("p2g_order", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("sigma", ctypes.c_double)]
 
 
 class sipf_diag(ctypes.Structure):
@@ -333,6 +334,7 @@ def make_params(p) -> sipf_params:
     q.H0 = float(getattr(p, "H0", 0.0))
     q.seed = int(getattr(p, "seed", 0))
     q.p2g_order = int(getattr(p, "p2g_order", 2))
+    q.sigma = float(getattr(p, "sigma", 0.0))
     return q
 
 

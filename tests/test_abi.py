@@ -47,8 +47,8 @@ int main(void) {
   printf("%zu %zu %zu\n", sizeof(sipf_grid), sizeof(sipf_params), sizeof(sipf_diag));
   printf("%zu %zu %zu\n", offsetof(sipf_grid, origin), offsetof(sipf_params, diffusion),
          offsetof(sipf_params, H0));
-  printf("%zu %zu %zu\n", offsetof(sipf_params, seed), offsetof(sipf_diag, nonfinite),
-         offsetof(sipf_params, p2g_order));
+  printf("%zu %zu %zu %zu\n", offsetof(sipf_params, seed), offsetof(sipf_diag, nonfinite),
+         offsetof(sipf_params, p2g_order), offsetof(sipf_params, sigma));
   return 0;
 }
 """
@@ -63,7 +63,7 @@ int main(void) {
             ctypes.sizeof(sipf.sipf_diag), sipf.sipf_grid.origin.offset,
             sipf.sipf_params.diffusion.offset, sipf.sipf_params.H0.offset,
             sipf.sipf_params.seed.offset, sipf.sipf_diag.nonfinite.offset,
-            sipf.sipf_params.p2g_order.offset]
+            sipf.sipf_params.p2g_order.offset, sipf.sipf_params.sigma.offset]
     assert got == want
 
 
@@ -92,6 +92,7 @@ def _create(lib, H=32, L=1.0, N=100, **kw):
     (dict(diffusion=7), sipf.SIPF_EINVAL),
     (dict(v_update=2), sipf.SIPF_EINVAL),
     (dict(p2g_order=3), sipf.SIPF_EINVAL),
+    (dict(sigma=-1e-3), sipf.SIPF_EINVAL),
     (dict(reserved=1), sipf.SIPF_EINVAL),
 ])
 def test_create_rejects_bad_arguments_without_touching_the_gpu(lib, kw, code):

@@ -690,3 +690,22 @@ def test_steps_match_oracle_216_grid():
     st = O.run(oracle_state(wl), wl.dt, 2)
     _compare(sim, st, wl)
     sim.close()
+
+
+@pytest.mark.parametrize("H,N,steps", [(32, 1 << 15, 1), (32, 1 << 15, 10), (48, 1 << 15, 10),
+                                       (72, 1 << 16, 4), (192, 1 << 18, 2)])
+def test_regularised_m_source_matches_oracle(H, N, steps):
+    """Eq. m_reg: the m equation driven by K_sigma * u_bar, sigma = (2h)^2
+    (a Gaussian two cells wide), through the fused plane passes (H <= 128)
+    and the per-axis pipeline (192), single steps and graph replay."""
+    wl = workload("small", H=H, N=N)
+    h = wl.L / H
+    p = dataclasses.replace(wl.params, sigma=(2 * h) ** 2)
+    sim = run_gpu(wl, steps, p=p)
+    st = O.run(oracle_state(wl, p=p), wl.dt, steps)
+    _compare(sim, st, wl)
+    sim.close()
+    # the smoothing is visible: m differs from the unregularised run by far
+    # more than the tolerance
+    plain = O.run(oracle_state(wl), wl.dt, steps)
+    assert rel_l2(st.m, plain.m) > 20 * FIELD_TOL
