@@ -66,6 +66,9 @@ template <> struct Cfg<512> { static constexpr int NT1 = 256, NT2 = 1024, NT3 = 
 template <int H> constexpr int zcols() { return H <= 128 ? H / 2 + 2 : 32; }
 
 template <int H> constexpr int kxp() { return H / 2 + 2; }
+// shared-memory pitch (float2) of half-spectrum rows in the inverse pass: odd,
+// so that lanes reading one element of consecutive rows hit distinct banks
+template <int H> constexpr int kxs() { return H / 2 + 1; }
 // shared-memory pitch (float2) of rows that are transformed along the row
 template <int H> constexpr int rowp() { return H + 1; }
 
@@ -117,53 +120,52 @@ __global__ void __launch_bounds__(Cfg<H>::NT1)
     const size_t plane = static_cast<size_t>(z) * H * H;
     const float c0 = *voff;   // the v spectrum only feeds derivatives: remove a constant
     {
-        // groups of 4 consecutive x; all loads of a batch are issued first
-        constexpr int NG = H * H / 4, ITER = (NG + NT - 1) / NT, CH = ITER < 2 ? ITER : 2;
-        const float4* v4 = reinterpret_cast<const float4*>(v + plane);
-        const float4* m4 = reinterpret_cast<const float4*>(m + plane);
-        const float4* w4 = reinterpret_cast<const float4*>(w + plane);
-        ulonglong2* a2 = reinterpret_cast<ulonglong2*>(acc + plane);
-        float4* vo4 = reinterpret_cast<float4*>(v_out + plane);
+        // node pairs (p, x), (p + H/2, x): consecutive lanes take consecutive x,
+        // so the rows of Z and the row pairs of Vb are written without bank
+        // conflicts; all loads of a batch are issued first
+        constexpr int HH = H / 2, NPR = HH * H, ITER = (NPR + NT - 1) / NT;
+        constexpr int CH = ITER < 2 ? ITER : 2;
+        const float* vp = v + plane;
+        const float* mp = m + plane;
+        const float* wp = w + plane;
+        unsigned long long* ap = acc + plane;
+        float* vo = v_out + plane;
 #pragma unroll
         for (int i0 = 0; i0 < ITER; i0 += CH) {
-            float4 rv[CH], rm[CH], rw[CH];
-            ulonglong2 ra[CH], rb[CH];
+            float rv[CH][2], rm[CH][2], rw[CH][2], ru[CH][2];
+            unsigned long long ra[CH][2];
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
-                const int g = threadIdx.x + (i0 + c) * NT;
-                if (i0 + c < ITER && g < NG) {
-                    rv[c] = v4[g];
-                    rm[c] = m4[g];
-                    rw[c] = w4[g];
-                    ra[c] = a2[2 * g];
-                    rb[c] = a2[2 * g + 1];
+                const int q = threadIdx.x + (i0 + c) * NT;
+                if (i0 + c < ITER && q < NPR) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int o = q + h * NPR;   // (p + h H/2) H + x
+                        rv[c][h] = vp[o];
+                        rm[c][h] = mp[o];
+                        rw[c][h] = wp[o];
+                        ra[c][h] = ap[o];
+                        ru[c][h] = us ? us[plane + o] : 0.f;
+                    }
                 }
             }
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
-                const int g = threadIdx.x + (i0 + c) * NT;
-                if (!(i0 + c < ITER && g < NG)) continue;
-                a2[2 * g] = make_ulonglong2(0ull, 0ull);
-                a2[2 * g + 1] = make_ulonglong2(0ull, 0ull);
-                const float vv[4] = {rv[c].x, rv[c].y, rv[c].z, rv[c].w};
-                const float mm[4] = {rm[c].x, rm[c].y, rm[c].z, rm[c].w};
-                const float ww[4] = {rw[c].x, rw[c].y, rw[c].z, rw[c].w};
-                const unsigned long long qq[4] = {ra[c].x, ra[c].y, rb[c].x, rb[c].y};
-                float vn[4];
-                const int y = (4 * g) / H, x0 = (4 * g) % H;
-                float* vrow = reinterpret_cast<float*>(Vb + (y >> 1) * RP);
-                float4 ru = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (us) ru = reinterpret_cast<const float4*>(us + plane)[g];
-                const float uu[4] = {ru.x, ru.y, ru.z, ru.w};
+                const int q = threadIdx.x + (i0 + c) * NT;
+                if (!(i0 + c < ITER && q < NPR)) continue;
+                const int pr = q / H, x = q % H;
+                float vn[2];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
+                for (int h = 0; h < 2; ++h) {
+                    const int o = q + h * NPR;
+                    ap[o] = 0ull;
                     float ms, ws;
-                    const float u = acc_to_float(qq[e]) * u_scale;
-                    react(a, vv[e], mm[e], ww[e], u, us ? uu[e] : u, ms, ws, vn[e]);
-                    Z[y * RP + x0 + e] = make_float2(ms, ws);
-                    vrow[2 * (x0 + e) + (y & 1)] = vn[e] - c0;
+                    const float u = acc_to_float(ra[c][h]) * u_scale;
+                    react(a, rv[c][h], rm[c][h], rw[c][h], u, us ? ru[c][h] : u, ms, ws, vn[h]);
+                    Z[(pr + h * HH) * RP + x] = make_float2(ms, ws);
+                    if (a.write_v) vo[o] = vn[h];
                 }
-                if (a.write_v) vo4[g] = make_float4(vn[0], vn[1], vn[2], vn[3]);
+                Vb[pr * RP + x] = make_float2(vn[0] - c0, vn[1] - c0);
             }
         }
     }
@@ -171,7 +173,8 @@ __global__ void __launch_bounds__(Cfg<H>::NT1)
     if (a.do_mw) fft_axis<H, H, 1, RP, NT, -1>(Z, tw);
     fft_axis<H, H / 2, 1, RP, NT, -1>(Vb, tw);
     {
-        // split each transformed row pair z = x1 + i x2 into X1, X2 (kx <= H/2)
+        // split each transformed row pair z = x1 + i x2 (rows p, p + H/2) into
+        // X1, X2 (kx <= H/2)
         constexpr int NS = (H / 2) * HK, SPT = (NS + NT - 1) / NT;
         float2 x1[SPT], x2[SPT];
 #pragma unroll
@@ -191,41 +194,33 @@ __global__ void __launch_bounds__(Cfg<H>::NT1)
             const int idx = threadIdx.x + s * NT;
             if (idx < NS) {
                 const int p = idx / HK, k = idx % HK;
-                Vb[(2 * p) * KXP + k] = x1[s];
-                Vb[(2 * p + 1) * KXP + k] = x2[s];
+                Vb[p * KXP + k] = x1[s];
+                Vb[(p + H / 2) * KXP + k] = x2[s];
             }
         }
         __syncthreads();
     }
     if (a.do_mw) fft_axis<H, H, RP, 1, NT, -1>(Z, tw);
     fft_axis<H, HK, KXP, 1, NT, -1>(Vb, tw);
-    // half spectra as pairs (kx, kx+1), the row's last slot (kx = H/2 + 1) is zero;
-    // M, W separated from the 2D spectrum of m* + i w*
-    constexpr int NP = H * (KXP / 2);
-    float4* m4 = reinterpret_cast<float4*>(gM + static_cast<size_t>(z) * H * KXP);
-    float4* w4 = reinterpret_cast<float4*>(gW + static_cast<size_t>(z) * H * KXP);
-    float4* v4o = reinterpret_cast<float4*>(gV + static_cast<size_t>(z) * H * KXP);
+    // half spectra, rows of KXP (the last slot, kx = H/2 + 1, is zero); M, W
+    // separated from the 2D spectrum of m* + i w*; one mode per thread
+    constexpr int NP = H * KXP;
+    const size_t sbase = static_cast<size_t>(z) * H * KXP;
     for (int idx = threadIdx.x; idx < NP; idx += NT) {
-        const int ky = idx / (KXP / 2), kx = 2 * (idx % (KXP / 2));
-        float2 M[2], W[2], V[2];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int k = kx + e;
-            if (k < HK) {
-                const float2 zk = Z[ky * RP + k];
-                const float2 zc = Z[neg_mod<H>(ky) * RP + neg_mod<H>(k)];
-                M[e] = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y - zc.y));
-                W[e] = make_float2(0.5f * (zk.y + zc.y), -0.5f * (zk.x - zc.x));
-                V[e] = Vb[ky * KXP + k];
-            } else {
-                M[e] = W[e] = V[e] = make_float2(0.f, 0.f);
-            }
+        const int ky = idx / KXP, k = idx % KXP;
+        float2 M = make_float2(0.f, 0.f), W = M, V = M;
+        if (k < HK) {
+            const float2 zk = Z[ky * RP + k];
+            const float2 zc = Z[neg_mod<H>(ky) * RP + neg_mod<H>(k)];
+            M = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y - zc.y));
+            W = make_float2(0.5f * (zk.y + zc.y), -0.5f * (zk.x - zc.x));
+            V = Vb[ky * KXP + k];
         }
         if (a.do_mw) {
-            m4[idx] = make_float4(M[0].x, M[0].y, M[1].x, M[1].y);
-            w4[idx] = make_float4(W[0].x, W[0].y, W[1].x, W[1].y);
+            gM[sbase + idx] = M;
+            gW[sbase + idx] = W;
         }
-        v4o[idx] = make_float4(V[0].x, V[0].y, V[1].x, V[1].y);
+        gV[sbase + idx] = V;
     }
 }
 
@@ -238,7 +233,6 @@ __global__ void __launch_bounds__(Cfg<H>::NT2)
                  const float2* __restrict__ gV, float2* __restrict__ gB, float2* __restrict__ gA,
                  const float2* __restrict__ twg, float* __restrict__ voff) {
     constexpr int NT = Cfg<H>::NT2, KXP = kxp<H>(), HK = H / 2 + 1, KB = zcols<H>();
-    static_assert(KB % 2 == 0, "float4 columns");
     extern __shared__ float2 sm[];
     float2* buf = sm;             // [H (z)][KB (kx)]
     float2* tw = buf + H * KB;
@@ -249,65 +243,51 @@ __global__ void __launch_bounds__(Cfg<H>::NT2)
     const float2* src = field == 0 ? gM : field == 1 ? gW : gV;
     float2* dst = field == 0 ? gM : field == 1 ? gW : field == 2 ? gB : gA;
     for (int i = threadIdx.x; i < H; i += NT) tw[i] = twg[i];
-    // rows (z, ky): KB/2 float4 from column k0, all loads issued first
-    constexpr int NQ = H * (KB / 2), ITER = (NQ + NT - 1) / NT;
-    {
-        float4 r[ITER];
-#pragma unroll
-        for (int i = 0; i < ITER; ++i) {
-            const int q = threadIdx.x + i * NT;
-            if (q < NQ) {
-                const int zz = q / (KB / 2), col = k0 + 2 * (q % (KB / 2));
-                r[i] = col < KXP ? *reinterpret_cast<const float4*>(
-                                       src + (static_cast<size_t>(zz) * H + ky) * KXP + col)
-                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+    constexpr int R1 = Radix<H>::R1;
+    // element (column t, z) of the block's tile in a [z][ky][KXP] half spectrum
+    auto at = [ky, k0](int t, int zz) -> size_t {
+        return (static_cast<size_t>(zz) * H + ky) * KXP + k0 + t;
+    };
+    // forward z DFT, its first stage loading the columns from global memory
+    stage1_from<H, R1, KB, KB, 1, NT, -1>(buf, [=](int t, int zz) {
+        return k0 + t < KXP ? src[at(t, zz)] : make_float2(0.f, 0.f);
+    });
+    // its last stage applies the per-mode factor on the way back to shared memory
+    const int qy = signed_mode(ky, H);
+    fft_rest_sink<H, KB, KB, 1, NT, -1>(buf, tw, [=](int t, int kz, float2 val) {
+        const int qx = k0 + t;
+        if (qx < HK) {
+            if (field == 2 && ky == 0 && qx == 0 && kz == 0) {
+                // DC of (v^n - c0): move the offset to the mean of v^n for the next step
+                *voff = *voff + val.x * a.out_scale;
+            }
+            const int qz = signed_mode(kz, H);
+            const float q2 = static_cast<float>(qx * qx + qy * qy + qz * qz);
+            float f = 1.0f;
+            if (field == 2) {
+                const float kz_phys =
+                    (qz == -H / 2) ? 0.0f : a.two_pi_over_L * static_cast<float>(qz);
+                val = make_float2(-kz_phys * val.y, kz_phys * val.x);
+            } else if (field < 2) {
+                const float c = field == 0 ? a.m_c : a.w_c;
+                f = a.diffusion == SIPF_DIFFUSION_IMPLICIT ? 1.0f / (1.0f + c * q2) : expf(-c * q2);
+            }
+            if (a.filter) f *= expf(-a.inv_H0sq_2pi2 * q2);
+            val = make_float2(f * val.x, f * val.y);
+            if (field < 2) {
+                // times r0 = hi + lo: the float32 rounding of r0 itself is compensated
+                const float hi = field == 0 ? a.m_r0_hi : a.w_r0_hi;
+                const float lo = field == 0 ? a.m_r0_lo : a.w_r0_lo;
+                val = make_float2(fmaf(val.x, lo, val.x * hi), fmaf(val.y, lo, val.y * hi));
             }
         }
-#pragma unroll
-        for (int i = 0; i < ITER; ++i) {
-            const int q = threadIdx.x + i * NT;
-            if (q < NQ) reinterpret_cast<float4*>(buf)[q] = r[i];
-        }
-    }
-    __syncthreads();
-    fft_axis<H, KB, KB, 1, NT, -1>(buf, tw);
-    if (field == 2 && ky == 0 && k0 == 0 && threadIdx.x == 0) {
-        // DC of (v^n - c0): move the offset to the mean of v^n for the next step
-        *voff = *voff + buf[0].x * a.out_scale;
-    }
-    const int qy = signed_mode(ky, H);
-    for (int idx = threadIdx.x; idx < H * KB; idx += NT) {
-        const int kz = idx / KB, qx = k0 + idx % KB;
-        if (qx >= HK) continue;
-        const int qz = signed_mode(kz, H);
-        const float q2 = static_cast<float>(qx * qx + qy * qy + qz * qz);
-        float f = 1.0f;
-        float2 val = buf[idx];
-        if (field == 2) {
-            const float kz_phys = (qz == -H / 2) ? 0.0f : a.two_pi_over_L * static_cast<float>(qz);
-            val = make_float2(-kz_phys * val.y, kz_phys * val.x);
-        } else if (field < 2) {
-            const float c = field == 0 ? a.m_c : a.w_c;
-            f = a.diffusion == SIPF_DIFFUSION_IMPLICIT ? 1.0f / (1.0f + c * q2) : expf(-c * q2);
-        }
-        if (a.filter) f *= expf(-a.inv_H0sq_2pi2 * q2);
-        val = make_float2(f * val.x, f * val.y);
-        if (field < 2) {
-            // times r0 = hi + lo: the float32 rounding of r0 itself is compensated
-            const float hi = field == 0 ? a.m_r0_hi : a.w_r0_hi;
-            const float lo = field == 0 ? a.m_r0_lo : a.w_r0_lo;
-            val = make_float2(fmaf(val.x, lo, val.x * hi), fmaf(val.y, lo, val.y * hi));
-        }
-        buf[idx] = val;
-    }
-    __syncthreads();
-    fft_axis<H, KB, KB, 1, NT, +1>(buf, tw);
-    for (int q = threadIdx.x; q < NQ; q += NT) {
-        const int zz = q / (KB / 2), col = k0 + 2 * (q % (KB / 2));
-        if (col < KXP)
-            *reinterpret_cast<float4*>(dst + (static_cast<size_t>(zz) * H + ky) * KXP + col) =
-                reinterpret_cast<const float4*>(buf)[q];
-    }
+        buf[kz * KB + t] = val;
+    });
+    // inverse z DFT, its last stage storing the columns to global memory
+    stage<H, R1, 1, KB, KB, 1, NT, +1>(buf, tw);
+    fft_rest_sink<H, KB, KB, 1, NT, +1>(buf, tw, [=](int t, int zz, float2 val) {
+        if (k0 + t < KXP) dst[at(t, zz)] = val;
+    });
 }
 
 // ---------------------------------------------------------------- pass 3
@@ -394,16 +374,17 @@ __global__ void __launch_bounds__(Cfg<H>::NT3)
                  const float2* __restrict__ gV, const float2* __restrict__ gB,
                  float* __restrict__ m_out, float* __restrict__ w_out, float* __restrict__ G,
                  const float2* __restrict__ twg) {
-    constexpr int NT = Cfg<H>::NT3, KXP = kxp<H>(), HK = H / 2 + 1, RP = rowp<H>();
-    constexpr int R1 = Radix<H>::R1;
-    static_assert(H * RP <= 2 * H * KXP, "packed rows must fit in B0/B1");
+    constexpr int NT = Cfg<H>::NT3, KXP = kxp<H>(), KXS = kxs<H>(), HK = H / 2 + 1;
+    constexpr int RP = rowp<H>(), R1 = Radix<H>::R1;
+    static_assert(H * RP <= 2 * H * KXS, "packed rows must fit in B0/B1");
+    static_assert((H / 2) * RP <= H * KXS, "packed row pairs must fit in B2");
     extern __shared__ float2 sm[];
-    float2* B0 = sm;              // [H][KXP]
-    float2* B1 = B0 + H * KXP;    // [H][KXP]
-    float2* B2 = B1 + H * KXP;    // [H][KXP] (group 1)
-    float2* tw = B2 + H * KXP;
+    float2* B0 = sm;              // [H][KXS]
+    float2* B1 = B0 + H * KXS;    // [H][KXS]
+    float2* B2 = B1 + H * KXS;    // [H][KXS] (group 1)
+    float2* tw = B2 + H * KXS;
     float2* Z = sm;               // [H][RP] packed rows (aliases B0/B1)
-    float2* Z2 = B2;              // [H/2][RP] packed row pairs of B2 (aliases B2)
+    float2* Z2 = B2;              // [H/2][RP] rows y, y + H/2 of B2 packed (aliases B2)
     const int z = blockIdx.x, group = 1 - blockIdx.y;
     if (group == 0 && !a.do_mw) return;
     for (int i = threadIdx.x; i < H; i += NT) tw[i] = twg[i];
@@ -411,43 +392,42 @@ __global__ void __launch_bounds__(Cfg<H>::NT3)
     const size_t pbase = static_cast<size_t>(z) * H * KXP;
     // inverse y: first stage from global, second in shared memory
     if (group == 0) {
-        stage1_from<H, R1, HK, KXP, 1, NT, +1>(B0, PlaneLoad{gM + pbase, KXP, 0.f, 0.f, H, 0});
-        stage1_from<H, R1, HK, KXP, 1, NT, +1>(B1, PlaneLoad{gW + pbase, KXP, 0.f, 0.f, H, 0});
+        stage1_from<H, R1, HK, KXS, 1, NT, +1>(B0, PlaneLoad{gM + pbase, KXP, 0.f, 0.f, H, 0});
+        stage1_from<H, R1, HK, KXS, 1, NT, +1>(B1, PlaneLoad{gW + pbase, KXP, 0.f, 0.f, H, 0});
     } else {
         const float k = a.two_pi_over_L;
-        stage1_from<H, R1, HK, KXP, 1, NT, +1>(B0, PlaneLoad{gV + pbase, KXP, k, k, H, 1});
-        stage1_from<H, R1, HK, KXP, 1, NT, +1>(B1, PlaneLoad{gV + pbase, KXP, k, k, H, 2});
-        stage1_from<H, R1, HK, KXP, 1, NT, +1>(B2, PlaneLoad{gB + pbase, KXP, 0.f, 0.f, H, 0});
+        stage1_from<H, R1, HK, KXS, 1, NT, +1>(B0, PlaneLoad{gV + pbase, KXP, k, k, H, 1});
+        stage1_from<H, R1, HK, KXS, 1, NT, +1>(B1, PlaneLoad{gV + pbase, KXP, k, k, H, 2});
+        stage1_from<H, R1, HK, KXS, 1, NT, +1>(B2, PlaneLoad{gB + pbase, KXP, 0.f, 0.f, H, 0});
     }
-    fft_rest<H, HK, KXP, 1, NT, +1>(B0, tw);
-    fft_rest<H, HK, KXP, 1, NT, +1>(B1, tw);
-    if (group == 1) fft_rest<H, HK, KXP, 1, NT, +1>(B2, tw);
+    fft_rest<H, HK, KXS, 1, NT, +1>(B0, tw);
+    fft_rest<H, HK, KXS, 1, NT, +1>(B1, tw);
+    if (group == 1) fft_rest<H, HK, KXS, 1, NT, +1>(B2, tw);
     // inverse x: first stage from the packed half spectra (in place), second stage
     if (group == 1) {
-        // B2's rows in pairs -> Z2 (B2's own space); done first, B0/B1 are still intact
-        stage1_from<H, R1, H / 2, 1, RP, NT, +1>(Z2, PackLoad<H>{B2, B2 + KXP, 2 * KXP, 2 * KXP});
+        // B2's rows y and y + H/2 as one complex row -> Z2 (B2's own space); done
+        // first, B0/B1 are still intact
+        stage1_from<H, R1, H / 2, 1, RP, NT, +1>(Z2,
+                                                  PackLoad<H>{B2, B2 + (H / 2) * KXS, KXS, KXS});
     }
-    stage1_from<H, R1, H, 1, RP, NT, +1>(Z, PackLoad<H>{B0, B1, KXP, KXP});
+    stage1_from<H, R1, H, 1, RP, NT, +1>(Z, PackLoad<H>{B0, B1, KXS, KXS});
     fft_rest<H, H, 1, RP, NT, +1>(Z, tw);
     if (group == 1) fft_rest<H, H / 2, 1, RP, NT, +1>(Z2, tw);
     const size_t plane = static_cast<size_t>(z) * H * H;
     float* Gp = G + 4 * plane;
     if (group == 0) {
         // m^n, w^n, and w^n again as the fourth component of the gather array
+        // (consecutive lanes read consecutive x: no bank conflicts)
         const float sc = a.out_scale;
-        float4* p1 = reinterpret_cast<float4*>(m_out + plane);
-        float4* p2 = reinterpret_cast<float4*>(w_out + plane);
-        for (int g = threadIdx.x; g < H * H / 4; g += NT) {
-            const int y = (4 * g) / H, x0 = (4 * g) % H;
-            const float2 e0 = Z[y * RP + x0], e1 = Z[y * RP + x0 + 1];
-            const float2 e2 = Z[y * RP + x0 + 2], e3 = Z[y * RP + x0 + 3];
-            p1[g] = make_float4(e0.x * sc, e1.x * sc, e2.x * sc, e3.x * sc);
-            const float4 wv = make_float4(e0.y * sc, e1.y * sc, e2.y * sc, e3.y * sc);
-            p2[g] = wv;
-            Gp[16 * g + 3] = wv.x;
-            Gp[16 * g + 7] = wv.y;
-            Gp[16 * g + 11] = wv.z;
-            Gp[16 * g + 15] = wv.w;
+        float* p1 = m_out + plane;
+        float* p2 = w_out + plane;
+        for (int i = threadIdx.x; i < H * H; i += NT) {
+            const int y = i / H, x = i % H;
+            const float2 e = Z[y * RP + x];
+            const float wv = e.y * sc;
+            p1[i] = e.x * sc;
+            p2[i] = wv;
+            Gp[4 * i + 3] = wv;
         }
     } else {
         // (dv/dx, dv/dy, dv/dz) into components 0..2 of the gather array
@@ -455,9 +435,10 @@ __global__ void __launch_bounds__(Cfg<H>::NT3)
         for (int i = threadIdx.x; i < H * H; i += NT) {
             const int y = i / H, x = i % H;
             const float2 e = Z[y * RP + x];
-            const float2 f = Z2[(y >> 1) * RP + x];
+            const bool upper = y >= H / 2;
+            const float2 f = Z2[(upper ? y - H / 2 : y) * RP + x];
             *reinterpret_cast<float2*>(Gp + 4 * i) = make_float2(e.x * sxy, e.y * sxy);
-            Gp[4 * i + 2] = ((y & 1) ? f.y : f.x) * sz_;
+            Gp[4 * i + 2] = (upper ? f.y : f.x) * sz_;
         }
     }
 }
@@ -718,7 +699,7 @@ cudaError_t spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass) {
     constexpr int KXP = kxp<H>();
     const size_t sm1 = (static_cast<size_t>(H) * rowp<H>() + H * KXP + H) * sizeof(float2);
     const size_t sm2 = (static_cast<size_t>(H) * zcols<H>() + H) * sizeof(float2);
-    const size_t sm3 = (3 * static_cast<size_t>(H) * KXP + H) * sizeof(float2);
+    const size_t sm3 = (3 * static_cast<size_t>(H) * kxs<H>() + H) * sizeof(float2);
     static int configured_device = -1;   // attributes are set once per process and device
     if (configured_device != c->device) {
         cudaFuncSetAttribute(k_forward_xy<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -179,6 +179,51 @@ __device__ __forceinline__ void stage1_from(float2* out, Load load) {
     __syncthreads();
 }
 
+// A Stockham stage like `stage` whose outputs go to sink(t, p, v) (transform
+// t, output position p) instead of back into buf.  A block barrier separates
+// the reads from the sink calls and follows them, so the sink may write into
+// buf for the next stage.
+template <int L, int R, int NS, int NTRANS, int ES, int TS, int NT, int SIGN, class Sink>
+__device__ __forceinline__ void stage_sink(const float2* buf, const float2* tw, Sink sink) {
+    constexpr int NB = NTRANS * (L / R);
+    constexpr int BPT = (NB + NT - 1) / NT;
+    float2 v[BPT][R];
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        const int b = threadIdx.x + i * NT;
+        if (b < NB) {
+            const int t = b % NTRANS;
+            const int j = b / NTRANS;
+            const int k = j % NS;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float2 x = buf[t * TS + (j + r * (L / R)) * ES];
+                if (NS > 1 && r > 0) {
+                    float2 wv = tw[r * k * (L / (NS * R))];
+                    if (SIGN > 0) wv.y = -wv.y;
+                    x = cmul(x, wv);
+                }
+                v[i][r] = x;
+            }
+            dft<R, SIGN>(v[i]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        const int b = threadIdx.x + i * NT;
+        if (b < NB) {
+            const int t = b % NTRANS;
+            const int j = b / NTRANS;
+            const int k = j % NS;
+            const int base = (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) sink(t, base + r * NS, v[i][r]);
+        }
+    }
+    __syncthreads();
+}
+
 // Radix plan of a length-L transform: two to four Stockham stages (R3, R4 =
 // 1: fewer).  Lengths are 2^a 3^b with 8 <= L <= 512.
 template <int L> struct Radix;
@@ -210,6 +255,23 @@ __device__ __forceinline__ void fft_rest(float2* buf, const float2* tw) {
     stage<L, R2, R1, NTRANS, ES, TS, NT, SIGN>(buf, tw);
     if constexpr (R3 > 1) stage<L, R3, R1 * R2, NTRANS, ES, TS, NT, SIGN>(buf, tw);
     if constexpr (R4 > 1) stage<L, R4, R1 * R2 * R3, NTRANS, ES, TS, NT, SIGN>(buf, tw);
+}
+
+// The stages after the first, the last one into a sink (see stage_sink).
+template <int L, int NTRANS, int ES, int TS, int NT, int SIGN, class Sink>
+__device__ __forceinline__ void fft_rest_sink(float2* buf, const float2* tw, Sink sink) {
+    constexpr int R1 = Radix<L>::R1, R2 = Radix<L>::R2, R3 = Radix<L>::R3, R4 = Radix<L>::R4;
+    static_assert(R1 * R2 * R3 * R4 == L, "radix plan");
+    if constexpr (R3 == 1) {
+        stage_sink<L, R2, R1, NTRANS, ES, TS, NT, SIGN>(buf, tw, sink);
+    } else if constexpr (R4 == 1) {
+        stage<L, R2, R1, NTRANS, ES, TS, NT, SIGN>(buf, tw);
+        stage_sink<L, R3, R1 * R2, NTRANS, ES, TS, NT, SIGN>(buf, tw, sink);
+    } else {
+        stage<L, R2, R1, NTRANS, ES, TS, NT, SIGN>(buf, tw);
+        stage<L, R3, R1 * R2, NTRANS, ES, TS, NT, SIGN>(buf, tw);
+        stage_sink<L, R4, R1 * R2 * R3, NTRANS, ES, TS, NT, SIGN>(buf, tw, sink);
+    }
 }
 
 // Batched length-L FFT along one axis of a shared-memory array.
