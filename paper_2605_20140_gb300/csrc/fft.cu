@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT1)
         const float* wp = w + plane;
         unsigned long long* ap = acc + plane;
         float* vo = v_out + plane;
-#pragma unroll
+#pragma unroll 1
         for (int i0 = 0; i0 < ITER; i0 += CH) {
             float rv[CH][2], rm[CH][2], rw[CH][2], ru[CH][2];
             unsigned long long ra[CH][2];

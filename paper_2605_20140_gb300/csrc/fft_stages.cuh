@@ -103,12 +103,23 @@ __device__ __forceinline__ void dft(float2 (&v)[R]) {
     }
 }
 
-// One Stockham stage of radix R after NS points have been combined.
-// Transform t, element j lives at buf[t * TS + j * ES].  Consecutive lanes
-// take consecutive transforms (same butterfly), so a warp's accesses are
-// contiguous when TS == 1 and spread over all banks when TS is odd.
-template <int L, int R, int NS, int NTRANS, int ES, int TS, int NT, int SIGN>
-__device__ __forceinline__ void stage(float2* buf, const float2* tw) {
+// Element addressing of a batch of transforms: element j of transform t is
+// buf[at(t, j)].  Strided: transform t at t * TS, elements ES apart.
+template <int TS, int ES>
+struct Strided {
+    __device__ __forceinline__ int operator()(int t, int j) const { return t * TS + j * ES; }
+};
+
+// One Stockham stage of radix R after NS points have been combined, over
+// NTRANS transforms addressed by `at`.  Consecutive lanes take consecutive
+// transforms (same butterfly), so a warp's accesses are contiguous when
+// transforms are adjacent and spread over all banks when their pitch is odd.
+// The outputs go to sink(t, p, v) (transform t, output position p); a block
+// barrier separates the reads from the sink calls and follows them, so the
+// sink may write into buf.
+template <int L, int R, int NS, int NTRANS, int NT, int SIGN, class At, class Sink>
+__device__ __forceinline__ void stage_sink_at(const float2* buf, const float2* tw, At at,
+                                              Sink sink) {
     constexpr int NB = NTRANS * (L / R);
     constexpr int BPT = (NB + NT - 1) / NT;
     float2 v[BPT][R];
@@ -121,83 +132,7 @@ __device__ __forceinline__ void stage(float2* buf, const float2* tw) {
             const int k = j % NS;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                float2 x = buf[t * TS + (j + r * (L / R)) * ES];
-                if (NS > 1 && r > 0) {
-                    float2 wv = tw[r * k * (L / (NS * R))];
-                    if (SIGN > 0) wv.y = -wv.y;
-                    x = cmul(x, wv);
-                }
-                v[i][r] = x;
-            }
-            dft<R, SIGN>(v[i]);
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < BPT; ++i) {
-        const int b = threadIdx.x + i * NT;
-        if (b < NB) {
-            const int t = b % NTRANS;
-            const int j = b / NTRANS;
-            const int k = j % NS;
-            const int base = (j - k) * R + k;
-#pragma unroll
-            for (int r = 0; r < R; ++r) buf[t * TS + (base + r * NS) * ES] = v[i][r];
-        }
-    }
-    __syncthreads();
-}
-
-// First Stockham stage (NS = 1) with inputs from a loader: element j of
-// transform t is load(t, j).  All loads precede all writes (a block barrier
-// in between), so the loader may read the memory `out` overwrites.
-template <int L, int R, int NTRANS, int ES, int TS, int NT, int SIGN, class Load>
-__device__ __forceinline__ void stage1_from(float2* out, Load load) {
-    constexpr int NB = NTRANS * (L / R);
-    constexpr int BPT = (NB + NT - 1) / NT;
-    float2 v[BPT][R];
-#pragma unroll
-    for (int i = 0; i < BPT; ++i) {
-        const int b = threadIdx.x + i * NT;
-        if (b < NB) {
-            const int t = b % NTRANS, j = b / NTRANS;
-#pragma unroll
-            for (int r = 0; r < R; ++r) v[i][r] = load(t, j + r * (L / R));
-            dft<R, SIGN>(v[i]);
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < BPT; ++i) {
-        const int b = threadIdx.x + i * NT;
-        if (b < NB) {
-            const int t = b % NTRANS, j = b / NTRANS;
-#pragma unroll
-            for (int r = 0; r < R; ++r) out[t * TS + (j * R + r) * ES] = v[i][r];
-        }
-    }
-    __syncthreads();
-}
-
-// A Stockham stage like `stage` whose outputs go to sink(t, p, v) (transform
-// t, output position p) instead of back into buf.  A block barrier separates
-// the reads from the sink calls and follows them, so the sink may write into
-// buf for the next stage.
-template <int L, int R, int NS, int NTRANS, int ES, int TS, int NT, int SIGN, class Sink>
-__device__ __forceinline__ void stage_sink(const float2* buf, const float2* tw, Sink sink) {
-    constexpr int NB = NTRANS * (L / R);
-    constexpr int BPT = (NB + NT - 1) / NT;
-    float2 v[BPT][R];
-#pragma unroll
-    for (int i = 0; i < BPT; ++i) {
-        const int b = threadIdx.x + i * NT;
-        if (b < NB) {
-            const int t = b % NTRANS;
-            const int j = b / NTRANS;
-            const int k = j % NS;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                float2 x = buf[t * TS + (j + r * (L / R)) * ES];
+                float2 x = buf[at(t, j + r * (L / R))];
                 if (NS > 1 && r > 0) {
                     float2 wv = tw[r * k * (L / (NS * R))];
                     if (SIGN > 0) wv.y = -wv.y;
@@ -224,6 +159,59 @@ __device__ __forceinline__ void stage_sink(const float2* buf, const float2* tw, 
     __syncthreads();
 }
 
+// The same stage in place.
+template <int L, int R, int NS, int NTRANS, int NT, int SIGN, class At>
+__device__ __forceinline__ void stage_at(float2* buf, const float2* tw, At at) {
+    stage_sink_at<L, R, NS, NTRANS, NT, SIGN>(
+        buf, tw, at, [=](int t, int p, float2 v) { buf[at(t, p)] = v; });
+}
+
+template <int L, int R, int NS, int NTRANS, int ES, int TS, int NT, int SIGN>
+__device__ __forceinline__ void stage(float2* buf, const float2* tw) {
+    stage_at<L, R, NS, NTRANS, NT, SIGN>(buf, tw, Strided<TS, ES>{});
+}
+
+template <int L, int R, int NS, int NTRANS, int ES, int TS, int NT, int SIGN, class Sink>
+__device__ __forceinline__ void stage_sink(const float2* buf, const float2* tw, Sink sink) {
+    stage_sink_at<L, R, NS, NTRANS, NT, SIGN>(buf, tw, Strided<TS, ES>{}, sink);
+}
+
+// First Stockham stage (NS = 1) with inputs from a loader: element j of
+// transform t is load(t, j).  All loads precede all writes (a block barrier
+// in between), so the loader may read the memory `out` overwrites.
+template <int L, int R, int NTRANS, int NT, int SIGN, class At, class Load>
+__device__ __forceinline__ void stage1_from_at(float2* out, At at, Load load) {
+    constexpr int NB = NTRANS * (L / R);
+    constexpr int BPT = (NB + NT - 1) / NT;
+    float2 v[BPT][R];
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        const int b = threadIdx.x + i * NT;
+        if (b < NB) {
+            const int t = b % NTRANS, j = b / NTRANS;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[i][r] = load(t, j + r * (L / R));
+            dft<R, SIGN>(v[i]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        const int b = threadIdx.x + i * NT;
+        if (b < NB) {
+            const int t = b % NTRANS, j = b / NTRANS;
+#pragma unroll
+            for (int r = 0; r < R; ++r) out[at(t, j * R + r)] = v[i][r];
+        }
+    }
+    __syncthreads();
+}
+
+template <int L, int R, int NTRANS, int ES, int TS, int NT, int SIGN, class Load>
+__device__ __forceinline__ void stage1_from(float2* out, Load load) {
+    stage1_from_at<L, R, NTRANS, NT, SIGN>(out, Strided<TS, ES>{}, load);
+}
+
 // Radix plan of a length-L transform: two to four Stockham stages (R3, R4 =
 // 1: fewer).  Lengths are 2^a 3^b with 8 <= L <= 512.
 template <int L> struct Radix;
@@ -247,38 +235,51 @@ template <> struct Radix<384> : RadixPlan<16, 8, 3> {};
 template <> struct Radix<432> : RadixPlan<16, 3, 3, 3> {};
 template <> struct Radix<512> : RadixPlan<8, 8, 8> {};
 
-// The stages after the first of a batched length-L FFT.
-template <int L, int NTRANS, int ES, int TS, int NT, int SIGN>
-__device__ __forceinline__ void fft_rest(float2* buf, const float2* tw) {
-    constexpr int R1 = Radix<L>::R1, R2 = Radix<L>::R2, R3 = Radix<L>::R3, R4 = Radix<L>::R4;
-    static_assert(R1 * R2 * R3 * R4 == L, "radix plan");
-    stage<L, R2, R1, NTRANS, ES, TS, NT, SIGN>(buf, tw);
-    if constexpr (R3 > 1) stage<L, R3, R1 * R2, NTRANS, ES, TS, NT, SIGN>(buf, tw);
-    if constexpr (R4 > 1) stage<L, R4, R1 * R2 * R3, NTRANS, ES, TS, NT, SIGN>(buf, tw);
-}
-
-// The stages after the first, the last one into a sink (see stage_sink).
-template <int L, int NTRANS, int ES, int TS, int NT, int SIGN, class Sink>
-__device__ __forceinline__ void fft_rest_sink(float2* buf, const float2* tw, Sink sink) {
+// The stages after the first of a batched length-L FFT, the last one into a
+// sink (see stage_sink_at).
+template <int L, int NTRANS, int NT, int SIGN, class At, class Sink>
+__device__ __forceinline__ void fft_rest_sink_at(float2* buf, const float2* tw, At at, Sink sink) {
     constexpr int R1 = Radix<L>::R1, R2 = Radix<L>::R2, R3 = Radix<L>::R3, R4 = Radix<L>::R4;
     static_assert(R1 * R2 * R3 * R4 == L, "radix plan");
     if constexpr (R3 == 1) {
-        stage_sink<L, R2, R1, NTRANS, ES, TS, NT, SIGN>(buf, tw, sink);
+        stage_sink_at<L, R2, R1, NTRANS, NT, SIGN>(buf, tw, at, sink);
     } else if constexpr (R4 == 1) {
-        stage<L, R2, R1, NTRANS, ES, TS, NT, SIGN>(buf, tw);
-        stage_sink<L, R3, R1 * R2, NTRANS, ES, TS, NT, SIGN>(buf, tw, sink);
+        stage_at<L, R2, R1, NTRANS, NT, SIGN>(buf, tw, at);
+        stage_sink_at<L, R3, R1 * R2, NTRANS, NT, SIGN>(buf, tw, at, sink);
     } else {
-        stage<L, R2, R1, NTRANS, ES, TS, NT, SIGN>(buf, tw);
-        stage<L, R3, R1 * R2, NTRANS, ES, TS, NT, SIGN>(buf, tw);
-        stage_sink<L, R4, R1 * R2 * R3, NTRANS, ES, TS, NT, SIGN>(buf, tw, sink);
+        stage_at<L, R2, R1, NTRANS, NT, SIGN>(buf, tw, at);
+        stage_at<L, R3, R1 * R2, NTRANS, NT, SIGN>(buf, tw, at);
+        stage_sink_at<L, R4, R1 * R2 * R3, NTRANS, NT, SIGN>(buf, tw, at, sink);
     }
 }
 
-// Batched length-L FFT along one axis of a shared-memory array.
+// The stages after the first, in place.
+template <int L, int NTRANS, int NT, int SIGN, class At>
+__device__ __forceinline__ void fft_rest_at(float2* buf, const float2* tw, At at) {
+    fft_rest_sink_at<L, NTRANS, NT, SIGN>(
+        buf, tw, at, [=](int t, int p, float2 v) { buf[at(t, p)] = v; });
+}
+
+template <int L, int NTRANS, int ES, int TS, int NT, int SIGN>
+__device__ __forceinline__ void fft_rest(float2* buf, const float2* tw) {
+    fft_rest_at<L, NTRANS, NT, SIGN>(buf, tw, Strided<TS, ES>{});
+}
+
+template <int L, int NTRANS, int ES, int TS, int NT, int SIGN, class Sink>
+__device__ __forceinline__ void fft_rest_sink(float2* buf, const float2* tw, Sink sink) {
+    fft_rest_sink_at<L, NTRANS, NT, SIGN>(buf, tw, Strided<TS, ES>{}, sink);
+}
+
+// Batched length-L FFT along one axis, in place.
+template <int L, int NTRANS, int NT, int SIGN, class At>
+__device__ __forceinline__ void fft_axis_at(float2* buf, const float2* tw, At at) {
+    stage_at<L, Radix<L>::R1, 1, NTRANS, NT, SIGN>(buf, tw, at);
+    fft_rest_at<L, NTRANS, NT, SIGN>(buf, tw, at);
+}
+
 template <int L, int NTRANS, int ES, int TS, int NT, int SIGN>
 __device__ __forceinline__ void fft_axis(float2* buf, const float2* tw) {
-    stage<L, Radix<L>::R1, 1, NTRANS, ES, TS, NT, SIGN>(buf, tw);
-    fft_rest<L, NTRANS, ES, TS, NT, SIGN>(buf, tw);
+    fft_axis_at<L, NTRANS, NT, SIGN>(buf, tw, Strided<TS, ES>{});
 }
 
 }  // namespace fftk
