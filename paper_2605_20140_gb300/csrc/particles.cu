@@ -304,11 +304,13 @@ __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
             double pl = 0.0;
             uint32_t pid = 0u;
             if (valid) {
-                px = src.sx[i];
-                py = src.sy[i];
-                pz = src.sz[i];
-                pl = src.dl[i];
-                pid = src.id[i];
+                // read and written once per step: evict first, so that the
+                // gather blocks and deposit sums keep their place in L2
+                px = __ldcs(src.sx + i);
+                py = __ldcs(src.sy + i);
+                pz = __ldcs(src.sz + i);
+                pl = __ldcs(src.dl + i);
+                pid = __ldcs(src.id + i);
             }
             const Cell c = locate(px, py, pz, H);
 
@@ -439,11 +441,11 @@ __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
                             atomicOr(status, kStatusSlot);
                     }
                     if (dest >= 0) {
-                        dst.sx[dest] = px;
-                        dst.sy[dest] = py;
-                        dst.sz[dest] = pz;
-                        dst.dl[dest] = pl;
-                        dst.id[dest] = pid;
+                        __stcs(dst.sx + dest, px);
+                        __stcs(dst.sy + dest, py);
+                        __stcs(dst.sz + dest, pz);
+                        __stcs(dst.dl + dest, pl);
+                        __stcs(dst.id + dest, pid);
                     }
                 }
             }
