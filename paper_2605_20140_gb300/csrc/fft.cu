@@ -52,15 +52,16 @@ template <> struct Cfg<72> { static constexpr int NT1 = 512, NT2 = 352, NT3 = 51
 template <> struct Cfg<96> { static constexpr int NT1 = 768, NT2 = 608, NT3 = 768; };
 // 544 = 17 warps: one radix-16 butterfly per thread for the 65 z-transforms
 template <> struct Cfg<128> { static constexpr int NT1 = 1024, NT2 = 544, NT3 = 1024; };
-// H > 128 runs the per-axis pipeline; NT2 is the z pass over 32-column tiles
-template <> struct Cfg<144> { static constexpr int NT1 = 256, NT2 = 288, NT3 = 256; };
-template <> struct Cfg<192> { static constexpr int NT1 = 256, NT2 = 384, NT3 = 256; };
-template <> struct Cfg<216> { static constexpr int NT1 = 256, NT2 = 896, NT3 = 256; };
-template <> struct Cfg<256> { static constexpr int NT1 = 256, NT2 = 512, NT3 = 256; };
-template <> struct Cfg<288> { static constexpr int NT1 = 256, NT2 = 576, NT3 = 256; };
-template <> struct Cfg<384> { static constexpr int NT1 = 256, NT2 = 768, NT3 = 256; };
-template <> struct Cfg<432> { static constexpr int NT1 = 256, NT2 = 896, NT3 = 256; };
-template <> struct Cfg<512> { static constexpr int NT1 = 256, NT2 = 1024, NT3 = 256; };
+// H > 128 runs the per-axis pipeline; only the z pass (over 32-column tiles)
+// takes its threads from here
+template <> struct Cfg<144> { static constexpr int NT2 = 288; };
+template <> struct Cfg<192> { static constexpr int NT2 = 384; };
+template <> struct Cfg<216> { static constexpr int NT2 = 896; };
+template <> struct Cfg<256> { static constexpr int NT2 = 512; };
+template <> struct Cfg<288> { static constexpr int NT2 = 576; };
+template <> struct Cfg<384> { static constexpr int NT2 = 768; };
+template <> struct Cfg<432> { static constexpr int NT2 = 896; };
+template <> struct Cfg<512> { static constexpr int NT2 = 1024; };
 
 // kx columns per block of the z pass: the whole padded row up to H = 128
 template <int H> constexpr int zcols() { return H <= 128 ? H / 2 + 2 : 32; }
