@@ -907,7 +907,10 @@ int step_grid(sipf_ctx* c) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<4>, kNT, 0);
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<2>, kNT, 0);
-    const int g = nsm * (per_sm > 0 ? per_sm : 1);
+    int g = nsm * (per_sm > 0 ? per_sm : 1);
+    // no more blocks than items can exist: a small run leaves the rest of the
+    // GPU to the runs beside it
+    if (g > c->max_items) g = c->max_items;
     return g > 0 ? g : 1;
 }
 
