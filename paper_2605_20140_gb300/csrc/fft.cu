@@ -6,14 +6,19 @@
 //  1. per z-plane: read v, m, w and the integer deposit accumulator, form
 //     m* = m + tau u, w* = w + tau (gamma v - eta(u) w), v^n = v/(1 + alpha tau m),
 //     store v^n, and transform m*, w*, v^n along x and y in shared memory
-//     (m* + i w* as one complex plane; v^n as pairs of rows).  Writes three
-//     half spectra [z][ky][kx], kx <= H/2.
+//     (m* + i w* as one complex plane; v^n as pairs of rows y, y + H/2).
+//     Writes three half spectra [z][ky][kx], kx <= H/2.
 //  2. per (ky, field) slab: forward FFT along z, multiply by
 //     1/(1 + tau beta + tau Dm |k|^2) (m), 1/(1 + tau + tau Dw |k|^2) (w), or
-//     i k_z (v -> B), inverse FFT along z; in place for m and w.
+//     i k_z (v -> B), inverse FFT along z; in place for m and w.  The load,
+//     the multiply and the store ride on the first and last DFT stages.
 //  3. per (z-plane, group): inverse FFT along y and a packed complex inverse
-//     along x: (m, w), (i k_x V, i k_y V) -> (dv/dx, dv/dy), and B in row
-//     pairs -> dv/dz.  Writes m^n, w^n and grad v^n, scaled by 1/H^3.
+//     along x: (m, w), (i k_x V, i k_y V) -> (dv/dx, dv/dy), and B in rows
+//     y, y + H/2 -> dv/dz.  Writes m^n, w^n and grad v^n, scaled by 1/H^3.
+//
+// Shared-memory layouts keep a warp's accesses free of bank conflicts: lanes
+// take consecutive transforms, whose elements lie one float2 apart or at an
+// odd pitch (H + 1 for rows, H/2 + 1 for the inverse pass's half spectra).
 //
 // The FFT is a Stockham radix-R formulation (natural order in and out): each
 // stage loads R strided elements per butterfly into registers, applies the
