@@ -154,7 +154,7 @@ def _peaks():
 # valid only while the kernel's source is the one captured.
 NCU_TRAFFIC = {"particle_step": (("paper_2605_20140_gb300/csrc/particles.cu",
                                   "paper_2605_20140_gb300/csrc/sipf_internal.cuh"),
-                                 "ca7ec99713cd6d84", 154.8e6)}
+                                 "25baa52bdeb1b600", 154.6e6)}
 
 
 def _ncu_traffic(group):
