@@ -317,30 +317,6 @@ __device__ __forceinline__ float2 pack_two(const float2* r1, const float2* r2, i
     return make_float2(a.x - b.y, a.y + b.x);
 }
 
-// Pack NR row pairs (rows 2r, 2r+1 of B, or row r of B and of B2) into
-// full complex rows Z[r][0..H) of pitch RP; all reads precede all writes.
-template <int H, int NR, int NT, bool PAIRS>
-__device__ __forceinline__ void pack_rows(const float2* B, const float2* B2, float2* Z) {
-    constexpr int KXP = kxp<H>(), RP = rowp<H>(), NE = NR * H, EPT = (NE + NT - 1) / NT;
-    float2 r[EPT];
-#pragma unroll
-    for (int s = 0; s < EPT; ++s) {
-        const int idx = threadIdx.x + s * NT;
-        if (idx < NE) {
-            const int row = idx / H, kx = idx % H;
-            r[s] = PAIRS ? pack_two<H>(B + (2 * row) * KXP, B + (2 * row + 1) * KXP, kx)
-                         : pack_two<H>(B + row * KXP, B2 + row * KXP, kx);
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int s = 0; s < EPT; ++s) {
-        const int idx = threadIdx.x + s * NT;
-        if (idx < NE) Z[(idx / H) * RP + idx % H] = r[s];
-    }
-    __syncthreads();
-}
-
 // Loaders for the fused first stages of the inverse pass.
 struct PlaneLoad {      // half-spectrum plane from global memory, optionally times i k
     const float2* p;
