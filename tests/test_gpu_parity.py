@@ -709,3 +709,16 @@ def test_regularised_m_source_matches_oracle(H, N, steps):
     # more than the tolerance
     plain = O.run(oracle_state(wl), wl.dt, steps)
     assert rel_l2(st.m, plain.m) > 20 * FIELD_TOL
+
+
+def test_all_options_together_radix3_grid():
+    """Fourth-order assignment, the low-pass filter H0 = H^(8/13) and the
+    K_sigma-regularised m source at once, on a 2^a 3^b grid: five steps
+    against the oracle."""
+    wl = workload("small", H=48, N=1 << 15)
+    h = wl.L / wl.H
+    p = dataclasses.replace(wl.params, p2g_order=4, H0=48 ** (8 / 13), sigma=(1.5 * h) ** 2)
+    sim = run_gpu(wl, 5, p=p)
+    st = O.run(oracle_state(wl, p=p), wl.dt, 5)
+    _compare(sim, st, wl)
+    sim.close()
