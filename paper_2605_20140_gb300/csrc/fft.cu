@@ -579,31 +579,27 @@ __global__ void __launch_bounds__(kSxNT)
     constexpr int RB = kSxRows, NT = kSxNT, KXP = kxp<H>(), RP = rowp<H>();
     constexpr int NZ = RB + RB + RB / 2;       // packed rows: (m, w), (dx, dy), dz pairs
     extern __shared__ float2 sm[];
-    float2* hb = sm;                           // 5 fields x [RB][KXP] half rows
-    float2* Z = hb + 5 * RB * KXP;             // [NZ][RP]
+    float2* Z = sm;                            // [NZ][RP]
     float2* tw = Z + NZ * RP;
     const int z = blockIdx.y, y0 = blockIdx.x * RB;
     for (int i = threadIdx.x; i < H; i += NT) tw[i] = twg[i];
-    for (int q = threadIdx.x; q < 5 * RB * (KXP / 2); q += NT) {
-        const int f = q / (RB * (KXP / 2)), rem = q % (RB * (KXP / 2));
-        const int r = rem / (KXP / 2), k = 2 * (rem % (KXP / 2));
-        if (f < 2 && !a.do_mw) continue;
-        const float2* src = f == 0 ? gM : f == 1 ? gW : f == 2 ? gDx : f == 3 ? gDy : gB;
-        *reinterpret_cast<float4*>(hb + (f * RB + r) * KXP + k) = *reinterpret_cast<const float4*>(
-            src + (static_cast<size_t>(z) * H + y0 + r) * KXP + k);
-    }
-    __syncthreads();
+    // pack straight from the half spectra in global memory (consecutive lanes
+    // read consecutive, or mirrored consecutive, kx), so that the block holds
+    // only the packed rows and more blocks share an SM
+    auto row = [z, y0](const float2* f, int r) {
+        return f + (static_cast<size_t>(z) * H + y0 + r) * KXP;
+    };
     for (int q = threadIdx.x; q < NZ * H; q += NT) {
         const int zr = q / H, kx = q % H;
         float2 val;
         if (zr < RB) {
-            val = a.do_mw ? pack_two<H>(hb + zr * KXP, hb + (RB + zr) * KXP, kx) : make_float2(0.f, 0.f);
+            val = a.do_mw ? pack_two<H>(row(gM, zr), row(gW, zr), kx) : make_float2(0.f, 0.f);
         } else if (zr < 2 * RB) {
             const int r = zr - RB;
-            val = pack_two<H>(hb + (2 * RB + r) * KXP, hb + (3 * RB + r) * KXP, kx);
+            val = pack_two<H>(row(gDx, r), row(gDy, r), kx);
         } else {
             const int p = zr - 2 * RB;
-            val = pack_two<H>(hb + (4 * RB + 2 * p) * KXP, hb + (4 * RB + 2 * p + 1) * KXP, kx);
+            val = pack_two<H>(row(gB, 2 * p), row(gB, 2 * p + 1), kx);
         }
         Z[zr * RP + kx] = val;
     }
@@ -636,8 +632,7 @@ cudaError_t spectral_pass_split(sipf_ctx* c, const SpectralArgs& a, int pass) {
     const size_t smx1 = (3 * static_cast<size_t>(RB) * KXP + H) * sizeof(float2);
     const size_t smy = (2 * static_cast<size_t>(H) * (KB + 1) + H) * sizeof(float2);
     const size_t smz = (static_cast<size_t>(H) * zcols<H>() + H) * sizeof(float2);
-    const size_t smx2 =
-        (5 * static_cast<size_t>(RB) * KXP + (2 * RB + RB / 2) * RP + H) * sizeof(float2);
+    const size_t smx2 = (static_cast<size_t>(2 * RB + RB / 2) * RP + H) * sizeof(float2);
     static int configured_device = -1;
     if (configured_device != c->device) {
         cudaFuncSetAttribute(k_sx_forward<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
