@@ -535,9 +535,9 @@ __global__ void __launch_bounds__(kSxNT)
                  const float2* __restrict__ twg, int plain) {
     constexpr int NT = kSxNT, KXP = kxp<H>(), KB = kSxCols, CP = KB + 1;
     extern __shared__ float2 sm[];
-    float2* b0 = sm;               // [H (y)][CP]
-    float2* b1 = b0 + H * CP;      // second buffer (derivatives)
-    float2* tw = b1 + H * CP;
+    float2* tw = sm;               // [H]
+    float2* b0 = tw + H;           // [H (y)][CP]
+    float2* b1 = b0 + H * CP;      // second buffer (derivatives; allocated only for them)
     const int k0 = blockIdx.x * KB, z = blockIdx.y, field = blockIdx.z;
     if (!plain && field < 2 && !a.do_mw) return;
     const bool deriv = !plain && SIGN > 0 && field == 2;
@@ -630,7 +630,9 @@ template <int H>
 cudaError_t spectral_pass_split(sipf_ctx* c, const SpectralArgs& a, int pass) {
     constexpr int KXP = kxp<H>(), RB = kSxRows, KB = kSxCols, RP = rowp<H>();
     const size_t smx1 = (3 * static_cast<size_t>(RB) * KXP + H) * sizeof(float2);
-    const size_t smy = (2 * static_cast<size_t>(H) * (KB + 1) + H) * sizeof(float2);
+    // the column passes: one buffer, or two where V becomes i k_x V and i k_y V
+    const size_t smy1 = (static_cast<size_t>(H) * (KB + 1) + H) * sizeof(float2);
+    const size_t smy2 = (2 * static_cast<size_t>(H) * (KB + 1) + H) * sizeof(float2);
     const size_t smz = (static_cast<size_t>(H) * zcols<H>() + H) * sizeof(float2);
     const size_t smx2 = (static_cast<size_t>(2 * RB + RB / 2) * RP + H) * sizeof(float2);
     static int configured_device = -1;
@@ -638,9 +640,9 @@ cudaError_t spectral_pass_split(sipf_ctx* c, const SpectralArgs& a, int pass) {
         cudaFuncSetAttribute(k_sx_forward<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(smx1));
         cudaFuncSetAttribute(k_sx_columns<H, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(smy));
+                             static_cast<int>(smy1));
         cudaFuncSetAttribute(k_sx_columns<H, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(smy));
+                             static_cast<int>(smy2));
         cudaFuncSetAttribute(k_z_multiply<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(smz));
         cudaFuncSetAttribute(k_sx_inverse<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -652,18 +654,18 @@ cudaError_t spectral_pass_split(sipf_ctx* c, const SpectralArgs& a, int pass) {
         k_sx_forward<H><<<dim3(H / RB, H), kSxNT, smx1, c->stream>>>(
             a, c->v, c->m, c->w, reinterpret_cast<unsigned long long*>(c->acc), c->v, c->specM,
             c->specW, c->specV, c->twiddle, c->voff, c->dsc + c->cur, c->us);
-        k_sx_columns<H, -1><<<gy, kSxNT, smy, c->stream>>>(a, c->specM, c->specW, c->specV,
-                                                             nullptr, nullptr, c->twiddle, 0);
+        k_sx_columns<H, -1><<<gy, kSxNT, smy1, c->stream>>>(a, c->specM, c->specW, c->specV,
+                                                              nullptr, nullptr, c->twiddle, 0);
     } else if (pass == 1) {
         k_z_multiply<H><<<dim3(H, 4, (KXP + zcols<H>() - 1) / zcols<H>()), Cfg<H>::NT2, smz,
                           c->stream>>>(a, c->specM, c->specW, c->specV, c->specB, c->specA,
                                        c->twiddle, c->voff);
     } else {
         // inverse y: M, W and B in place; V (or its filtered copy) -> i k_x V, i k_y V
-        k_sx_columns<H, +1><<<gy, kSxNT, smy, c->stream>>>(
+        k_sx_columns<H, +1><<<gy, kSxNT, smy2, c->stream>>>(
             a, c->specM, c->specW, a.filter ? c->specA : c->specV, c->specDx, c->specDy, c->twiddle,
             0);
-        k_sx_columns<H, +1><<<dim3(gy.x, H, 1), kSxNT, smy, c->stream>>>(
+        k_sx_columns<H, +1><<<dim3(gy.x, H, 1), kSxNT, smy1, c->stream>>>(
             a, c->specB, c->specB, c->specB, nullptr, nullptr, c->twiddle, 1);
         k_sx_inverse<H><<<dim3(H / RB, H), kSxNT, smx2, c->stream>>>(
             a, c->specM, c->specW, c->specDx, c->specDy, c->specB, c->m, c->w, c->G, c->twiddle);
