@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 from oracle import sipf_oracle as O
-from sipf_inputs import Params
+from sipf_inputs import Params, workload
 
 
 def _state(H=16, L=1.0, N=64, p=None, x=None, mass=None, v=None, m=None, w=None, seed=0):
@@ -521,3 +521,39 @@ def test_gaussian_smoothing_equals_the_periodised_kernel_in_real_space():
     got = O.gaussian_smooth(u, L, sigma)
     assert np.max(np.abs(got - want)) <= 1e-9 * np.abs(want).max()
     assert abs(got.mean() - u.mean()) <= 1e-14
+
+
+def test_gather_error_is_second_order_on_smooth_fields():
+    """Trilinear interpolation of a smooth periodic field at random points:
+    the error falls as h^2 (ratio about 4 per halving of h)."""
+    rng = np.random.default_rng(7)
+    pts = rng.random((4000, 3))                      # physical positions in [0, 1)^3
+
+    def f(x, y, z):
+        return np.sin(2 * np.pi * x + 0.3) * np.cos(2 * np.pi * y) + 0.5 * np.sin(4 * np.pi * z)
+
+    errs = []
+    for H in (16, 32, 64):
+        q = np.arange(H) / H
+        Z, Y, X = np.meshgrid(q, q, q, indexing="ij")
+        g = O.gather(f(X, Y, Z), pts * H)
+        errs.append(np.max(np.abs(g - f(pts[:, 0], pts[:, 1], pts[:, 2]))))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.3 < r1 < 4.7 and 3.3 < r2 < 4.7, errs
+
+
+def test_positivity_on_the_small_workload():
+    """The deposit is non-negative exactly (trilinear weights), v stays
+    positive under the implicit update and w under its source (tau <= 1/2);
+    m is positive up to the negative off-centre entries of the truncated
+    implicit multiplier, bounded by 3 n tau Dm / h^2 of its maximum after n
+    steps (measured -1.3e-5 after 20 steps, against the bound 6.1e-5)."""
+    wl = workload("small", H=32, N=1 << 15)
+    st = O.make_state(wl.H, wl.L, wl.origin, wl.params, wl.x, wl.mass, wl.ids, wl.v, wl.m, wl.w)
+    h = wl.L / wl.H
+    for n in range(1, 21):
+        st = O.step(st, wl.dt)
+        assert O.density(st).min() >= 0.0
+        assert st.v.min() > 0.0
+        assert st.w.min() > 0.0
+        assert st.m.min() >= -3 * n * wl.dt * wl.params.Dm / h ** 2 * np.abs(st.m).max()
