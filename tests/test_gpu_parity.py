@@ -722,3 +722,25 @@ def test_all_options_together_radix3_grid():
     st = O.run(oracle_state(wl, p=p), wl.dt, 5)
     _compare(sim, st, wl)
     sim.close()
+
+
+def test_non_finite_field_is_reported_and_the_context_recovers():
+    """Failure detection without a fault: a NaN planted in v makes grad v, and
+    so every pushed position, non-finite; the step kernel resets those
+    positions to 0 and raises the status word, which the next synchronising
+    call reports as SIPF_ENONFINITE.  The word is then clear, and a fresh
+    state steps cleanly on the same context."""
+    wl = workload("small", H=16, N=4096)
+    v = wl.v.copy()
+    v[3, 4, 5] = np.nan
+    sim = run_gpu(wl, 0, v=v)
+    sim.step(wl.dt, 1)
+    with pytest.raises(sipf.SipfError) as err:
+        sipf.sipf_sync(sim.ctx)
+    assert err.value.code == sipf.SIPF_ENONFINITE
+    sim.set_state(wl.x, wl.mass, wl.ids, wl.v, wl.m, wl.w)
+    sim.step(wl.dt, 2)
+    sipf.sipf_sync(sim.ctx)
+    d = sim.diagnostics()
+    assert d["nonfinite"] == 0 and d["step"] == 2
+    sim.close()
