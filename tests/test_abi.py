@@ -11,6 +11,7 @@ import tempfile
 import pytest
 
 from paper_2605_20140_gb300 import sipf
+from sipf_inputs import Params
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "sipf.h")
@@ -180,3 +181,13 @@ def test_server_queues_and_validates_without_touching_the_gpu(lib):
         assert e.value.code == sipf.SIPF_EINVAL
     finally:
         small.close()
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without the built library every entry point raises."""
+    monkeypatch.setattr(sipf, "LIB_PATH", str(tmp_path / "libsipf.so"))
+    monkeypatch.setattr(sipf, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        sipf.load()
+    with pytest.raises(RuntimeError, match="missing"):
+        sipf.Simulation(16, 1.0, (0.0, 0.0, 0.0), 64, Params())
