@@ -175,6 +175,21 @@ def _ncu_traffic(group):
     return traffic if h.hexdigest()[:16] == digest else None
 
 
+def _host_cpu():
+    """Core count and CPU model of this host (reported beside the CPU numbers)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                if not model.isdigit():
+                    break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
 def _cpu_baseline(wl_fn, n_sample_steps=1):
     """The FP64 oracle as it stands on this host: one full step of the
     workload (about 10-30 s of CPU work)."""
@@ -187,7 +202,8 @@ def _cpu_baseline(wl_fn, n_sample_steps=1):
     dt = time.perf_counter() - t0
     return {"value": wl.N * n_sample_steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{n_sample_steps} full step(s) of the 128^3 / 2^22 workload, "
-                      f"NumPy FP64, single thread, {dt:.1f} s"}
+                      f"NumPy FP64, single thread, {dt:.1f} s",
+            "host": _host_cpu()}
 
 
 def run_reference(args, rank, world):
@@ -224,7 +240,7 @@ def run_reference(args, rank, world):
            "data": "synthetic",
            "config": {"workload": WORKLOAD + " (sampled)", "H": H, "N": n_sample},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": sample},
+                            "sample": sample, "host": _host_cpu()},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -277,16 +293,23 @@ def run_sipf(args, rank, world, local):
     clocks = ClockSampler(local)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    _barrier(world)
-    torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
-    e0.record(stream)
-    n_diag = _advance(sim, dt, args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    _barrier(world)
-    ms_total = _max_over_ranks(e0.elapsed_time(e1), world)
+    # `repeats` timed regions of --steps steps each (CUDA events on the
+    # launching stream, barrier and synchronisation on both sides); the line
+    # reports the median region and the spread of all of them
+    reps = []
+    n_diag = 0
+    for _ in range(args.repeats):
+        _barrier(world)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        n_diag += _advance(sim, dt, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        _barrier(world)
+        reps.append(_max_over_ranks(e0.elapsed_time(e1), world))
+    ms_total = statistics.median(reps)
     # ---- per-kernel-group times: further steps traced with CUDA events between
     # the groups on the launching stream (tracing enqueues launch by launch)
     n_prof = min(args.steps, 200)
@@ -323,7 +346,7 @@ def run_sipf(args, rank, world, local):
     # per step: the traced groups' launches, plus the bucket-layout plan kernel
     # on the context's second stream
     launches = int(round((sum(v[1] for v in prof.values()) / max(n_prof, 1) + 1) * args.steps))
-    launches += DIAG_LAUNCHES * n_diag
+    launches += DIAG_LAUNCHES * n_diag // max(args.repeats, 1)
     sim.close()
 
     # ---- end to end through the C ABI with host buffers
@@ -342,17 +365,26 @@ def run_sipf(args, rank, world, local):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sipf.sipf_set_state(sim2.ctx, hx, hm, hid, hv, hmm, hw, sipf.SIPF_HOST)
+        t1 = time.perf_counter()
         _advance(sim2, dt, args.steps)
+        sipf.sipf_sync(sim2.ctx)
+        t2 = time.perf_counter()
         sipf.sipf_fields(sim2.ctx, sipf.FIELD_U | sipf.FIELD_V | sipf.FIELD_M | sipf.FIELD_W,
                          out, sipf.SIPF_HOST)
-        el = _max_over_ranks(time.perf_counter() - t0, world)
+        t3 = time.perf_counter()
+        el = _max_over_ranks(t3 - t0, world)
         sim2.close()
         h2d = hx.nbytes + hm.nbytes + hid.nbytes + hv.nbytes + hmm.nbytes + hw.nbytes
         d2h = out.nbytes
         e2e = {"value": world * N * args.steps / el, "unit": UNIT,
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                "job": f"set_state from pinned host + {args.steps} steps (diagnostics every "
-                      f"{DIAG_EVERY}) + u,v,m,w to host"}
+                      f"{DIAG_EVERY}) + u,v,m,w to host",
+               # the one-off upload and download against the steps: a short run
+               # is dominated by the upload, not by a slow step path
+               "split_ms": {"upload_set_state": 1e3 * (t1 - t0),
+                            "steps": 1e3 * (t2 - t1), "download_fields": 1e3 * (t3 - t2)},
+               "steps_only_value": world * N * args.steps / (t2 - t1)}
 
     if rank != 0:
         return 0
@@ -361,6 +393,9 @@ def run_sipf(args, rank, world, local):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32 (f64 log-mass and reductions)", "data": "synthetic",
+           "repeats": {"n": len(reps), "ms_per_step": [r / args.steps for r in reps],
+                       "spread": (max(reps) - min(reps)) / ms_total,
+                       "value_is": "median of the timed regions"},
            "config": {"workload": WORKLOAD, "H": H, "N": N, "dt": dt,
                       "parallelism": f"replicas x{world}",
                       "l2": "no flush: the step's working set (~300 MB) exceeds the 129 MB L2",
@@ -531,6 +566,8 @@ def main():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["sipf", "reference"], default="sipf")
+    ap.add_argument("--repeats", type=int, default=5,
+                    help="timed regions of --steps steps; the median is reported")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -177,6 +177,19 @@ int sipf_particle_state(sipf_ctx* ctx, float* s, double* loga, uint32_t* id, int
  * ((cz%8) 8 + cy%8) 8 + cx%8, cell (cx, cy, cz) = floor(s).  Synchronises. */
 int sipf_cell_start(sipf_ctx* ctx, int32_t* cell_start, int where);
 
+/* The canonical particle order: cell_start as sipf_cell_start (may be NULL)
+ * and ids (N uint32; may be NULL) = the particles' ids sorted by (cell key,
+ * id), a deterministic order for the particle loops of Alg. 1
+ * (particle-to-grid) and Alg. 2 (grid-to-particle), which the paper leaves
+ * unordered; the run of cell key k is ids[cell_start[k] .. cell_start[k+1]).
+ * The step itself never needs this order: its deposit sums integers, so no
+ * order of the particles changes u_bar by a bit; this call makes the order a
+ * checkable output.  Computed on the device (counting sort by key, then rank
+ * by id inside each cell's run); uses the context's free particle buffer as
+ * work space, allocates nothing.  Synchronises.  Errors: SIPF_EINVAL (both
+ * pointers NULL, bad `where`, no state), SIPF_ECUDA. */
+int sipf_canonical_order(sipf_ctx* ctx, int32_t* cell_start, uint32_t* ids, int where);
+
 /* FP64 diagnostics of the current state; synchronises. */
 int sipf_diagnostics(sipf_ctx* ctx, sipf_diag* out);
 
@@ -257,9 +270,27 @@ int64_t sipf_device_bytes(const sipf_ctx* ctx);
  * sipf_server_collect: copies the fields of a finished request (mask and
  * layout as sipf_fields, host buffer) and releases its device memory; mask
  * 0 only releases.  sipf_server_stats: device bytes in use and at most in
- * use so far, queued and admitted-but-uncollected requests.  Errors of a
- * request's own calls are returned by the call that made them, with
- * sipf_server_last_error describing them. */
+ * use so far, queued and admitted-but-uncollected requests.
+ *
+ * Failures: submit rejects what sipf_create or sipf_set_state would reject
+ * (SIPF_EINVAL, including a negative or non-finite mass).  A request whose
+ * admission or steps fail later (a CUDA error; device memory short of the
+ * budget) is marked failed and stops; it never blocks the queue.  It is
+ * reported by sipf_server_poll like a finished one, and sipf_server_collect
+ * returns its error code (with sipf_server_last_error saying what failed)
+ * and releases it.
+ *
+ * Device memory: a request's context takes its arrays from a stream-ordered
+ * memory pool owned by the server (cudaMallocFromPoolAsync), whose release
+ * threshold is the budget, and its stream and event from a free list, so
+ * admission and collection call neither cudaMalloc nor cudaFree (which can
+ * synchronise the device and stall the requests in flight).
+ *
+ * sipf_server_set_limit: admit at most max_live requests at a time (0, the
+ * default: only the budget limits); 1 serves the requests one at a time.
+ * sipf_server_fail_next_admission: fault injection for tests -- the next
+ * admission attempt fails with `code` (< 0) before touching the GPU.
+ * Errors of both: SIPF_EINVAL. */
 typedef struct sipf_server sipf_server;
 int sipf_server_create(int64_t budget_bytes, sipf_server** out);
 int sipf_server_submit(sipf_server* srv, const sipf_grid* grid, int64_t N,
@@ -273,6 +304,8 @@ int sipf_server_stats(const sipf_server* srv, int64_t* in_use, int64_t* peak, in
                       int32_t* live);
 const char* sipf_server_last_error(const sipf_server* srv);
 void sipf_server_destroy(sipf_server* srv);
+int sipf_server_set_limit(sipf_server* srv, int32_t max_live);
+int sipf_server_fail_next_admission(sipf_server* srv, int code);
 
 /* Checkpoint / resume.  The paper has no checkpoint; what is saved is the
  * state of the scheme after step n of Alg. 3: the particles X^n (grid units)
@@ -356,6 +389,8 @@ const char* sipf_profile_name(int k);
  * SIPF_FIELD_U, for N particles with physical positions x (3*N floats, SoA,
  * wrapped into the box) and masses `mass` (N doubles, >= 0), into u (H^3
  * floats, [z][y][x]); x, mass and u are device pointers owned by the caller.
+ * A particle whose mass is not finite (inf, NaN) or not positive contributes
+ * nothing (the context path rejects such masses in sipf_set_state instead).
  * It calls no cudaMalloc, cudaFree or other allocating routine: its integer
  * accumulator is a fixed array in the library's device memory, sized for at
  * most 64^3 nodes, which every GPU that loads the library keeps until the
@@ -364,7 +399,9 @@ const char* sipf_profile_name(int k);
  * Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default
  * stream) and the call returns without waiting; launch failures return
  * SIPF_ECUDA.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) and should come before any stream capture.
+ * address (cudaGetSymbolAddress) and should come before any stream capture;
+ * the address is kept for the life of the process, so the call must not be
+ * used on a device after a cudaDeviceReset of it in the same process.
  * Every call on a device shares the one array and clears it before use, so
  * calls whose work overlaps on the GPU (different streams, or threads
  * without ordering) race and corrupt each other's results; order them on

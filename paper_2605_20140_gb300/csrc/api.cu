@@ -115,6 +115,8 @@ size_t ctx_device_bytes(int H, int64_t N, bool filter, bool smoothing) {
     return b;
 }
 
+// Frees the arrays sipf_create allocated (stream-ordered on the context's
+// stream when they came from a pool) and the resampling work space.
 void free_all(sipf_ctx* c) {
     void* ptrs[] = {c->sx[0], c->sx[1], c->sy[0], c->sy[1], c->sz[0], c->sz[1], c->dl[0],
                     c->dl[1], c->id[0], c->id[1], c->bstart[0], c->bstart[1], c->cap[0],
@@ -122,10 +124,16 @@ void free_all(sipf_ctx* c) {
                     c->work, c->count, c->cell_start, c->scan_tmp, c->acc, c->v, c->m, c->w,
                     c->G, c->specM, c->specW, c->specV, c->specB, c->specA, c->specDx,
                     c->specDy, c->twiddle,
-                    c->status, c->diag_tmp, c->diag_out, c->diag_ll, c->voff, c->rs_scratch,
+                    c->status, c->diag_tmp, c->diag_out, c->diag_ll, c->voff,
                     c->dsc, c->us, c->ksig};
-    for (void* q : ptrs)
-        if (q) cudaFree(q);
+    for (void* q : ptrs) {
+        if (!q) continue;
+        if (c->pool)
+            cudaFreeAsync(q, c->stream);
+        else
+            cudaFree(q);
+    }
+    if (c->rs_scratch) cudaFree(c->rs_scratch);
 }
 
 int copy_in(sipf_ctx* c, void* dst, const void* src, size_t bytes, int where) {
@@ -454,6 +462,15 @@ const char* sipf_last_error(const sipf_ctx* ctx) { return ctx ? ctx->last_error.
 
 int sipf_create(const sipf_grid* grid, int64_t N, const sipf_params* params, void* stream,
                 sipf_ctx** out) {
+    return sipf::create_in_pool(grid, N, params, static_cast<cudaStream_t>(stream), nullptr, out);
+}
+
+}  // extern "C"
+
+namespace sipf {
+
+int create_in_pool(const sipf_grid* grid, int64_t N, const sipf_params* params,
+                   cudaStream_t stream, cudaMemPool_t pool, sipf_ctx** out) {
     if (!out || !grid || !params) return SIPF_EINVAL;
     *out = nullptr;
     std::string why;
@@ -474,7 +491,8 @@ int sipf_create(const sipf_grid* grid, int64_t N, const sipf_params* params, voi
     c->N = N;
     c->p = *params;
     if (c->p.p2g_order == 0) c->p.p2g_order = 2;
-    c->stream = static_cast<cudaStream_t>(stream);
+    c->stream = stream;
+    c->pool = pool;
     cudaGetDevice(&c->device);
     const CtxSizes z = ctx_sizes(c->H, N);
     const size_t H3 = z.H3, spec = z.spec;
@@ -491,6 +509,9 @@ int sipf_create(const sipf_grid* grid, int64_t N, const sipf_params* params, voi
     // every allocation of the context is counted in dev_bytes
     auto da = [c](auto** p, size_t n) {
         c->dev_bytes += n * sizeof(**p);
+        if (c->pool)
+            return cudaMallocFromPoolAsync(reinterpret_cast<void**>(p), n * sizeof(**p), c->pool,
+                                           c->stream);
         return dalloc(p, n);
     };
     bool ok = true;
@@ -528,13 +549,16 @@ int sipf_create(const sipf_grid* grid, int64_t N, const sipf_params* params, voi
         delete c;
         return SIPF_ENOMEM;
     }
+    // host staging lives until the stream synchronisation below
     std::vector<float2> tw(c->H);
+    std::vector<float> ks(c->ksig ? c->H : 0);
     fill_twiddles(c->H, tw.data());
-    cudaError_t e = cudaMemcpy(c->twiddle, tw.data(), c->H * sizeof(float2), cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpyAsync(c->twiddle, tw.data(), c->H * sizeof(float2),
+                                    cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && c->ksig) {
-        std::vector<float> ks(c->H);
         fill_smoothing(c->H, c->L, params->sigma, ks.data());
-        e = cudaMemcpy(c->ksig, ks.data(), c->H * sizeof(float), cudaMemcpyHostToDevice);
+        e = cudaMemcpyAsync(c->ksig, ks.data(), c->H * sizeof(float), cudaMemcpyHostToDevice,
+                            c->stream);
     }
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
         e = cudaMemsetAsync(c->bstart[b], 0, sizeof(int) * c->ntiles, c->stream);
@@ -563,6 +587,10 @@ int sipf_create(const sipf_grid* grid, int64_t N, const sipf_params* params, voi
     *out = c;
     return SIPF_OK;
 }
+
+}  // namespace sipf
+
+extern "C" {
 
 int sipf_set_state(sipf_ctx* c, const float* x, const double* mass, const uint32_t* id,
                    const float* v, const float* m, const float* w, int where) {
@@ -593,23 +621,27 @@ int sipf_set_state(sipf_ctx* c, const float* x, const double* mass, const uint32
     set_mass_reference(c);
     c->step = 0;
     c->time = 0.0;
-    // upload into buffer 1 (unordered), then bin into buffer 0
-    float* xin = nullptr;
-    double* min_ = nullptr;
+    // wrap into buffer 1 (unordered), then bin into buffer 0.  Host input is
+    // staged in buffer 0 first (free until the binning; each of its arrays
+    // has room for N values), so the call allocates nothing.
+    const float* px = x;
+    const float* py = x + N;
+    const float* pz = x + 2 * N;
+    const double* pm = mass;
     if (where == SIPF_HOST) {
-        SIPF_CUDA(c, dalloc(&xin, 3 * N));
-        SIPF_CUDA(c, dalloc(&min_, N));
-        int r = copy_in(c, xin, x, 3 * N * sizeof(float), SIPF_HOST);
-        if (r == SIPF_OK) r = copy_in(c, min_, mass, N * sizeof(double), SIPF_HOST);
-        if (r != SIPF_OK) {
-            cudaFree(xin);
-            cudaFree(min_);
-            return r;
-        }
+        int r = copy_in(c, c->sx[0], x, N * sizeof(float), SIPF_HOST);
+        if (r == SIPF_OK) r = copy_in(c, c->sy[0], x + N, N * sizeof(float), SIPF_HOST);
+        if (r == SIPF_OK) r = copy_in(c, c->sz[0], x + 2 * N, N * sizeof(float), SIPF_HOST);
+        if (r == SIPF_OK) r = copy_in(c, c->dl[0], mass, N * sizeof(double), SIPF_HOST);
+        if (r != SIPF_OK) return r;
+        px = c->sx[0];
+        py = c->sy[0];
+        pz = c->sz[0];
+        pm = c->dl[0];
     }
     int r = SIPF_OK;
-    cudaError_t e = launch_wrap_positions(c, where == SIPF_HOST ? xin : x, 1);
-    if (e == cudaSuccess) e = launch_rel_log_mass(c, where == SIPF_HOST ? min_ : mass, 1);
+    cudaError_t e = launch_wrap_positions(c, px, py, pz, 1);
+    if (e == cudaSuccess) e = launch_rel_log_mass(c, pm, 1);
     if (e == cudaSuccess) {
         if (id) {
             r = copy_in(c, c->id[1], id, N * sizeof(uint32_t), where);
@@ -649,8 +681,6 @@ int sipf_set_state(sipf_ctx* c, const float* x, const double* mass, const uint32
         if (e == cudaSuccess) e = launch_spectral_step(c, spectral_args(c, 0.0, 0));
     }
     if (e == cudaSuccess && r == SIPF_OK) e = cudaStreamSynchronize(c->stream);
-    if (xin) cudaFree(xin);
-    if (min_) cudaFree(min_);
     if (e != cudaSuccess) return cuda_fail(c, e, "sipf_set_state");
     if (r != SIPF_OK) return r;
     r = check_status(c);
@@ -677,7 +707,9 @@ int sipf_fields(sipf_ctx* c, uint32_t mask, float* dst, int where) {
     if (!c->state_set) return fail(c, SIPF_EINVAL, "sipf_set_state has not been called");
     const size_t H3 = static_cast<size_t>(c->H) * c->H * c->H;
     const float* src[4] = {nullptr, c->v, c->m, c->w};
-    float* tmp = nullptr;
+    // staging for host copies: the per-cell histogram array (H^3 words, used
+    // only by sipf_cell_start), so the call allocates nothing
+    float* tmp = reinterpret_cast<float*>(c->count);
     size_t off = 0;
     for (int b = 0; b < 7; ++b) {
         if (!(mask & (1u << b))) continue;
@@ -685,14 +717,11 @@ int sipf_fields(sipf_ctx* c, uint32_t mask, float* dst, int where) {
             if (where == SIPF_DEVICE) {
                 SIPF_CUDA(c, launch_component(c, b - 4, dst + off));
             } else {
-                SIPF_CUDA(c, dalloc(&tmp, H3));
                 cudaError_t e = launch_component(c, b - 4, tmp);
                 if (e == cudaSuccess)
                     e = cudaMemcpyAsync(dst + off, tmp, H3 * sizeof(float), cudaMemcpyDeviceToHost,
                                         c->stream);
                 if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-                cudaFree(tmp);
-                tmp = nullptr;
                 if (e != cudaSuccess) return cuda_fail(c, e, "sipf_fields(grad v)");
             }
         } else if (b == 0) {
@@ -701,14 +730,11 @@ int sipf_fields(sipf_ctx* c, uint32_t mask, float* dst, int where) {
             if (where == SIPF_DEVICE) {
                 SIPF_CUDA(c, launch_acc_to_float(c, dst + off, acc_to_u(c)));
             } else {
-                SIPF_CUDA(c, dalloc(&tmp, H3));
                 cudaError_t e = launch_acc_to_float(c, tmp, acc_to_u(c));
                 if (e == cudaSuccess)
                     e = cudaMemcpyAsync(dst + off, tmp, H3 * sizeof(float), cudaMemcpyDeviceToHost,
                                         c->stream);
                 if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-                cudaFree(tmp);
-                tmp = nullptr;
                 if (e != cudaSuccess) return cuda_fail(c, e, "sipf_fields(U)");
             }
         } else {
@@ -750,36 +776,24 @@ int sipf_particles(sipf_ctx* c, float* x, double* mass, uint32_t* id, int where)
     int r = compact_current(c);
     if (r != SIPF_OK) return r;
     const int o = c->cur ^ 1;
-    float* tx = nullptr;
-    double* tm = nullptr;
+    // the compacted copy in the free buffer is converted in place (positions
+    // to physical coordinates, log-masses to masses), so nothing is allocated
     cudaError_t e = cudaSuccess;
+    const cudaMemcpyKind kind = where == SIPF_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     if (x) {
-        float* dx = x;
-        if (where == SIPF_HOST) {
-            e = dalloc(&tx, 3 * N);
-            dx = tx;
-        }
-        if (e == cudaSuccess) e = launch_export_positions(c, o, dx);
-        if (e == cudaSuccess && where == SIPF_HOST)
-            e = cudaMemcpyAsync(x, tx, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+        e = launch_export_positions_inplace(c, o);
+        const float* arr[3] = {c->sx[o], c->sy[o], c->sz[o]};
+        for (int d = 0; d < 3 && e == cudaSuccess; ++d)
+            e = cudaMemcpyAsync(x + d * N, arr[d], N * sizeof(float), kind, c->stream);
     }
     if (e == cudaSuccess && mass) {
-        double* dm = mass;
-        if (where == SIPF_HOST) {
-            e = dalloc(&tm, N);
-            dm = tm;
-        }
-        if (e == cudaSuccess) e = launch_export_mass(c, o, dm, 0);
-        if (e == cudaSuccess && where == SIPF_HOST)
-            e = cudaMemcpyAsync(mass, tm, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        e = launch_export_mass(c, o, c->dl[o], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(mass, c->dl[o], N * sizeof(double), kind, c->stream);
     }
     if (e == cudaSuccess && id)
-        e = cudaMemcpyAsync(id, c->id[o], N * sizeof(uint32_t),
-                            where == SIPF_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
-                            c->stream);
+        e = cudaMemcpyAsync(id, c->id[o], N * sizeof(uint32_t), kind, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (tx) cudaFree(tx);
-    if (tm) cudaFree(tm);
     if (e != cudaSuccess) return cuda_fail(c, e, "sipf_particles");
     return check_status(c);
 }
@@ -793,6 +807,22 @@ int sipf_cell_start(sipf_ctx* c, int32_t* cell_start, int where) {
     if (r != SIPF_OK) return r;
     SIPF_CUDA(c, launch_cell_histogram(c, c->cur ^ 1, c->count, c->scan_tmp, c->cell_start));
     r = copy_out(c, cell_start, c->cell_start, (H3 + 1) * sizeof(int32_t), where);
+    if (r != SIPF_OK) return r;
+    return check_status(c);
+}
+
+int sipf_canonical_order(sipf_ctx* c, int32_t* cell_start, uint32_t* ids, int where) {
+    if (!c || (!cell_start && !ids)) return SIPF_EINVAL;
+    if (where != SIPF_HOST && where != SIPF_DEVICE) return fail(c, SIPF_EINVAL, "bad where");
+    if (!c->state_set) return fail(c, SIPF_EINVAL, "sipf_set_state has not been called");
+    const size_t H3 = static_cast<size_t>(c->H) * c->H * c->H;
+    int r = compact_current(c);
+    if (r != SIPF_OK) return r;
+    const int o = c->cur ^ 1;
+    SIPF_CUDA(c, launch_canonical_order(c, o));
+    if (cell_start) r = copy_out(c, cell_start, c->cell_start, (H3 + 1) * sizeof(int32_t), where);
+    if (r == SIPF_OK && ids)
+        r = copy_out(c, ids, c->id[o], static_cast<size_t>(c->N) * sizeof(uint32_t), where);
     if (r != SIPF_OK) return r;
     return check_status(c);
 }

@@ -38,11 +38,16 @@ __global__ void k_na_clear(unsigned long long* s, int nodes) {
     if (i < kCtl + nodes) s[i] = 0ull;
 }
 
-__global__ void k_na_max_mass(const double* __restrict__ mass, int N, unsigned long long* s) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// A particle contributes only if its mass is finite and positive: an
+// infinite or NaN mass is skipped (it would otherwise fix the scale of every
+// node), a zero mass adds nothing anyway.
+__device__ __forceinline__ bool na_counts(double m) { return isfinite(m) && m > 0.0; }
+
+__global__ void k_na_max_mass(const double* __restrict__ mass, int64_t N, unsigned long long* s) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i < N) {
         const double m = mass[i];
-        if (m > 0.0) atomicMax(reinterpret_cast<long long*>(s), __double_as_longlong(m));
+        if (na_counts(m)) atomicMax(reinterpret_cast<long long*>(s), __double_as_longlong(m));
     }
 }
 
@@ -55,13 +60,13 @@ __device__ __forceinline__ int na_shift(const unsigned long long* s) {
     return 30 - e;
 }
 
-__global__ void k_na_deposit(const float* __restrict__ x, const double* __restrict__ mass, int N,
-                             int H, float o0, float o1, float o2, float h,
+__global__ void k_na_deposit(const float* __restrict__ x, const double* __restrict__ mass,
+                             int64_t N, int H, float o0, float o1, float o2, float h,
                              unsigned long long* s) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double m = mass[i];
-    if (!(m > 0.0)) return;
+    if (!na_counts(m)) return;
     const float Hf = __int2float_rn(H);
     const float o[3] = {o0, o1, o2};
     int c[3], c1[3];
@@ -69,13 +74,13 @@ __global__ void k_na_deposit(const float* __restrict__ x, const double* __restri
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         // grid units, wrapped into [0, H) (a result rounding to H becomes 0)
-        float v = __fdiv_rn(__fsub_rn(x[d * N + i], o[d]), h);
+        float v = __fdiv_rn(__fsub_rn(x[static_cast<int64_t>(d) * N + i], o[d]), h);
         if (!(v >= 0.0f && v < Hf)) {
             v = __fsub_rn(v, __fmul_rn(Hf, floorf(__fdiv_rn(v, Hf))));
             if (v < 0.0f) v = __fadd_rn(v, Hf);
             if (!(v < Hf)) v = 0.0f;
         }
-        c[d] = min(static_cast<int>(v), H - 1);
+        c[d] = min(max(static_cast<int>(v), 0), H - 1);
         c1[d] = c[d] + 1 < H ? c[d] + 1 : 0;
         f[d] = __fsub_rn(v, __int2float_rn(c[d]));
     }
@@ -103,6 +108,8 @@ __global__ void k_na_finish(const unsigned long long* s, int nodes, double inv_h
 
 // Device address of the scratch array on the current device (looked up
 // once per device; host code only sees a host-side stand-in otherwise).
+// The address is kept for the life of the process, so the entry point must
+// not be used on a device after cudaDeviceReset in the same process.
 int scratch_for_current_device(unsigned long long** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SIPF_ECUDA;
@@ -132,12 +139,12 @@ extern "C" int sipf_deposit_noalloc(const sipf_grid* grid, const float* x, const
     if (r != SIPF_OK) return r;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int nodes = H * H * H;
-    const int n = static_cast<int>(N);
     const double h = grid->L / H;
+    const unsigned pblocks = static_cast<unsigned>((N + 255) / 256);   // N < 2^31: fits
     k_na_clear<<<(kCtl + nodes + 255) / 256, 256, 0, st>>>(s, nodes);
-    k_na_max_mass<<<(n + 255) / 256, 256, 0, st>>>(mass, n, s);
-    k_na_deposit<<<(n + 255) / 256, 256, 0, st>>>(
-        x, mass, n, H, static_cast<float>(grid->origin[0]), static_cast<float>(grid->origin[1]),
+    k_na_max_mass<<<pblocks, 256, 0, st>>>(mass, N, s);
+    k_na_deposit<<<pblocks, 256, 0, st>>>(
+        x, mass, N, H, static_cast<float>(grid->origin[0]), static_cast<float>(grid->origin[1]),
         static_cast<float>(grid->origin[2]), static_cast<float>(h), s);
     k_na_finish<<<(nodes + 255) / 256, 256, 0, st>>>(s, nodes, 1.0 / (h * h * h), u);
     if (cudaGetLastError() != cudaSuccess) return SIPF_ECUDA;

@@ -698,8 +698,46 @@ __global__ void __launch_bounds__(kScanNT) k_scan_apply(const int* __restrict__ 
     }
 }
 
+// ------------------------------------------------------------------ canonical order
+// The particles of a buffer sorted by (cell key, id): a counting sort by key
+// (slots of a cell's run taken in arrival order), then each particle's rank
+// among the ids of its run, which places it at its canonical position.  Ties
+// in id (possible only for caller-given duplicate ids) are broken by slot,
+// so the result is always a permutation.
+__global__ void k_canon_scatter(const float* __restrict__ sx, const float* __restrict__ sy,
+                                const float* __restrict__ sz, const uint32_t* __restrict__ id,
+                                int N, int H, const int* __restrict__ cell_start,
+                                int* __restrict__ fill, uint32_t* __restrict__ keys_tmp,
+                                uint32_t* __restrict__ ids_tmp) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const Cell c = locate(sx[i], sy[i], sz[i], H);
+    const uint32_t key = cell_key(c.cx, c.cy, c.cz, H >> 3);
+    const int slot = cell_start[key] + atomicAdd(fill + key, 1);
+    keys_tmp[slot] = key;
+    ids_tmp[slot] = id[i];
+}
+
+__global__ void k_canon_rank(const uint32_t* __restrict__ keys_tmp,
+                             const uint32_t* __restrict__ ids_tmp, int N,
+                             const int* __restrict__ cell_start, uint32_t* __restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const uint32_t key = keys_tmp[j];
+    const int b = cell_start[key], e = cell_start[key + 1];
+    const uint32_t me = ids_tmp[j];
+    int rank = 0;
+    for (int t = b; t < e; ++t) {
+        const uint32_t o = ids_tmp[t];
+        rank += (o < me) || (o == me && t < j);
+    }
+    out[b + rank] = me;
+}
+
 // ------------------------------------------------------------------ misc
-__global__ void k_wrap_positions(const float* __restrict__ x, int N, float o0, float o1, float o2,
+// Physical coordinates (three arrays) -> grid units wrapped into [0, H).
+__global__ void k_wrap_positions(const float* __restrict__ x, const float* __restrict__ y,
+                                 const float* __restrict__ z, int N, float o0, float o1, float o2,
                                  float h, int H, float* sx, float* sy, float* sz,
                                  int* __restrict__ status) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -707,8 +745,8 @@ __global__ void k_wrap_positions(const float* __restrict__ x, int N, float o0, f
     const float Hf = __int2float_rn(H);
     int bad = 0;
     sx[i] = wrap(__fdiv_rn(__fsub_rn(x[i], o0), h), Hf, &bad);
-    sy[i] = wrap(__fdiv_rn(__fsub_rn(x[N + i], o1), h), Hf, &bad);
-    sz[i] = wrap(__fdiv_rn(__fsub_rn(x[2 * N + i], o2), h), Hf, &bad);
+    sy[i] = wrap(__fdiv_rn(__fsub_rn(y[i], o1), h), Hf, &bad);
+    sz[i] = wrap(__fdiv_rn(__fsub_rn(z[i], o2), h), Hf, &bad);
     if (bad) atomicOr(status, kStatusNonfinite);
 }
 
@@ -722,14 +760,10 @@ __global__ void k_iota(uint32_t* id, int N) {
     if (i < N) id[i] = static_cast<uint32_t>(i);
 }
 
-__global__ void k_export_positions(const float* __restrict__ sx, const float* __restrict__ sy,
-                                   const float* __restrict__ sz, int N, float o0, float o1,
-                                   float o2, float h, float* x) {
+// Grid units -> physical coordinates, in place (each array on its own).
+__global__ void k_export_inplace(float* __restrict__ s, int N, float o, float h) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    x[i] = __fmaf_rn(sx[i], h, o0);
-    x[N + i] = __fmaf_rn(sy[i], h, o1);
-    x[2 * N + i] = __fmaf_rn(sz[i], h, o2);
+    if (i < N) s[i] = __fmaf_rn(s[i], h, o);
 }
 
 __global__ void k_export_mass(const double* __restrict__ dl, int N, double logref, double* out,
@@ -827,13 +861,19 @@ __global__ void __launch_bounds__(kDiagNT)
     }
 }
 
-__global__ void k_diag_final(const double* __restrict__ part_d, const long long* __restrict__ part_l,
-                             double acc_to_u, int K, double logref, double* __restrict__ out) {
-    if (threadIdx.x != 0) return;
+// One block: each thread folds a strided share of the partials, then a
+// shared-memory tree.  Every quantity is exact (integer sums, 128-bit mass
+// sum, minima, counts held exactly in doubles), so the result does not
+// depend on the order of the combination.
+constexpr int kDiagFinalNT = 256;
+
+__global__ void __launch_bounds__(kDiagFinalNT)
+    k_diag_final(const double* __restrict__ part_d, const long long* __restrict__ part_l,
+                 double acc_to_u, int K, double logref, double* __restrict__ out) {
     double mv = INFINITY, mm = INFINITY, mw = INFINITY, nf = 0;
     unsigned __int128 mass = 0;
     long long as = 0, amin = LLONG_MAX;
-    for (int b = 0; b < kDiagBlocks; ++b) {
+    for (int b = threadIdx.x; b < kDiagBlocks; b += kDiagFinalNT) {
         mv = dmin(mv, part_d[b * 5 + 1]);
         mm = dmin(mm, part_d[b * 5 + 2]);
         mw = dmin(mw, part_d[b * 5 + 3]);
@@ -843,20 +883,47 @@ __global__ void k_diag_final(const double* __restrict__ part_d, const long long*
         mass += (static_cast<unsigned __int128>(static_cast<uint64_t>(part_l[b * 4 + 3])) << 64) |
                 static_cast<uint64_t>(part_l[b * 4 + 2]);
     }
-    const double mass_d = static_cast<double>(static_cast<uint64_t>(mass >> 64)) * 18446744073709551616.0 +
-                          static_cast<double>(static_cast<uint64_t>(mass));
+    __shared__ double sd[4][kDiagFinalNT];
+    __shared__ long long sl[2][kDiagFinalNT];
+    __shared__ unsigned __int128 sq[kDiagFinalNT];
+    const int t = threadIdx.x;
+    sd[0][t] = mv;
+    sd[1][t] = mm;
+    sd[2][t] = mw;
+    sd[3][t] = nf;
+    sl[0][t] = as;
+    sl[1][t] = amin;
+    sq[t] = mass;
+    __syncthreads();
+    for (int s = kDiagFinalNT / 2; s > 0; s >>= 1) {
+        if (t < s) {
+            sd[0][t] = dmin(sd[0][t], sd[0][t + s]);
+            sd[1][t] = dmin(sd[1][t], sd[1][t + s]);
+            sd[2][t] = dmin(sd[2][t], sd[2][t + s]);
+            sd[3][t] += sd[3][t + s];
+            sl[0][t] += sl[0][t + s];
+            sl[1][t] = sl[1][t + s] < sl[1][t] ? sl[1][t + s] : sl[1][t];
+            sq[t] += sq[t + s];
+        }
+        __syncthreads();
+    }
+    if (t != 0) return;
+    const unsigned __int128 total = sq[0];
+    const double mass_d = static_cast<double>(static_cast<uint64_t>(total >> 64)) * 18446744073709551616.0 +
+                          static_cast<double>(static_cast<uint64_t>(total));
     out[0] = scalbn(mass_d, -K) * exp(logref);
-    out[1] = static_cast<double>(as) * acc_to_u;   // sum of u_bar (times h^3 on the host)
-    out[2] = static_cast<double>(amin) * acc_to_u;
-    out[3] = mv;
-    out[4] = mm;
-    out[5] = mw;
-    out[6] = nf;
+    out[1] = static_cast<double>(sl[0][0]) * acc_to_u;   // sum of u_bar (times h^3 on the host)
+    out[2] = static_cast<double>(sl[1][0]) * acc_to_u;
+    out[3] = sd[0][0];
+    out[4] = sd[1][0];
+    out[5] = sd[2][0];
+    out[6] = sd[3][0];
 }
 
-__global__ void k_normals(const uint32_t* __restrict__ ids, int N, uint32_t n, uint32_t k0,
+__global__ void k_normals(const uint32_t* __restrict__ ids, int64_t N, uint32_t n, uint32_t k0,
                           uint32_t k1, float* __restrict__ z, uint32_t* __restrict__ bits) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    // 64-bit offsets: 4 N exceeds the int range for N above 2^29
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= N) return;
     uint4 raw;
     const float3 r = brownian(ids[i], n, k0, k1, &raw);
@@ -971,10 +1038,30 @@ cudaError_t launch_cell_histogram(sipf_ctx* c, int b, int* count, int* tmp, int*
     return cudaGetLastError();
 }
 
-cudaError_t launch_wrap_positions(sipf_ctx* c, const float* x, int buf) {
+cudaError_t launch_canonical_order(sipf_ctx* c, int b) {
+    const int N = static_cast<int>(c->N);
+    const int n = c->H * c->H * c->H;
+    cudaError_t e = launch_cell_histogram(c, b, c->count, c->scan_tmp, c->cell_start);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(c->count, 0, static_cast<size_t>(n) * sizeof(int), c->stream);
+    if (e != cudaSuccess) return e;
+    // the buffer's log-mass array (8 N bytes) holds the keys and ids of the
+    // counting sort; the ranked ids go to the buffer's id array
+    uint32_t* keys_tmp = reinterpret_cast<uint32_t*>(c->dl[b]);
+    uint32_t* ids_tmp = keys_tmp + N;
+    k_canon_scatter<<<blocks_for(N, 256), 256, 0, c->stream>>>(
+        c->sx[b], c->sy[b], c->sz[b], c->id[b], N, c->H, c->cell_start, c->count, keys_tmp,
+        ids_tmp);
+    k_canon_rank<<<blocks_for(N, 256), 256, 0, c->stream>>>(keys_tmp, ids_tmp, N, c->cell_start,
+                                                            c->id[b]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wrap_positions(sipf_ctx* c, const float* x, const float* y, const float* z,
+                                  int buf) {
     const int N = static_cast<int>(c->N);
     k_wrap_positions<<<blocks_for(N, 256), 256, 0, c->stream>>>(
-        x, N, static_cast<float>(c->origin[0]), static_cast<float>(c->origin[1]),
+        x, y, z, N, static_cast<float>(c->origin[0]), static_cast<float>(c->origin[1]),
         static_cast<float>(c->origin[2]), static_cast<float>(c->h), c->H, c->sx[buf], c->sy[buf],
         c->sz[buf], c->status);
     return cudaGetLastError();
@@ -992,12 +1079,12 @@ cudaError_t launch_iota(sipf_ctx* c, int buf) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_export_positions(sipf_ctx* c, int b, float* x) {
+cudaError_t launch_export_positions_inplace(sipf_ctx* c, int b) {
     const int N = static_cast<int>(c->N);
-    k_export_positions<<<blocks_for(N, 256), 256, 0, c->stream>>>(
-        c->sx[b], c->sy[b], c->sz[b], N, static_cast<float>(c->origin[0]),
-        static_cast<float>(c->origin[1]), static_cast<float>(c->origin[2]),
-        static_cast<float>(c->h), x);
+    float* arr[3] = {c->sx[b], c->sy[b], c->sz[b]};
+    for (int d = 0; d < 3; ++d)
+        k_export_inplace<<<blocks_for(N, 256), 256, 0, c->stream>>>(
+            arr[d], N, static_cast<float>(c->origin[d]), static_cast<float>(c->h));
     return cudaGetLastError();
 }
 
@@ -1030,14 +1117,14 @@ cudaError_t launch_diagnostics(sipf_ctx* c, int b, double acc_to_u) {
         c->dl[b], c->logref, c->sx[b], c->sy[b], c->sz[b], static_cast<int>(c->N), c->v, c->m,
         c->w, reinterpret_cast<const unsigned long long*>(c->acc), c->H * c->H * c->H, K,
         c->diag_tmp, c->diag_ll);
-    k_diag_final<<<1, 32, 0, c->stream>>>(c->diag_tmp, c->diag_ll, acc_to_u, K, c->logref,
+    k_diag_final<<<1, kDiagFinalNT, 0, c->stream>>>(c->diag_tmp, c->diag_ll, acc_to_u, K, c->logref,
                                           c->diag_out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_normals(const uint32_t* ids, int64_t N, uint32_t n, uint64_t seed, float* z,
                            uint32_t* bits, cudaStream_t s) {
-    k_normals<<<blocks_for(N, 256), 256, 0, s>>>(ids, static_cast<int>(N), n,
+    k_normals<<<blocks_for(N, 256), 256, 0, s>>>(ids, N, n,
                                                  static_cast<uint32_t>(seed),
                                                  static_cast<uint32_t>(seed >> 32), z, bits);
     return cudaGetLastError();

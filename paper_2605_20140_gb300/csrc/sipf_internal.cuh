@@ -150,6 +150,7 @@ struct sipf_ctx {
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_join = nullptr;
     int device = 0;
+    cudaMemPool_t pool = nullptr;        // stream-ordered allocation from this pool (null: cudaMalloc)
 
     // particle store, ping-pong; positions in grid units, log-mass relative
     // to logref, ids; tile buckets followed by an overflow region of N
@@ -247,10 +248,14 @@ cudaError_t launch_tile_count(sipf_ctx* c, int b, int* cnt);
 cudaError_t launch_plan_flat(sipf_ctx* c);
 cudaError_t launch_compact(sipf_ctx* c, int b, int out);
 cudaError_t launch_cell_histogram(sipf_ctx* c, int b, int* count, int* tmp, int* cell_start);
-cudaError_t launch_wrap_positions(sipf_ctx* c, const float* x, int buf);
+// cell_start of buffer b and its ids in canonical (cell key, id) order, the
+// latter into b's id array (b's log-masses are overwritten as work space)
+cudaError_t launch_canonical_order(sipf_ctx* c, int b);
+cudaError_t launch_wrap_positions(sipf_ctx* c, const float* x, const float* y, const float* z,
+                                  int buf);
+cudaError_t launch_export_positions_inplace(sipf_ctx* c, int b);
 cudaError_t launch_rel_log_mass(sipf_ctx* c, const double* mass, int buf);
 cudaError_t launch_iota(sipf_ctx* c, int buf);
-cudaError_t launch_export_positions(sipf_ctx* c, int b, float* x);
 cudaError_t launch_export_mass(sipf_ctx* c, int b, double* out, int as_log);
 cudaError_t launch_acc_to_float(sipf_ctx* c, float* dst, float scale);
 cudaError_t launch_component(sipf_ctx* c, int comp, float* dst);
@@ -261,6 +266,11 @@ cudaError_t launch_conv_check(const float* f, const double* d, int n, int* misma
                               cudaStream_t s);
 // api.cu
 int run_steps_for(sipf_ctx* c, double dt, int64_t k);
+// sipf_create with every device array taken from `pool` on `stream`
+// (cudaMallocFromPoolAsync; freed with cudaFreeAsync by sipf_destroy), so
+// that creating and destroying contexts never calls cudaMalloc or cudaFree.
+int create_in_pool(const sipf_grid* grid, int64_t N, const sipf_params* params,
+                   cudaStream_t stream, cudaMemPool_t pool, sipf_ctx** out);
 // smooth.cu
 cudaError_t launch_smooth(sipf_ctx* c, float* us, cudaStream_t s);
 void fill_smoothing(int H, double L, double sigma, float* host_out);

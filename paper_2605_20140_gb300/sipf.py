@@ -41,6 +41,7 @@ EXPORTED = (
     "sipf_ensemble_destroy", "sipf_context_bytes", "sipf_device_bytes", "sipf_server_create",
     "sipf_server_submit", "sipf_server_advance", "sipf_server_poll", "sipf_server_collect",
     "sipf_server_stats", "sipf_server_last_error", "sipf_server_destroy",
+    "sipf_server_set_limit", "sipf_server_fail_next_admission", "sipf_canonical_order",
 )
 PROFILE_GROUPS = 4
 
@@ -94,6 +95,7 @@ def load() -> ctypes.CDLL:
         "sipf_particles": ([P, P, P, P, I32], I32),
         "sipf_particle_state": ([P, P, P, P, I32], I32),
         "sipf_cell_start": ([P, P, I32], I32),
+        "sipf_canonical_order": ([P, P, P, I32], I32),
         "sipf_diagnostics": ([P, ctypes.POINTER(sipf_diag)], I32),
         "sipf_sync": ([P], I32),
         "sipf_destroy": ([P], None),
@@ -125,6 +127,8 @@ def load() -> ctypes.CDLL:
                                ctypes.POINTER(I32)], I32),
         "sipf_server_last_error": ([P], ctypes.c_char_p),
         "sipf_server_destroy": ([P], None),
+        "sipf_server_set_limit": ([P, I32], I32),
+        "sipf_server_fail_next_admission": ([P, I32], I32),
         "sipf_describe": ([P, ctypes.POINTER(sipf_grid), ctypes.POINTER(I64),
                            ctypes.POINTER(sipf_params), ctypes.POINTER(I64),
                            ctypes.POINTER(ctypes.c_double)], I32),
@@ -198,6 +202,10 @@ def sipf_particle_state(ctx, s=None, loga=None, id_=None, where=SIPF_HOST):
 
 def sipf_cell_start(ctx, dst, where=SIPF_HOST):
     _check(load().sipf_cell_start(ctx, _ptr(dst), where), ctx)
+
+
+def sipf_canonical_order(ctx, cell_start=None, ids=None, where=SIPF_HOST):
+    _check(load().sipf_canonical_order(ctx, _ptr(cell_start), _ptr(ids), where), ctx)
 
 
 def sipf_diagnostics(ctx) -> dict:
@@ -414,6 +422,13 @@ class Simulation:
         sipf_cell_start(self.ctx, cs, SIPF_HOST)
         return cs
 
+    def canonical_order(self):
+        """(cell_start, ids in (cell key, id) order) of the current particles."""
+        cs = np.empty(self.H ** 3 + 1, dtype=np.int32)
+        ids = np.empty(self.N, dtype=np.uint32)
+        sipf_canonical_order(self.ctx, cs, ids, SIPF_HOST)
+        return cs, ids
+
     def diagnostics(self) -> dict:
         return sipf_diagnostics(self.ctx)
 
@@ -465,11 +480,17 @@ def _check_srv(code: int, srv):
 class Server:
     """Continuous-batching request scheduler (host calls of one thread)."""
 
-    def __init__(self, budget_bytes: int):
+    def __init__(self, budget_bytes: int, max_live: int = 0):
         out = ctypes.c_void_p()
         _check(load().sipf_server_create(int(budget_bytes), ctypes.byref(out)))
         self.srv = out.value
         self.H = {}
+        if max_live:
+            _check_srv(load().sipf_server_set_limit(self.srv, int(max_live)), self.srv)
+
+    def fail_next_admission(self, code: int):
+        """Fault injection for tests: the next admission fails with `code`."""
+        _check_srv(load().sipf_server_fail_next_admission(self.srv, int(code)), self.srv)
 
     def submit(self, H, L, origin, N, params, x, mass, v, m, w, dt, steps) -> int:
         xs = np.ascontiguousarray(np.asarray(x, dtype=np.float32).T)

@@ -7,7 +7,9 @@ import os
 import numpy as np
 import pytest
 
+from oracle import sipf_oracle as O
 from paper_2605_20140_gb300 import sipf
+from parity_helpers import compare, oracle_state
 from sipf_inputs import ensemble_workloads
 
 torch = pytest.importorskip("torch")
@@ -69,3 +71,25 @@ def test_step_checks_every_member():
             ens.step([1e-3, 0.0], 1)
         ens.step([1e-3, 1e-3], 2)
         ens.sync()
+
+
+def test_member_with_drawn_parameters_matches_oracle():
+    """A member on a radix-3 grid (H = 48) with its own drawn chi, alpha, Du and
+    Philox key, advanced inside an uneven ensemble, against the FP64 oracle
+    run of the same member alone: fields, positions and log-masses within the
+    parity tolerances."""
+    runs = ensemble_workloads(8, seed=21, max_log2_N=15)
+    pick = [i for i, w in enumerate(runs) if w.H == 48]
+    assert pick, [w.H for w in runs]
+    i = pick[0]
+    steps = 40
+    with sipf.Ensemble([(w.H, w.L, w.origin, w.N, w.params) for w in runs]) as ens:
+        for sim, w in zip(ens.members, runs):
+            sim.set_state(w.x, w.mass, w.ids, w.v, w.m, w.w)
+        ens.step(np.array([w.dt for w in runs]), steps)
+        ens.sync()
+        w = runs[i]
+        st = O.run(oracle_state(w), w.dt, steps)
+        errs = compare(ens.members[i], st, w)
+    print(f"member {i} (H={w.H}, N={w.N}, chi={w.params.chi:.4f}, alpha={w.params.alpha:.2f}, "
+          f"Du={w.params.Du:.2e}) rel-L2:", {k: f"{v:.1e}" for k, v in errs.items()})

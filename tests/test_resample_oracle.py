@@ -95,3 +95,43 @@ def test_mass_is_conserved_and_storage_order_does_not_matter():
     np.testing.assert_array_equal(i1, np.arange(P))
     with pytest.raises(ValueError):
         R.resample_state(s, a, np.zeros(P, np.int64), n=1, seed=0)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_fixed_point_decisions_against_real_masses(seed):
+    """Ordinary (non-dyadic) float64 masses: Alg. 4 on the exact rational
+    masses gives k_p = floor(a_p / a_bar) with a_bar = sum(a) / P and the
+    residual r_p / a_bar = a_p / a_bar - k_p.  The oracle decides on 31-bit
+    fixed-point weights Q_p = floor(a_p 2^(31-E)), so x_p = a_p / a_bar is
+    replaced by Q_p P / S.  With s = 2^(31-E), Q_p = a_p s - d_p and
+    S = (sum a) s - D (0 <= d_p < 1, 0 <= D < P), which moves x_p by at most
+    eps_p = (1 + x_p) P / ((sum a) s - P) (first order, plus a 1% margin).  So
+    k_p may differ from the real-mass decision only where x_p lies within
+    eps_p of an integer, and the residual probabilities agree to eps_p / P."""
+    rng = np.random.default_rng(100 + seed)
+    P = 2000
+    a = rng.lognormal(0.0, 1.2, P) / P
+    a[rng.integers(0, P, 5)] *= 40.0                     # a few heavy particles
+    E, Q = R.fixed_point_weights(a)
+    S, k, Rr = R.split_counts(Q)
+    fa = [Fraction(float(v)) for v in a]                 # exact values of the float64 masses
+    A = sum(fa)
+    s = Fraction(2) ** (31 - E)
+    margin = Fraction(101, 100) * P / (A * s - P)
+    mismatches = 0
+    for p in range(P):
+        x = fa[p] * P / A                                # a_p / a_bar, exact
+        kp = math.floor(x)
+        eps = (1 + x) * margin
+        if k[p] != kp:
+            mismatches += 1
+            near = min(x - math.floor(x), math.ceil(x) - x)
+            assert near <= eps, (p, float(x), int(k[p]), kp)
+            assert abs(int(k[p]) - kp) == 1
+        else:
+            # residual probability r_p / sum(r) with sum(r) = P - sum(k) in units of a_bar
+            got = Fraction(int(Rr[p]), S)                # = Q_p P / S - k_p
+            assert abs(got - (x - kp)) <= eps, (p, float(got), float(x - kp))
+    # the bound is tight enough that decisions essentially never flip
+    assert mismatches <= 2
+    assert float(margin) < 1e-5

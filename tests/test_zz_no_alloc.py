@@ -53,6 +53,26 @@ def test_noalloc_deposit_matches_context_path_twice():
         assert abs(got.sum() * h3 - wl.mass.sum()) <= 1e-6 * wl.mass.sum()
 
 
+def test_noalloc_skips_non_finite_masses():
+    """An infinite or NaN mass contributes nothing (it must not set the scale
+    of every node): the result equals the context path's deposit of the same
+    particles with those masses set to zero (massless tracers)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    wl = workload("small", H=32, N=1 << 14, seed=5)
+    bad = wl.mass.copy()
+    bad[[3, 77]] = [np.inf, np.nan]
+    clean = wl.mass.copy()
+    clean[[3, 77]] = 0.0
+    wl.mass = clean
+    ref = _context_deposit(wl)
+    wl.mass = bad
+    got = _noalloc_deposit(wl)
+    assert np.isfinite(got).all()
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert rel <= 1e-6, rel
+
+
 def test_noalloc_rejects_grids_beyond_its_scratch():
     """H = 128 needs more nodes than the fixed scratch holds: refused up front."""
     if not torch.cuda.is_available():
