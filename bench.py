@@ -300,7 +300,13 @@ def run_sipf(args, rank, world, local):
     # reports the median region and the spread of all of them
     reps = []
     n_diag = 0
-    for _ in range(args.repeats):
+    for r in range(args.repeats):
+        if r:
+            # every region times the same trajectory: back to the initial
+            # state and the same warm-up (untimed), so the repeats differ
+            # only by measurement noise
+            sim.set_state(wl.x, wl.mass, wl.ids, wl.v, wl.m, wl.w)
+            sim.step(dt, args.warmup)
         _barrier(world)
         torch.cuda.synchronize()
         e0.record(stream)
@@ -472,21 +478,61 @@ def run_ensemble(args, rank, world, local):
     return 0
 
 
+def _serve_once(sipf, runs, steps, arrival, budget, quantum, max_live):
+    """One pass of the request stream through a server: time-to-result of
+    every request (collection time - arrival time), makespan, peak bytes.
+    max_live = 1 serves the requests one at a time (same server, same
+    pooled memory, same kernels), 0 lets the budget alone limit admission."""
+    R = len(runs)
+    mask = sipf.FIELD_U | sipf.FIELD_V | sipf.FIELD_M | sipf.FIELD_W
+    ttr, rid_of, results = {}, {}, {}
+    srv = sipf.Server(budget, max_live=max_live)
+    try:
+        t0 = time.perf_counter()
+        nxt = 0
+        while len(ttr) < R:
+            now = time.perf_counter() - t0
+            while nxt < R and arrival[nxt] <= now:
+                w = runs[nxt]
+                rid_of[srv.submit(w.H, w.L, w.origin, w.N, w.params, w.x, w.mass, w.v, w.m,
+                                  w.w, w.dt, steps[nxt])] = nxt
+                nxt += 1
+            pending = srv.advance(quantum)
+            for rid in srv.poll():
+                i = rid_of[rid]
+                results[i] = srv.collect(rid, mask)
+                ttr[i] = time.perf_counter() - t0 - arrival[i]
+            if pending == 0 and nxt < R:
+                time.sleep(max(0.0, arrival[nxt] - (time.perf_counter() - t0)))
+        makespan = time.perf_counter() - t0
+        st = srv.stats()
+    finally:
+        srv.close()
+    lat = np.array([ttr[i] for i in range(R)])
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "requests_per_s": R / makespan,
+            "makespan_s": makespan, "peak_device_bytes": st["peak"]}, results
+
+
 def run_serve(args, rank, world, local):
     """Continuous batching: requests drawn like the ensemble's runs plus a
     simulated time T ~ U[0.05, 0.5] (T/dt steps), arriving as a Poisson
     process of rate --rate per second, served from one GPU under a 150 GB
-    device-memory budget; time-to-result = collection time - arrival time."""
+    device-memory budget; time-to-result = collection time - arrival time.
+    The same request stream is then served one at a time (the server with
+    at most one admitted request), and the two arms' results are compared
+    bit for bit.  --rates a,b,c sweeps the arrival rate (one stream per rate)."""
     import torch
     from paper_2605_20140_gb300 import sipf
     from sipf_inputs import ensemble_workloads
 
     torch.cuda.set_device(local)
-    R, rate = args.requests, args.rate
+    R = args.requests
+    rates = [float(r) for r in args.rates.split(",")] if args.rates else [args.rate]
     rng = np.random.default_rng(np.random.PCG64(9000 + rank))
     runs = ensemble_workloads(R, seed=100 + rank)
     steps = [max(1, int(round(rng.uniform(0.05, 0.5) / w.dt))) for w in runs]
-    arrival = np.cumsum(rng.exponential(1.0 / rate, R))
+    gaps = rng.exponential(1.0, R)
     budget = 150 * 10 ** 9
     # warm-up: one request per grid size (graph capture, kernel attributes)
     with sipf.Server(budget) as warm:
@@ -499,55 +545,43 @@ def run_serve(args, rank, world, local):
             pass
         for rid in warm.poll():
             warm.collect(rid, 0)
-    mask = sipf.FIELD_U | sipf.FIELD_V | sipf.FIELD_M | sipf.FIELD_W
-    ttr, rid_of = {}, {}
     clocks = ClockSampler(local)
     _barrier(world)
     torch.cuda.synchronize()
     clocks.start()
-    srv = sipf.Server(budget)
-    try:
-        t0 = time.perf_counter()
-        nxt = 0
-        while len(ttr) < R:
-            now = time.perf_counter() - t0
-            while nxt < R and arrival[nxt] <= now:
-                w = runs[nxt]
-                rid_of[srv.submit(w.H, w.L, w.origin, w.N, w.params, w.x, w.mass, w.v, w.m,
-                                  w.w, w.dt, steps[nxt])] = nxt
-                nxt += 1
-            pending = srv.advance(args.quantum)
-            for rid in srv.poll():
-                srv.collect(rid, mask)
-                i = rid_of[rid]
-                ttr[i] = time.perf_counter() - t0 - arrival[i]
-            if pending == 0 and nxt < R:
-                time.sleep(max(0.0, arrival[nxt] - (time.perf_counter() - t0)))
-        makespan = time.perf_counter() - t0
-        st = srv.stats()
-    finally:
-        srv.close()
+    sweep = []
+    for rate in rates:
+        arrival = np.cumsum(gaps / rate)
+        served, res_a = _serve_once(sipf, runs, steps, arrival, budget, args.quantum, 0)
+        alone, res_b = _serve_once(sipf, runs, steps, arrival, budget, args.quantum, 1)
+        same = all(np.array_equal(res_a[i][k], res_b[i][k]) for i in range(R) for k in res_a[i])
+        sweep.append({"rate": rate, "served": served, "one_at_a_time": alone,
+                      "bit_identical": bool(same)})
     clk = clocks.stop()
-    lat = np.array([ttr[i] for i in range(R)])
-    p50, p99 = float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
-    p99 = _max_over_ranks(p99, world)
+    head = sweep[0]
+    p99 = _max_over_ranks(head["served"]["p99_s"], world)
     total_steps = sum(steps)
     h2d = sum(w.x.nbytes + w.mass.nbytes + 3 * w.v.nbytes for w in runs)
     d2h = sum(4 * w.v.nbytes for w in runs)
     if rank == 0:
         line = {
-            "metric": f"p99 time-to-result, Poisson arrivals at {rate:g} requests/s",
+            "metric": f"p99 time-to-result, Poisson arrivals at {head['rate']:g} requests/s",
             "value": p99, "unit": "s", "n_gpus": world, "steps": total_steps,
-            "warmup": len(seen), "ms_per_step": 1e3 * makespan / total_steps,
+            "warmup": len(seen),
+            "ms_per_step": 1e3 * head["served"]["makespan_s"] / total_steps,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 (f64 log-mass and reductions)", "data": "synthetic",
             "config": {"workload": f"serve: {R} requests drawn as the ensemble's runs "
                                    "(H in {32, 48, 64, 96}, N = 2^U[14, 20]) with "
                                    "T ~ U[0.05, 0.5], dt 1e-3; 150 GB budget",
                        "quantum_steps": args.quantum, "parallelism": f"replicas x{world}"},
-            "p50_s": p50, "p99_s": p99, "mean_s": float(lat.mean()),
-            "requests_per_s": R / makespan, "makespan_s": makespan,
-            "peak_device_bytes": st["peak"],
+            **{k: head["served"][k] for k in ("p50_s", "p99_s", "mean_s", "requests_per_s",
+                                               "makespan_s", "peak_device_bytes")},
+            "one_at_a_time": head["one_at_a_time"],
+            "speedup_runs_per_s": head["served"]["requests_per_s"] /
+                                  head["one_at_a_time"]["requests_per_s"],
+            "bit_identical_to_one_at_a_time": head["bit_identical"],
+            "sweep": sweep,
             "e2e": {"value": p99, "unit": "s", "h2d_bytes_per_step": h2d / total_steps,
                     "d2h_bytes_per_step": d2h / total_steps},
             "gpu_launches": 5 * total_steps, "clocks": clk,
@@ -561,6 +595,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--workload", choices=["headline", "ensemble", "serve"], default="headline")
     ap.add_argument("--rate", type=float, default=100.0, help="serve: arrivals per second")
+    ap.add_argument("--rates", default=None,
+                    help="serve: comma-separated arrival rates to sweep (overrides --rate)")
     ap.add_argument("--requests", type=int, default=128, help="serve: number of requests")
     ap.add_argument("--quantum", type=int, default=2, help="serve: steps per round")
     ap.add_argument("--steps", type=int, default=None)

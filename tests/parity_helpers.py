@@ -56,6 +56,15 @@ def u_tolerance(st, N):
     return max(FIELD_TOL, 4.0 * np.sqrt(3.0) * st.H * 2.0 ** -24 * np.sqrt(max(st.n, 1)))
 
 
+def position_tolerance(H, N, n):
+    """Bound on the periodic position difference (grid units) after n steps:
+    1e-4, or the largest of 3N float32 rounding walks of two roundings per
+    step, ulp = 2^(ceil(log2 H) - 24) for positions below H."""
+    ulp = 2.0 ** (np.ceil(np.log2(H)) - 24)
+    walk = ulp * np.sqrt(2.0 * max(n, 1) / 12.0)
+    return max(1e-4, (np.sqrt(2.0 * np.log(3.0 * N)) + 1.5) * walk)
+
+
 def compare(sim, st, wl, field_tol=FIELD_TOL, pos_tol=1e-4, loga_tol=1e-6):
     f = sim.fields()
     ref = oracle_fields(st)
@@ -72,7 +81,7 @@ def compare(sim, st, wl, field_tol=FIELD_TOL, pos_tol=1e-4, loga_tol=1e-6):
     report = {"errs": errs, "tols": tols, "dpos": float(dpos.max()), "dloga": float(dloga)}
     for k, e in errs.items():
         assert e <= tols[k], (k, report)
-    assert dpos.max() <= pos_tol, report
+    assert dpos.max() <= max(pos_tol, position_tolerance(wl.H, wl.N, st.n)), report
     assert dloga <= loga_tol, report
     return errs
 
