@@ -39,16 +39,91 @@ __device__ __forceinline__ float unit_open(uint32_t b) {
     return __fsub_rn(__uint_as_float(0x3F800000u | (b >> 9)), __uint_as_float(0x3F7FFFFFu));
 }
 
-// Box-Muller on the four words of one Philox block: three standard normals.
+// ------------------------------------------------------------------ short math
+// Box-Muller needs -2 ln u, a square root and cos/sin(2 pi u) of uniforms
+// u in (0, 1) with at most 24 significant bits, and the mass update needs
+// ln(1 + x) for |x| <= tau.  Their arguments lie in these known ranges, so
+// branch-free forms from textbook series suffice (the logarithm from the
+// atanh series, sine and cosine from their Taylor series on an eighth of a
+// turn); each is within a few float32 ulp, checked against the FP64
+// oracle's normals and masses.
+
+// float(e) for |e| < 2^22: the low mantissa bits of 1.5 2^23 + e.
+__device__ __forceinline__ float small_int_to_float(int e) {
+    return __fsub_rn(__int_as_float(0x4B400000 + e), 12582912.0f);
+}
+
+// -2 ln u for u in (0, 1): u = m 2^e with m in [sqrt(1/2), sqrt(2)) (the
+// exponent taken from the bits of u / sqrt(1/2)), ln m = 2 atanh(s) with
+// s = (m - 1)/(m + 1), |s| <= 0.1716, summed to s^9 (remainder < 3e-9
+// relative).
+__device__ __forceinline__ float neg2_log_unit(float u) {
+    const int e = static_cast<int>(__float_as_uint(u) - 0x3F3504F3u) >> 23;
+    const float m = __int_as_float(__float_as_int(u) - (e << 23));
+    const float f = __fsub_rn(m, 1.0f);
+    const float s = __fdividef(f, __fadd_rn(2.0f, f));
+    const float z = __fmul_rn(s, s);
+    // -2 ln m = s (-4 - z (4/3 + z (4/5 + z (4/7 + z 4/9))))
+    float p = __fmaf_rn(z, -4.0f / 9.0f, -4.0f / 7.0f);
+    p = __fmaf_rn(z, p, -4.0f / 5.0f);
+    p = __fmaf_rn(z, p, -4.0f / 3.0f);
+    p = __fmaf_rn(z, p, -4.0f);
+    return __fmaf_rn(small_int_to_float(e), -1.3862943611198906f, __fmul_rn(s, p));
+}
+
+// sqrt(x) for 0 < x < 2^126: x times the hardware reciprocal square root.
+__device__ __forceinline__ float sqrt_pos(float x) { return __fmul_rn(x, rsqrtf(x)); }
+
+// (cos 2 pi u, sin 2 pi u) for u in [0, 1): 8u = n + f with n = round(8u),
+// exact because u has at most 24 significant bits; phi = f pi/4 lies in
+// [-pi/8, pi/8], where the Taylor series to phi^7 (sine) and phi^6 (cosine)
+// leave remainders below 2e-8; then a rotation by n eighths of a turn.
+__device__ __forceinline__ float2 cis_2pi(float u) {
+    const float t = __fmul_rn(u, 8.0f);
+    const float r = __fadd_rn(t, 12582912.0f);          // 1.5 2^23 + round(t)
+    const int n = __float_as_int(r) - 0x4B400000;
+    const float phi = __fmul_rn(__fsub_rn(t, __fsub_rn(r, 12582912.0f)), 0.78539816339744831f);
+    const float p = __fmul_rn(phi, phi);
+    const float qs = __fmaf_rn(p, __fmaf_rn(p, -1.0f / 5040.0f, 1.0f / 120.0f), -1.0f / 6.0f);
+    const float sn = __fmaf_rn(__fmul_rn(phi, p), qs, phi);
+    const float qc = __fmaf_rn(p, __fmaf_rn(p, -1.0f / 720.0f, 1.0f / 24.0f), -0.5f);
+    const float cs = __fmaf_rn(p, qc, 1.0f);
+    // odd n: rotate by pi/4 first
+    const bool odd = n & 1;
+    const float ca = odd ? __fmul_rn(__fsub_rn(cs, sn), 0.70710678118654752f) : cs;
+    const float sa = odd ? __fmul_rn(__fadd_rn(cs, sn), 0.70710678118654752f) : sn;
+    // quarter turns q: (c, s) -> (c, s), (-s, c), (-c, -s), (s, -c)
+    const int q = (n >> 1) & 3;
+    const float c2 = (q & 1) ? sa : ca;
+    const float s2 = (q & 1) ? ca : sa;
+    return make_float2(((q + 1) & 2) ? -c2 : c2, (q & 2) ? -s2 : s2);
+}
+
+// Box-Muller on the four words of one Philox block: three standard normals,
+// z0, z1 from (u0, u1) and z2 from (u2, u3).
 __device__ __forceinline__ float3 box_muller(const uint4 b) {
-    const float u0 = unit_open(b.x), u1 = unit_open(b.y);
-    const float u2 = unit_open(b.z), u3 = unit_open(b.w);
-    const float r01 = sqrtf(-2.0f * logf(u0));
-    const float r23 = sqrtf(-2.0f * logf(u2));
-    float s1, c1;
-    sincospif(2.0f * u1, &s1, &c1);
-    const float c3 = cospif(2.0f * u3);
-    return make_float3(r01 * c1, r01 * s1, r23 * c3);
+    const float r01 = sqrt_pos(neg2_log_unit(unit_open(b.x)));
+    const float r23 = sqrt_pos(neg2_log_unit(unit_open(b.z)));
+    const float2 e1 = cis_2pi(unit_open(b.y));
+    const float2 e3 = cis_2pi(unit_open(b.w));
+    return make_float3(__fmul_rn(r01, e1.x), __fmul_rn(r01, e1.y), __fmul_rn(r23, e3.x));
+}
+
+// 2^x (hardware approximation, relative error about 2^-22).
+__device__ __forceinline__ float exp2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ln(1 + x) for |x| <= 1/16: 2 atanh(s), s = x/(2 + x), |s| <= 0.0323,
+// summed to s^7 (remainder below 1e-12 relative).
+__device__ __forceinline__ float log1p_small(float x) {
+    const float s = __fdividef(x, __fadd_rn(2.0f, x));
+    const float z = __fmul_rn(s, s);
+    return __fmul_rn(s, __fmaf_rn(z, __fmaf_rn(z, __fmaf_rn(z, 2.0f / 7.0f, 2.0f / 5.0f),
+                                                2.0f / 3.0f),
+                                  2.0f));
 }
 
 // Three standard normals of particle `id` in step n: Box-Muller on the four
@@ -232,6 +307,39 @@ __device__ __forceinline__ int round_signed_small(float v) {
     return __float_as_int(__fadd_rn(v, 12582912.0f)) - 0x4B400000;
 }
 
+// Wrap of a pushed position, all three axes at once: positions normally stay
+// in [0, H), so the full periodic reduction runs only when one leaves it.
+__device__ __forceinline__ void wrap3(float& x, float& y, float& z, float Hf, int* bad) {
+    if (!(x >= 0.0f && x < Hf && y >= 0.0f && y < Hf && z >= 0.0f && z < Hf)) {
+        x = wrap(x, Hf, bad);
+        y = wrap(y, Hf, bad);
+        z = wrap(z, Hf, bad);
+    }
+}
+
+// Tile of a position in [0, H) (the cell split without the fraction).
+__device__ __forceinline__ int tile_at(float x, float y, float z, int T) {
+    const int cx = static_cast<int>(__float_as_uint(__fadd_rz(x, 8388608.0f)) - 0x4B000000u);
+    const int cy = static_cast<int>(__float_as_uint(__fadd_rz(y, 8388608.0f)) - 0x4B000000u);
+    const int cz = static_cast<int>(__float_as_uint(__fadd_rz(z, 8388608.0f)) - 0x4B000000u);
+    return ((cz >> 3) * T + (cy >> 3)) * T + (cx >> 3);
+}
+
+// Mask of the lanes below this one.
+__device__ __forceinline__ unsigned lanes_below() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// A slot in the overflow region, or -1 (with the status bit) when it is full.
+__device__ __forceinline__ int overflow_slot(const Layout& L, int* status) {
+    const int o = atomicAdd(L.ovf, 1);
+    if (o < L.ovf_cap) return L.ovf_base + o;
+    atomicOr(status, kStatusSlot);
+    return -1;
+}
+
 template <int ORDER>
 __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
     k_step(PushArgs a, const StepScalars* __restrict__ sc, const float4* __restrict__ G, Buf src,
@@ -239,15 +347,25 @@ __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
            unsigned long long* __restrict__ acc, int do_deposit, int do_move,
            int* __restrict__ status) {
     using DB = DepBlock<ORDER>;
-    __shared__ int dep[DB::N];              // node sums of the item (exact: |sum| < 2^31)
+    // Item sums in 32 bits: the trilinear contributions are non-negative and
+    // below 2^19.5 (the deposit scale's bound), so kFlushItems items (4096
+    // particles) sum below 2^32 unsigned; R^(4)'s signed sums are moved to
+    // the 64-bit tile sums after every item.
+    constexpr int kFlushItems = ORDER == 2 ? 4 : 1;
+    __shared__ int dep[DB::N];              // node sums of the items since the last flush
     __shared__ long long dep64[DB::N];      // node sums of the tile's items so far
     __shared__ float4 gblk[kBlock];         // (dv/dx, dv/dy, dv/dz, w) on the tile's 9^3 nodes
+    __shared__ int tslot[2];                // capacity and first slot of the item tile's bucket
     const int H = a.H, T = H >> 3;
-    const int lane = threadIdx.x & 31;
     const float Hf = __int2float_rn(H);
     const int total = *n_items;
     const uint32_t step_n = sc->n;                 // Philox counter word 0 of this step
     const float dscale = sc->deposit_scale;        // 2^S of the fixed-point deposit
+    const float dshift = static_cast<float>(sc->deposit_shift);
+    // a contribution's mass in deposit units, a 2^S = 2^(dl log2 e + S), is
+    // below 2^19.5 by the choice of S; the clamp keeps a corrupt log-mass
+    // (NaN) inside the bound the item sums rely on
+    constexpr float kMaxLog2Unit = 19.49f;
     for (int i = threadIdx.x; i < DB::N; i += kNT) {
         dep[i] = 0;
         dep64[i] = 0;
@@ -258,10 +376,27 @@ __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
     const int i_lo = static_cast<int>(static_cast<long long>(blockIdx.x) * total / gridDim.x);
     const int i_hi = static_cast<int>(static_cast<long long>(blockIdx.x + 1) * total / gridDim.x);
     int cur = -1, cx0 = 0, cy0 = 0, cz0 = 0;   // tile held in dep64 / gblk, its first cell
+    int pending = 0;                           // items summed in dep since its last flush
     for (int item_idx = i_lo; item_idx <= i_hi; ++item_idx) {
         const Item it = item_idx < i_hi ? items[item_idx] : Item{-1, 0, 0, 0, 0, 0, 0, 0};
         const int tile = it.tile;
-        if (tile != cur || tile < 0) {
+        const bool change = tile != cur || tile < 0;
+        // every thread moves its own nodes (j = threadIdx.x + k kNT) from dep
+        // to dep64 and from dep64 to the grid, so no barrier is needed between
+        // the two; the barrier that ended the last item ordered them after
+        // its atomics
+        if (do_deposit && pending > 0 && (change || pending == kFlushItems)) {
+            for (int j = threadIdx.x; j < DB::N; j += kNT) {
+                const int v = dep[j];
+                if (v) {
+                    dep64[j] += ORDER == 2 ? static_cast<long long>(static_cast<unsigned>(v))
+                                           : static_cast<long long>(v);
+                    dep[j] = 0;
+                }
+            }
+            pending = 0;
+        }
+        if (change) {
             if (cur >= 0 && do_deposit) {
                 // flush the finished tile's node block into the grid accumulator
                 // (two's complement sums)
@@ -294,6 +429,13 @@ __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
             }
         }
         const int tx0 = cx0, ty0 = cy0, tz0 = cz0;
+        // the destination bucket of the particles that stay in this tile (the
+        // common case: a step moves a particle by a fraction of a cell)
+        const bool binned = tile >= 0;
+        if (do_move && binned && threadIdx.x == 0) {
+            tslot[0] = __ldg(L.cap + tile);
+            tslot[1] = __ldg(L.bstart + tile);
+        }
         __syncthreads();
         int bad = 0;
         for (int j = 0; j < kPT; ++j) {
@@ -313,18 +455,17 @@ __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
                 pid = __ldcs(src.id + i);
             }
             const Cell c = locate(px, py, pz, H);
+            const int lx = c.cx - tx0, ly = c.cy - ty0, lz = c.cz - tz0;
+            const bool in_tile = binned && ((lx | ly | lz) & ~7) == 0;
+            if (binned && valid && !in_tile) bad |= 2;   // bucket does not match position
 
             if (do_deposit && valid) {
                 // a_p R_h(X_p, node) h^3 in units of exp(logref) 2^-S as integers
-                // (below 2^20 in magnitude by the choice of S; the clamp keeps a
-                // non-finite mass inside the rounding's range)
-                const float ea = fminf(__fmul_rn(expf(d2f_bits(pl)), dscale), 2097152.0f);
                 const float wx0 = __fsub_rn(1.0f, c.fx), wy0 = __fsub_rn(1.0f, c.fy);
                 const float wz0 = __fsub_rn(1.0f, c.fz);
-                const int lx = c.cx - tx0, ly = c.cy - ty0, lz = c.cz - tz0;
-                const bool in_tile = tile >= 0 && ((lx | ly | lz) & ~7) == 0;
-                if (tile >= 0 && !in_tile) bad |= 2;   // bucket does not match position
                 if constexpr (ORDER == 2) {
+                    const float ea = exp2_approx(
+                        fminf(__fmaf_rn(d2f_bits(pl), 1.4426950408889634f, dshift), kMaxLog2Unit));
                     const float e0 = __fmul_rn(ea, wz0), e1 = __fmul_rn(ea, c.fz);
                     const float xy[4] = {__fmul_rn(wx0, wy0), __fmul_rn(c.fx, wy0),
                                          __fmul_rn(wx0, c.fy), __fmul_rn(c.fx, c.fy)};
@@ -336,14 +477,11 @@ __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
                     }
                     if (in_tile) {
                         // particles of a bucket are in random cells of the tile, so lanes
-                        // rarely collide: one shared 32-bit atomic per corner (an item has
-                        // at most kItem particles and each value is < 2^21, so sums are exact)
-                        const int nbase = DB::idx(lx, ly, lz);
+                        // rarely collide: one shared 32-bit atomic per corner
+                        unsigned* depu = reinterpret_cast<unsigned*>(dep) + DB::idx(lx, ly, lz);
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            const int node = nbase + (k & 1) + ((k >> 1) & 1) * 9 + (k >> 2) * 81;
-                            if (q[k]) atomicAdd(dep + node, static_cast<int>(q[k]));
-                        }
+                        for (int k = 0; k < 8; ++k)
+                            atomicAdd(depu + (k & 1) + ((k >> 1) & 1) * 9 + (k >> 2) * 81, q[k]);
                     } else {
                         const int x1 = c.cx + 1 < H ? c.cx + 1 : 0;
                         const int y1 = c.cy + 1 < H ? c.cy + 1 : 0;
@@ -362,6 +500,7 @@ __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
                     // g = 1 + sum_j f_j (1 - f_j) / 2; along axis j the nodes c_j - 1 and
                     // c_j + 2 carry -f (1 - f)(2 - f) / 6 and -f (1 - f)(1 + f) / 6 times
                     // the bilinear weight of the other two axes (cases of R_h^(4))
+                    const float ea = fminf(__fmul_rn(expf(d2f_bits(pl)), dscale), 741455.0f);
                     const float fx = c.fx, fy = c.fy, fz = c.fz;
                     const float bx = __fmul_rn(fx, wx0), by = __fmul_rn(fy, wy0), bz = __fmul_rn(fz, wz0);
                     const float g = __fadd_rn(1.0f, __fmul_rn(0.5f, __fadd_rn(__fadd_rn(bx, by), bz)));
@@ -403,66 +542,66 @@ __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
 
             if (do_move) {
                 if (a.push && valid) {
-                    const int lx = c.cx - tx0, ly = c.cy - ty0, lz = c.cz - tz0;
-                    const bool in_tile = tile >= 0 && ((lx | ly | lz) & ~7) == 0;
                     const float4 g = in_tile ? gather4_block(gblk, c, (lz * 9 + ly) * 9 + lx)
                                              : gather4(G, c, H);
                     // mass factor 1 + tau (rho(w_H) - 1), rho(w) = 2w/(1+w) (Eq. u_hat_update)
-                    const float rho = __fdiv_rn(2.0f * g.w, __fadd_rn(1.0f, g.w));
-                    const float inc = log1pf(__fmul_rn(a.tau, __fsub_rn(rho, 1.0f)));
+                    const float rho = __fdividef(__fmul_rn(2.0f, g.w), __fadd_rn(1.0f, g.w));
+                    const float x = __fmul_rn(a.tau, __fsub_rn(rho, 1.0f));
+                    const float inc = a.tau <= 0.0625f ? log1p_small(x) : log1pf(x);
                     pl = pl + f2d_bits(inc);
                     // Euler-Maruyama push in grid units
                     const float3 nz = box_muller(philox4x32_10(make_uint4(step_n, 0u, pid, 0u), a.rk));
-                    px = wrap(__fmaf_rn(a.noise, nz.x, __fmaf_rn(a.drift, g.x, px)), Hf, &bad);
-                    py = wrap(__fmaf_rn(a.noise, nz.y, __fmaf_rn(a.drift, g.y, py)), Hf, &bad);
-                    pz = wrap(__fmaf_rn(a.noise, nz.z, __fmaf_rn(a.drift, g.z, pz)), Hf, &bad);
+                    px = __fmaf_rn(a.noise, nz.x, __fmaf_rn(a.drift, g.x, px));
+                    py = __fmaf_rn(a.noise, nz.y, __fmaf_rn(a.drift, g.y, py));
+                    pz = __fmaf_rn(a.noise, nz.z, __fmaf_rn(a.drift, g.z, pz));
+                    wrap3(px, py, pz, Hf, &bad);
                 }
-                const Cell cn = locate(px, py, pz, H);
-                const int nt = valid ? (((cn.cz >> 3) * T + (cn.cy >> 3)) * T + (cn.cx >> 3)) : -1;
-                // slots in the destination bucket: one atomic per warp and tile (the
-                // lanes bound for the same tile take consecutive slots), then the
-                // particle is written straight from registers; a full bucket sends
-                // it to the overflow region
-                const unsigned peers = __match_any_sync(kFull, nt);
-                const int leader = __ffs(peers) - 1;
-                int base = 0;
-                if (nt >= 0 && lane == leader) base = atomicAdd(L.cnt + nt, __popc(peers));
-                base = __shfl_sync(kFull, base, leader);
-                if (nt >= 0) {
-                    const int slot = base + __popc(peers & ((1u << lane) - 1u));
-                    int dest = -1;
-                    if (slot < __ldg(L.cap + nt)) {
-                        dest = __ldg(L.bstart + nt) + slot;
-                    } else {
-                        const int o = atomicAdd(L.ovf, 1);
-                        if (o < L.ovf_cap)
-                            dest = L.ovf_base + o;
-                        else
-                            atomicOr(status, kStatusSlot);
+                const int nt = valid ? tile_at(px, py, pz, T) : -1;
+                int dest = -1;
+                if (binned) {
+                    // the lanes that stay in the item's tile take consecutive slots
+                    // reserved by one atomic; the few that leave it reserve their own
+                    const bool stay = nt == tile;
+                    const unsigned sm = __ballot_sync(kFull, stay);
+                    int base = 0;
+                    if (sm) {
+                        // the lowest staying lane reserves for all of them
+                        if (stay && !(sm & lanes_below())) base = atomicAdd(L.cnt + tile, __popc(sm));
+                        base = __shfl_sync(kFull, base, __ffs(sm) - 1);
                     }
-                    if (dest >= 0) {
-                        __stcs(dst.sx + dest, px);
-                        __stcs(dst.sy + dest, py);
-                        __stcs(dst.sz + dest, pz);
-                        __stcs(dst.dl + dest, pl);
-                        __stcs(dst.id + dest, pid);
+                    if (stay) {
+                        const int slot = base + __popc(sm & lanes_below());
+                        dest = slot < tslot[0] ? tslot[1] + slot : overflow_slot(L, status);
+                    } else if (nt >= 0) {
+                        const int slot = atomicAdd(L.cnt + nt, 1);
+                        dest = slot < __ldg(L.cap + nt) ? __ldg(L.bstart + nt) + slot
+                                                        : overflow_slot(L, status);
                     }
+                } else {
+                    // unbinned input or the overflow region: particles of one warp go to
+                    // many tiles; the lanes bound for one tile share one atomic
+                    const unsigned peers = __match_any_sync(kFull, nt);
+                    int base = 0;
+                    if (nt >= 0 && !(peers & lanes_below())) base = atomicAdd(L.cnt + nt, __popc(peers));
+                    base = __shfl_sync(kFull, base, __ffs(peers) - 1);
+                    if (nt >= 0) {
+                        const int slot = base + __popc(peers & lanes_below());
+                        dest = slot < __ldg(L.cap + nt) ? __ldg(L.bstart + nt) + slot
+                                                        : overflow_slot(L, status);
+                    }
+                }
+                if (dest >= 0) {
+                    __stcs(dst.sx + dest, px);
+                    __stcs(dst.sy + dest, py);
+                    __stcs(dst.sz + dest, pz);
+                    __stcs(dst.dl + dest, pl);
+                    __stcs(dst.id + dest, pid);
                 }
             }
         }
         if (bad & 1) atomicOr(status, kStatusNonfinite);
         if (bad & 2) atomicOr(status, kStatusSlot);
-        __syncthreads();
-        if (do_deposit && tile >= 0) {
-            // the item's exact 32-bit sums into the tile's 64-bit sums
-            for (int j = threadIdx.x; j < DB::N; j += kNT) {
-                const int v = dep[j];
-                if (v) {
-                    dep64[j] += v;
-                    dep[j] = 0;
-                }
-            }
-        }
+        if (do_deposit && binned) ++pending;
         __syncthreads();
     }
 }

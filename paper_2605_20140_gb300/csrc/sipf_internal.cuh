@@ -72,7 +72,7 @@ struct PushArgs {
 // captured sequence of steps can be replayed.
 struct StepScalars {
     uint32_t n;            // the step being taken (Philox counter word 0), from 1
-    uint32_t pad;
+    int32_t deposit_shift; // S of deposit_scale = 2^S
     double time;           // t_{n-1}
     float deposit_scale;   // 2^S: contribution of a particle to a node is
                            // exp(log a - logref) * weight * 2^S, rounded to an integer
@@ -97,7 +97,7 @@ __host__ __device__ inline void fill_step_scalars(StepScalars* s, uint32_t n, do
                                                   double h3) {
     const int S = deposit_shift_at(log2_maxrel, t);
     s->n = n;
-    s->pad = 0;
+    s->deposit_shift = S;
     s->time = t;
     s->deposit_scale = static_cast<float>(ldexp(1.0, S));
     s->u_scale = static_cast<float>(ldexp(exp_logref, -S) / h3);
