@@ -92,17 +92,19 @@ __device__ __forceinline__ float acc_to_float(unsigned long long q) {
 
 // R_tau at one node: (m*, w*) and v^n.
 // um is the u of the m source: u itself, or K_sigma * u (Eq. m_reg).
+// The quotients use the hardware reciprocal (within 2 ulp): the
+// denominators are at least 1.
 __device__ __forceinline__ void react(const SpectralArgs& a, float vv, float mm, float ww, float u,
                                       float um, float& ms, float& ws, float& vn) {
     ms = mm;
     ws = ww;
     if (a.do_mw) {
         // explicit Euler of S = (-alpha m v; u; gamma v - eta(u) w), eta(u) = 2u/(1+u)
-        const float eta = 2.0f * u / (1.0f + u);
+        const float eta = __fdividef(2.0f * u, 1.0f + u);
         ms = mm + a.tau * um;
         ws = ww + a.tau * (a.gamma * vv - eta * ww);
     }
-    vn = (a.v_update == SIPF_V_IMPLICIT) ? vv / (1.0f + a.alpha * a.tau * mm)
+    vn = (a.v_update == SIPF_V_IMPLICIT) ? __fdividef(vv, 1.0f + a.alpha * a.tau * mm)
                                          : vv * (1.0f - a.alpha * a.tau * mm);
 }
 
@@ -276,7 +278,8 @@ __global__ void __launch_bounds__(Cfg<H>::NT2)
                 val = make_float2(-kz_phys * val.y, kz_phys * val.x);
             } else if (field < 2) {
                 const float c = field == 0 ? a.m_c : a.w_c;
-                f = a.diffusion == SIPF_DIFFUSION_IMPLICIT ? 1.0f / (1.0f + c * q2) : expf(-c * q2);
+                f = a.diffusion == SIPF_DIFFUSION_IMPLICIT ? __fdividef(1.0f, 1.0f + c * q2)
+                                                           : expf(-c * q2);
             }
             if (a.filter) f *= expf(-a.inv_H0sq_2pi2 * q2);
             val = make_float2(f * val.x, f * val.y);
