@@ -416,8 +416,12 @@ def run_sipf(args, rank, world, local):
 
 def run_ensemble(args, rank, world, local):
     """64 uneven independent runs (H in {32, 48, 64, 96}, N = 2^U[14, 20],
-    chi, alpha, Du drawn per run, one Philox key each) advanced together, one
-    stream per run, against the same runs stepped one at a time."""
+    chi, alpha, Du drawn per run, one Philox key each) advanced together:
+    batched (one particle-step launch over all runs' work list, one launch per
+    spectral pass and grid size, replayed as a CUDA graph), against the same
+    runs one stream each, and one at a time.  Every arm starts from the same
+    initial states; the batched and per-stream members must end bit for bit
+    equal."""
     import torch
     from paper_2605_20140_gb300 import sipf
     from sipf_inputs import ensemble_workloads
@@ -426,52 +430,81 @@ def run_ensemble(args, rank, world, local):
     count, K, W = 64, args.steps, args.warmup
     runs = ensemble_workloads(count, seed=rank)
     dts = np.array([w.dt for w in runs])
-    ens = sipf.Ensemble([(w.H, w.L, w.origin, w.N, w.params) for w in runs])
+    specs = [(w.H, w.L, w.origin, w.N, w.params) for w in runs]
+
+    def timed(mode):
+        ens = sipf.Ensemble(specs, mode=mode)
+        try:
+            for sim, w in zip(ens.members, runs):
+                sim.set_state(w.x, w.mass, w.ids, w.v, w.m, w.w)
+            ens.step(dts, W)
+            ens.sync()
+            for sim, w in zip(ens.members, runs):
+                sim.set_state(w.x, w.mass, w.ids, w.v, w.m, w.w)
+            _barrier(world)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ens.step(dts, K)
+            ens.sync()
+            el = time.perf_counter() - t0
+            path = ens.last_path()
+            fields = [sim.fields(sipf.FIELD_U | sipf.FIELD_M) for sim in ens.members[:8]]
+        finally:
+            ens.close()
+        return el, path, fields
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_batched, path_b, f_b = timed(sipf.SIPF_ENSEMBLE_BATCHED)
+    t_streams, path_s, f_s = timed(sipf.SIPF_ENSEMBLE_STREAMS)
+    # one at a time: the same runs, each alone on one stream (its own graphs)
+    stream = torch.cuda.Stream()
+    sims = [sipf.Simulation(*spec, stream=stream.cuda_stream) for spec in specs]
     try:
-        for sim, w in zip(ens.members, runs):
+        for sim, w in zip(sims, runs):
             sim.set_state(w.x, w.mass, w.ids, w.v, w.m, w.w)
-        ens.step(dts, W)
-        ens.sync()
-        clocks = ClockSampler(local)
-        _barrier(world)
+            sim.step(w.dt, W)
+            sim.set_state(w.x, w.mass, w.ids, w.v, w.m, w.w)
         torch.cuda.synchronize()
-        clocks.start()
         t0 = time.perf_counter()
-        ens.step(dts, K)
-        ens.sync()
-        t_together = time.perf_counter() - t0
-        clk = clocks.stop()
-        t0 = time.perf_counter()
-        for sim, dt in zip(ens.members, dts):
+        for sim, dt in zip(sims, dts):
             sim.step(dt, K)
             sipf.sipf_sync(sim.ctx)
         t_alone = time.perf_counter() - t0
-        _barrier(world)
-        t_together = _max_over_ranks(t_together, world)
-        t_alone = _max_over_ranks(t_alone, world)
     finally:
-        ens.close()
+        for sim in sims:
+            sim.close()
+    clk = clocks.stop()
+    _barrier(world)
+    t_batched = _max_over_ranks(t_batched, world)
+    t_streams = _max_over_ranks(t_streams, world)
+    t_alone = _max_over_ranks(t_alone, world)
+    same = all(np.array_equal(a[k], b[k]) for a, b in zip(f_b, f_s) for k in a)
     member_steps = count * K * world
     particle_steps = sum(w.N for w in runs) * K * world
     if rank == 0:
         line = {
             "metric": f"runs/s, {count} uneven runs of {K} steps (H in 32..96, N in 2^14..2^20)",
-            "value": count * world / t_together,
+            "value": count * world / t_batched,
             "unit": "runs/s",
             "n_gpus": world, "steps": K, "warmup": W,
-            "ms_per_step": 1e3 * t_together / K,
+            "ms_per_step": 1e3 * t_batched / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 (f64 log-mass and reductions)", "data": "synthetic",
             "config": {"workload": f"ensemble: {count} runs, H in {{32, 48, 64, 96}}, "
                                    "N = 2^U[14, 20], chi ~ U[0.005, 0.03], alpha ~ U[5, 20], "
                                    "Du ~ U[5e-4, 2e-3], dt 1e-3",
-                       "parallelism": f"one stream per run, replicas x{world}",
-                       "timing": "host wall clock around enqueue + sync of all runs"},
+                       "parallelism": f"batched launches across runs, replicas x{world}",
+                       "timing": "host wall clock around enqueue + sync of all runs",
+                       "path": "batched" if path_b == sipf.SIPF_ENSEMBLE_BATCHED else "streams"},
+            "one_stream_per_run": {"value": count * world / t_streams, "unit": "runs/s",
+                                   "speedup_of_batched": t_streams / t_batched},
             "one_at_a_time": {"value": count * world / t_alone, "unit": "runs/s",
-                              "speedup": t_alone / t_together},
-            "member_steps_per_s": member_steps / t_together,
-            "particle_steps_per_s": particle_steps / t_together,
-            "gpu_launches": 5 * member_steps,
+                              "speedup_of_batched": t_alone / t_batched},
+            "bit_identical_batched_vs_streams": bool(same),
+            "member_steps_per_s": member_steps / t_batched,
+            "particle_steps_per_s": particle_steps / t_batched,
+            "gpu_launches": (1 + 1 + 3 * len({w.H for w in runs})) * K,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

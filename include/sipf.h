@@ -229,12 +229,31 @@ int sipf_resample(sipf_ctx* ctx, double ratio, int32_t* resampled);
  * sipf_ensemble_step: k steps of every member, dt[i] for member i (host
  * array of count doubles); enqueues only.  Errors: SIPF_EINVAL (a member
  * without state, a dt outside (0, 0.5]).
+ * Batched steps (mode SIPF_ENSEMBLE_BATCHED, the default): when every member
+ * uses the trilinear assignment without the filter or the K_sigma source, has
+ * H <= 128, and all members are at the same buffer parity (true for members
+ * whose states were set and that were stepped together; at most 256 members),
+ * a step of the whole ensemble is one persistent particle-step launch over
+ * the concatenated (run, tile-item) work list of all members, one launch
+ * planning every member's next step, and each of the three spectral passes
+ * once per grid size (the members of one size batched, 64 per launch); pairs
+ * of steps are captured once per (dt vector, parity) as a CUDA graph (at most
+ * four kept) and replayed.  Otherwise, or in mode SIPF_ENSEMBLE_STREAMS, each
+ * member advances on its own stream with its own two-step graph.  Either way
+ * each member ends bit for bit where the same run alone ends.
+ * sipf_ensemble_set_mode selects the mode (SIPF_EINVAL for anything else);
+ * sipf_ensemble_last_path returns the mode the last sipf_ensemble_step used
+ * (-1 before the first).
  * sipf_ensemble_sync: waits for all members; returns the first deferred
  * device error.  sipf_ensemble_last_error: message of the last failed call
  * ("" if none).  sipf_ensemble_destroy frees everything (NULL: no-op). */
 typedef struct sipf_ensemble sipf_ensemble;
+#define SIPF_ENSEMBLE_BATCHED 0
+#define SIPF_ENSEMBLE_STREAMS 1
 int sipf_ensemble_create(int32_t count, const sipf_grid* grids, const int64_t* N,
                          const sipf_params* params, sipf_ensemble** out);
+int sipf_ensemble_set_mode(sipf_ensemble* ens, int mode);
+int sipf_ensemble_last_path(const sipf_ensemble* ens);
 sipf_ctx* sipf_ensemble_member(sipf_ensemble* ens, int32_t i);
 int sipf_ensemble_step(sipf_ensemble* ens, const double* dt, int64_t k);
 int sipf_ensemble_sync(sipf_ensemble* ens);

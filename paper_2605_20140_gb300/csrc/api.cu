@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <new>
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -1067,17 +1068,216 @@ int sipf_describe(const sipf_ctx* c, sipf_grid* grid, int64_t* N, sipf_params* p
 struct sipf_ensemble {
     std::vector<sipf_ctx*> members;
     std::vector<cudaStream_t> streams;   // one per member, owned here
+    int mode = SIPF_ENSEMBLE_BATCHED;
+    int last_path = -1;
+    // batched steps: the ensemble's own streams and events, and the captured
+    // two-step graphs, each with the run table its kernels read
+    cudaStream_t main = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_done = nullptr;
+    std::vector<cudaEvent_t> ev_member;
+    struct BatchGraph {
+        std::vector<double> dt;
+        int parity;
+        cudaGraphExec_t exec;
+        sipf::RunDesc* d_runs;
+    };
+    std::vector<BatchGraph> graphs;
     std::string last_error;
 };
 
 namespace {
 void ensemble_free(sipf_ensemble* e) {
+    if (e->main) cudaStreamSynchronize(e->main);
+    if (e->side) cudaStreamSynchronize(e->side);
+    for (auto& g : e->graphs) {
+        cudaGraphExecDestroy(g.exec);
+        cudaFree(g.d_runs);
+    }
     for (sipf_ctx* c : e->members)
         if (c) sipf_destroy(c);
     for (cudaStream_t s : e->streams)
         if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t ev : e->ev_member) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : {e->ev_fork, e->ev_join, e->ev_done})
+        if (ev) cudaEventDestroy(ev);
+    if (e->main) cudaStreamDestroy(e->main);
+    if (e->side) cudaStreamDestroy(e->side);
     delete e;
 }
+}  // namespace
+
+extern "C" {
+
+}  // extern "C"
+
+namespace {
+
+// The batched step applies when every member uses the trilinear assignment
+// without the filter or the K_sigma source, has a fused-pass grid (H <= 128),
+// a stream of its own and no tracing, and all members read the same buffer
+// parity.
+bool batchable(const sipf_ensemble* e) {
+    if (e->members.empty() || e->members.size() > static_cast<size_t>(kMaxRuns)) return false;
+    const int parity = e->members[0]->cur;
+    for (const sipf_ctx* c : e->members) {
+        const bool filter = c->p.H0 > 0.0 && c->p.H0 < c->H;
+        if (c->p.p2g_order != 2 || filter || c->us || c->H > 128 || !c->stream || c->prof_on ||
+            c->cur != parity)
+            return false;
+    }
+    return true;
+}
+
+// One batched step of every member from buffer `parity`: the particle step
+// of all runs in one persistent launch, the plans of all runs in one launch
+// on the second stream, and each fused spectral pass once per grid size
+// (runs of one size batched into one launch).
+int enqueue_batched_step(sipf_ensemble* e, const double* dt, const RunDesc* d_runs, int parity) {
+    const int n = static_cast<int>(e->members.size());
+    auto cuda = [e](cudaError_t err, const char* where) {
+        if (err == cudaSuccess) return SIPF_OK;
+        cudaGetLastError();
+        e->last_error = std::string(where) + ": " + cudaGetErrorString(err);
+        return SIPF_ECUDA;
+    };
+    int r = cuda(launch_step_multi(d_runs, n, parity, e->main), "batched particle step");
+    if (r == SIPF_OK) r = cuda(cudaEventRecord(e->ev_fork, e->main), "cudaEventRecord");
+    if (r == SIPF_OK) r = cuda(cudaStreamWaitEvent(e->side, e->ev_fork, 0), "cudaStreamWaitEvent");
+    if (r == SIPF_OK) r = cuda(launch_plan_multi(d_runs, n, parity, e->side), "batched plan");
+    if (r == SIPF_OK) r = cuda(cudaEventRecord(e->ev_join, e->side), "cudaEventRecord");
+    // runs grouped by grid size, in member order within a size
+    std::vector<int> sizes;
+    for (const sipf_ctx* c : e->members)
+        if (std::find(sizes.begin(), sizes.end(), c->H) == sizes.end()) sizes.push_back(c->H);
+    std::sort(sizes.begin(), sizes.end());
+    const int device = e->members[0]->device;
+    for (int H : sizes) {
+        std::vector<SpecRun> runs;
+        for (int i = 0; i < n; ++i)
+            if (e->members[i]->H == H)
+                runs.push_back(spec_run(e->members[i], spectral_args(e->members[i], dt[i], 1)));
+        for (size_t b0 = 0; b0 < runs.size() && r == SIPF_OK; b0 += kMaxBatch) {
+            const int nb = static_cast<int>(std::min<size_t>(kMaxBatch, runs.size() - b0));
+            for (int pass = 0; pass < 3 && r == SIPF_OK; ++pass)
+                r = cuda(launch_spectral_batch(H, runs.data() + b0, nb, pass, device, e->main),
+                         "batched spectral pass");
+        }
+    }
+    if (r == SIPF_OK) r = cuda(cudaStreamWaitEvent(e->main, e->ev_join, 0), "cudaStreamWaitEvent");
+    if (r != SIPF_OK) return r;
+    for (int i = 0; i < n; ++i) advance_host(e->members[i], dt[i]);
+    return SIPF_OK;
+}
+
+// The two-step graph of the current parity and dt vector (captured on the
+// first call), with its run table.
+int batched_graph(sipf_ensemble* e, const double* dt, sipf_ensemble::BatchGraph** out) {
+    *out = nullptr;
+    const size_t n = e->members.size();
+    const int parity = e->members[0]->cur;
+    std::vector<double> dts(dt, dt + n);
+    for (auto& g : e->graphs)
+        if (g.parity == parity && g.dt == dts) {
+            *out = &g;
+            return SIPF_OK;
+        }
+    std::vector<RunDesc> host(n);
+    for (size_t i = 0; i < n; ++i) host[i] = run_desc(e->members[i], dt[i]);
+    RunDesc* d_runs = nullptr;
+    if (cudaMalloc(&d_runs, n * sizeof(RunDesc)) != cudaSuccess ||
+        cudaMemcpy(d_runs, host.data(), n * sizeof(RunDesc), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        if (d_runs) cudaFree(d_runs);
+        e->last_error = "run table of the batched step";
+        return SIPF_ENOMEM;
+    }
+    std::vector<int> cur0(n);
+    std::vector<int64_t> step0(n);
+    std::vector<double> time0(n);
+    for (size_t i = 0; i < n; ++i) {
+        cur0[i] = e->members[i]->cur;
+        step0[i] = e->members[i]->step;
+        time0[i] = e->members[i]->time;
+    }
+    if (cudaStreamBeginCapture(e->main, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(d_runs);
+        e->last_error = "stream capture of the batched step";
+        return SIPF_ECUDA;
+    }
+    int r = enqueue_batched_step(e, dt, d_runs, parity);
+    if (r == SIPF_OK) r = enqueue_batched_step(e, dt, d_runs, parity ^ 1);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(e->main, &graph);
+    for (size_t i = 0; i < n; ++i) {
+        e->members[i]->cur = cur0[i];
+        e->members[i]->step = step0[i];
+        e->members[i]->time = time0[i];
+    }
+    cudaGraphExec_t exec = nullptr;
+    const bool ok = r == SIPF_OK && ce == cudaSuccess && graph &&
+                    cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+        cudaGetLastError();
+        cudaFree(d_runs);
+        if (r == SIPF_OK) e->last_error = "instantiating the batched step graph";
+        return r == SIPF_OK ? SIPF_ECUDA : r;
+    }
+    if (e->graphs.size() >= 4) {
+        cudaGraphExecDestroy(e->graphs.front().exec);
+        cudaFree(e->graphs.front().d_runs);
+        e->graphs.erase(e->graphs.begin());
+    }
+    e->graphs.push_back({dts, parity, exec, d_runs});
+    *out = &e->graphs.back();
+    return SIPF_OK;
+}
+
+// k batched steps: the members' streams are ordered before and after the
+// ensemble's own stream, pairs of steps replay the captured graph, an odd
+// last step is enqueued launch by launch with the graph's run table.
+int batched_steps(sipf_ensemble* e, const double* dt, int64_t k) {
+    const size_t n = e->members.size();
+    for (size_t i = 0; i < n; ++i) {
+        if (cudaEventRecord(e->ev_member[i], e->members[i]->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(e->main, e->ev_member[i], 0) != cudaSuccess) {
+            cudaGetLastError();
+            e->last_error = "ordering the member streams";
+            return SIPF_ECUDA;
+        }
+    }
+    int r = SIPF_OK;
+    for (int64_t done = 0; done < k && r == SIPF_OK;) {
+        sipf_ensemble::BatchGraph* g = nullptr;
+        r = batched_graph(e, dt, &g);
+        if (r != SIPF_OK) break;
+        if (k - done >= 2) {
+            if (cudaGraphLaunch(g->exec, e->main) != cudaSuccess) {
+                cudaGetLastError();
+                e->last_error = "cudaGraphLaunch";
+                r = SIPF_ECUDA;
+                break;
+            }
+            for (size_t i = 0; i < n; ++i) {
+                advance_host(e->members[i], dt[i]);
+                advance_host(e->members[i], dt[i]);
+            }
+            done += 2;
+        } else {
+            r = enqueue_batched_step(e, dt, g->d_runs, e->members[0]->cur);
+            done += 1;
+        }
+    }
+    // later calls on a member (fields, diagnostics, ...) follow the batched work
+    if (cudaEventRecord(e->ev_done, e->main) != cudaSuccess) r = SIPF_ECUDA;
+    for (size_t i = 0; i < n; ++i)
+        if (cudaStreamWaitEvent(e->members[i]->stream, e->ev_done, 0) != cudaSuccess) r = SIPF_ECUDA;
+    if (r == SIPF_ECUDA) cudaGetLastError();
+    return r;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1104,6 +1304,22 @@ int sipf_ensemble_create(int32_t count, const sipf_grid* grids, const int64_t* N
             return r;
         }
         e->members.push_back(c);
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            ensemble_free(e);
+            return SIPF_ECUDA;
+        }
+        e->ev_member.push_back(ev);
+    }
+    if (cudaStreamCreateWithFlags(&e->main, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&e->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e->ev_done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        ensemble_free(e);
+        return SIPF_ECUDA;
     }
     *out = e;
     return SIPF_OK;
@@ -1113,6 +1329,14 @@ sipf_ctx* sipf_ensemble_member(sipf_ensemble* e, int32_t i) {
     if (!e || i < 0 || i >= static_cast<int32_t>(e->members.size())) return nullptr;
     return e->members[i];
 }
+
+int sipf_ensemble_set_mode(sipf_ensemble* e, int mode) {
+    if (!e || (mode != SIPF_ENSEMBLE_BATCHED && mode != SIPF_ENSEMBLE_STREAMS)) return SIPF_EINVAL;
+    e->mode = mode;
+    return SIPF_OK;
+}
+
+int sipf_ensemble_last_path(const sipf_ensemble* e) { return e ? e->last_path : SIPF_EINVAL; }
 
 int sipf_ensemble_step(sipf_ensemble* e, const double* dt, int64_t k) {
     if (!e || !dt || k < 0) return SIPF_EINVAL;
@@ -1127,6 +1351,12 @@ int sipf_ensemble_step(sipf_ensemble* e, const double* dt, int64_t k) {
             return SIPF_EINVAL;
         }
     }
+    if (k == 0) return SIPF_OK;
+    if (e->mode == SIPF_ENSEMBLE_BATCHED && batchable(e)) {
+        e->last_path = SIPF_ENSEMBLE_BATCHED;
+        return batched_steps(e, dt, k);
+    }
+    e->last_path = SIPF_ENSEMBLE_STREAMS;
     // every member's work goes to its own stream, so the kernels of different
     // members run concurrently; pairs of steps replay each member's captured
     // two-step graph, interleaved member after member

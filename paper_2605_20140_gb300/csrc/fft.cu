@@ -109,14 +109,25 @@ __device__ __forceinline__ void react(const SpectralArgs& a, float vv, float mm,
 }
 
 // ---------------------------------------------------------------- pass 1
-template <int H>
+// Launch-parameter batches: NB = 1 for one context's step, kMaxBatch for an
+// ensemble's runs of one grid size (the run index is a grid dimension).
+template <int H, int NB>
 __global__ void __launch_bounds__(Cfg<H>::NT1)
-    k_forward_xy(SpectralArgs a, const float* v, const float* __restrict__ m,
-                 const float* __restrict__ w, unsigned long long* __restrict__ acc,
-                 float* v_out, float2* __restrict__ gM, float2* __restrict__ gW,
-                 float2* __restrict__ gV, const float2* __restrict__ twg,
-                 const float* __restrict__ voff, const StepScalars* __restrict__ sc,
-                 const float* __restrict__ us) {
+    k_forward_xy(const __grid_constant__ SpecBatch<NB> batch) {
+    const SpecRun& R = batch.run[NB == 1 ? 0 : blockIdx.y];
+    const SpectralArgs& a = R.a;
+    const float* v = R.v;
+    const float* __restrict__ m = R.m;
+    const float* __restrict__ w = R.w;
+    unsigned long long* __restrict__ acc = R.acc;
+    float* v_out = R.v_out;
+    float2* __restrict__ gM = R.specM;
+    float2* __restrict__ gW = R.specW;
+    float2* __restrict__ gV = R.specV;
+    const float2* __restrict__ twg = R.twiddle;
+    const float* __restrict__ voff = R.voff;
+    const StepScalars* __restrict__ sc = R.sc;
+    const float* __restrict__ us = R.us;
     constexpr int NT = Cfg<H>::NT1, KXP = kxp<H>(), HK = H / 2 + 1, RP = rowp<H>();
     const float u_scale = sc->u_scale;   // u_bar per accumulator unit
     extern __shared__ float2 sm[];
@@ -235,17 +246,26 @@ __global__ void __launch_bounds__(Cfg<H>::NT1)
 // ---------------------------------------------------------------- pass 2
 // Block (ky, field, kx tile): forward DFT along z of the KB columns
 // [k0, k0 + KB) of the (z, ky) rows, the per-mode multiplier, inverse DFT.
-template <int H>
+template <int H, int NB>
 __global__ void __launch_bounds__(Cfg<H>::NT2)
-    k_z_multiply(SpectralArgs a, float2* __restrict__ gM, float2* __restrict__ gW,
-                 const float2* __restrict__ gV, float2* __restrict__ gB, float2* __restrict__ gA,
-                 const float2* __restrict__ twg, float* __restrict__ voff) {
+    k_z_multiply(const __grid_constant__ SpecBatch<NB> batch) {
     constexpr int NT = Cfg<H>::NT2, KXP = kxp<H>(), HK = H / 2 + 1, KB = zcols<H>();
+    // batches (H <= 128: one kx tile per row) take the run from grid dimension z
+    static_assert(NB == 1 || KB >= KXP, "batched z pass needs one kx tile");
+    const SpecRun& R = batch.run[NB == 1 ? 0 : blockIdx.z];
+    const SpectralArgs& a = R.a;
+    float2* __restrict__ gM = R.specM;
+    float2* __restrict__ gW = R.specW;
+    const float2* __restrict__ gV = R.specV;
+    float2* __restrict__ gB = R.specB;
+    float2* __restrict__ gA = R.specA;
+    const float2* __restrict__ twg = R.twiddle;
+    float* __restrict__ voff = R.voff;
     extern __shared__ float2 sm[];
     float2* buf = sm;             // [H (z)][KB (kx)]
     float2* tw = buf + H * KB;
     const int ky = blockIdx.x, field = blockIdx.y;   // 0 m, 1 w, 2 v -> i k_z V, 3 v -> filtered V
-    const int k0 = blockIdx.z * KB;
+    const int k0 = NB == 1 ? blockIdx.z * KB : 0;
     if (field < 2 && !a.do_mw) return;
     if (field == 3 && !a.filter) return;
     const float2* src = field == 0 ? gM : field == 1 ? gW : gV;
@@ -353,12 +373,19 @@ struct PackLoad {       // complex row of two real signals from their half spect
 // group 1: (i k_x V, i k_y V, B) -> grad v^n; group 0: (m, w) -> m^n, w^n.
 // The first inverse-y stage reads the planes straight from global memory and
 // the first inverse-x stage reads the packed rows straight from the y output.
-template <int H>
+template <int H, int NB>
 __global__ void __launch_bounds__(Cfg<H>::NT3)
-    k_inverse_xy(SpectralArgs a, const float2* __restrict__ gM, const float2* __restrict__ gW,
-                 const float2* __restrict__ gV, const float2* __restrict__ gB,
-                 float* __restrict__ m_out, float* __restrict__ w_out, float* __restrict__ G,
-                 const float2* __restrict__ twg) {
+    k_inverse_xy(const __grid_constant__ SpecBatch<NB> batch) {
+    const SpecRun& R = batch.run[NB == 1 ? 0 : blockIdx.z];
+    const SpectralArgs& a = R.a;
+    const float2* __restrict__ gM = R.specM;
+    const float2* __restrict__ gW = R.specW;
+    const float2* __restrict__ gV = a.filter ? R.specA : R.specV;
+    const float2* __restrict__ gB = R.specB;
+    float* __restrict__ m_out = R.m_out;
+    float* __restrict__ w_out = R.w_out;
+    float* __restrict__ G = R.G;
+    const float2* __restrict__ twg = R.twiddle;
     constexpr int NT = Cfg<H>::NT3, KXP = kxp<H>(), KXS = kxs<H>(), HK = H / 2 + 1;
     constexpr int RP = rowp<H>(), R1 = Radix<H>::R1;
     static_assert(H * RP <= 2 * H * KXS, "packed rows must fit in B0/B1");
@@ -646,7 +673,7 @@ cudaError_t spectral_pass_split(sipf_ctx* c, const SpectralArgs& a, int pass) {
                              static_cast<int>(smy1));
         cudaFuncSetAttribute(k_sx_columns<H, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(smy2));
-        cudaFuncSetAttribute(k_z_multiply<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_z_multiply<H, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(smz));
         cudaFuncSetAttribute(k_sx_inverse<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(smx2));
@@ -660,9 +687,10 @@ cudaError_t spectral_pass_split(sipf_ctx* c, const SpectralArgs& a, int pass) {
         k_sx_columns<H, -1><<<gy, kSxNT, smy1, c->stream>>>(a, c->specM, c->specW, c->specV,
                                                               nullptr, nullptr, c->twiddle, 0);
     } else if (pass == 1) {
-        k_z_multiply<H><<<dim3(H, 4, (KXP + zcols<H>() - 1) / zcols<H>()), Cfg<H>::NT2, smz,
-                          c->stream>>>(a, c->specM, c->specW, c->specV, c->specB, c->specA,
-                                       c->twiddle, c->voff);
+        SpecBatch<1> one;
+        one.run[0] = spec_run(c, a);
+        k_z_multiply<H, 1><<<dim3(H, 4, (KXP + zcols<H>() - 1) / zcols<H>()), Cfg<H>::NT2, smz,
+                             c->stream>>>(one);
     } else {
         // inverse y: M, W and B in place; V (or its filtered copy) -> i k_x V, i k_y V
         k_sx_columns<H, +1><<<gy, kSxNT, smy2, c->stream>>>(
@@ -676,37 +704,55 @@ cudaError_t spectral_pass_split(sipf_ctx* c, const SpectralArgs& a, int pass) {
     return cudaGetLastError();
 }
 
-template <int H>
-cudaError_t spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass) {
-    constexpr int KXP = kxp<H>();
-    const size_t sm1 = (static_cast<size_t>(H) * rowp<H>() + H * KXP + H) * sizeof(float2);
-    const size_t sm2 = (static_cast<size_t>(H) * zcols<H>() + H) * sizeof(float2);
-    const size_t sm3 = (3 * static_cast<size_t>(H) * kxs<H>() + H) * sizeof(float2);
+// Shared memory of the fused passes.
+template <int H> struct FusedSmem {
+    static constexpr size_t fwd = (static_cast<size_t>(H) * rowp<H>() + H * kxp<H>() + H) * sizeof(float2);
+    static constexpr size_t z = (static_cast<size_t>(H) * zcols<H>() + H) * sizeof(float2);
+    static constexpr size_t inv = (3 * static_cast<size_t>(H) * kxs<H>() + H) * sizeof(float2);
+};
+
+template <int H, int NB>
+void configure_fused(int device) {
     static int configured_device = -1;   // attributes are set once per process and device
-    if (configured_device != c->device) {
-        cudaFuncSetAttribute(k_forward_xy<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(sm1));
-        cudaFuncSetAttribute(k_z_multiply<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(sm2));
-        cudaFuncSetAttribute(k_inverse_xy<H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(sm3));
-        configured_device = c->device;
-    }
+    if (configured_device == device) return;
+    cudaFuncSetAttribute(k_forward_xy<H, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(FusedSmem<H>::fwd));
+    cudaFuncSetAttribute(k_z_multiply<H, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(FusedSmem<H>::z));
+    cudaFuncSetAttribute(k_inverse_xy<H, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(FusedSmem<H>::inv));
+    configured_device = device;
+}
+
+// One fused pass over a batch of nb runs of grid size H.
+template <int H, int NB>
+cudaError_t fused_pass(const SpecBatch<NB>& batch, int nb, int pass, int device, cudaStream_t s) {
+    configure_fused<H, NB>(device);
+    constexpr int KXP = kxp<H>();
     if (pass == 0) {
-        k_forward_xy<H><<<H, Cfg<H>::NT1, sm1, c->stream>>>(
-            a, c->v, c->m, c->w, reinterpret_cast<unsigned long long*>(c->acc), c->v, c->specM,
-            c->specW, c->specV, c->twiddle, c->voff, c->dsc + c->cur, c->us);
+        k_forward_xy<H, NB><<<dim3(H, nb), Cfg<H>::NT1, FusedSmem<H>::fwd, s>>>(batch);
     } else if (pass == 1) {
-        k_z_multiply<H><<<dim3(H, 4, (KXP + zcols<H>() - 1) / zcols<H>()), Cfg<H>::NT2, sm2,
-                            c->stream>>>(a, c->specM, c->specW, c->specV,
-                                                             c->specB, c->specA, c->twiddle,
-                                                             c->voff);
+        const int kt = (KXP + zcols<H>() - 1) / zcols<H>();
+        k_z_multiply<H, NB><<<dim3(H, 4, NB == 1 ? kt : nb), Cfg<H>::NT2, FusedSmem<H>::z, s>>>(
+            batch);
     } else {
-        k_inverse_xy<H><<<dim3(H, 2), Cfg<H>::NT3, sm3, c->stream>>>(
-            a, c->specM, c->specW, a.filter ? c->specA : c->specV, c->specB, c->m, c->w, c->G,
-            c->twiddle);
+        k_inverse_xy<H, NB><<<dim3(H, 2, nb), Cfg<H>::NT3, FusedSmem<H>::inv, s>>>(batch);
     }
     return cudaGetLastError();
+}
+
+template <int H>
+cudaError_t spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass) {
+    SpecBatch<1> one;
+    one.run[0] = spec_run(c, a);
+    return fused_pass<H, 1>(one, 1, pass, c->device, c->stream);
+}
+
+template <int H>
+cudaError_t batch_pass(const SpecRun* runs, int n, int pass, int device, cudaStream_t s) {
+    SpecBatch<kMaxBatch> batch;
+    for (int i = 0; i < n; ++i) batch.run[i] = runs[i];
+    return fused_pass<H, kMaxBatch>(batch, n, pass, device, s);
 }
 
 }  // namespace
@@ -730,6 +776,46 @@ cudaError_t launch_spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass) {
         case 384: return spectral_pass_split<384>(c, a, pass);
         case 432: return spectral_pass_split<432>(c, a, pass);
         case 512: return spectral_pass_split<512>(c, a, pass);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+SpecRun spec_run(const sipf_ctx* c, const SpectralArgs& a) {
+    SpecRun r;
+    r.a = a;
+    r.v = c->v;
+    r.m = c->m;
+    r.w = c->w;
+    r.acc = reinterpret_cast<unsigned long long*>(c->acc);
+    r.v_out = c->v;
+    r.m_out = c->m;
+    r.w_out = c->w;
+    r.G = c->G;
+    r.specM = c->specM;
+    r.specW = c->specW;
+    r.specV = c->specV;
+    r.specB = c->specB;
+    r.specA = c->specA;
+    r.twiddle = c->twiddle;
+    r.voff = c->voff;
+    r.sc = c->dsc + c->cur;
+    r.us = c->us;
+    return r;
+}
+
+cudaError_t launch_spectral_batch(int H, const SpecRun* runs, int n, int pass, int device,
+                                  cudaStream_t s) {
+    if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
+    switch (H) {
+        case 8: return batch_pass<8>(runs, n, pass, device, s);
+        case 16: return batch_pass<16>(runs, n, pass, device, s);
+        case 24: return batch_pass<24>(runs, n, pass, device, s);
+        case 32: return batch_pass<32>(runs, n, pass, device, s);
+        case 48: return batch_pass<48>(runs, n, pass, device, s);
+        case 64: return batch_pass<64>(runs, n, pass, device, s);
+        case 72: return batch_pass<72>(runs, n, pass, device, s);
+        case 96: return batch_pass<96>(runs, n, pass, device, s);
+        case 128: return batch_pass<128>(runs, n, pass, device, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -340,45 +340,81 @@ __device__ __forceinline__ int overflow_slot(const Layout& L, int* status) {
     return -1;
 }
 
-template <int ORDER>
-__global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
-    k_step(PushArgs a, const StepScalars* __restrict__ sc, const float4* __restrict__ G, Buf src,
-           Buf dst, Layout L, const Item* __restrict__ items, const int* __restrict__ n_items,
-           unsigned long long* __restrict__ acc, int do_deposit, int do_move,
-           int* __restrict__ status) {
+// What one run's particle step reads: the single-run kernel builds it from
+// its launch arguments, the ensemble kernel from its run table.
+struct StepView {
+    int H;
+    float drift, noise, tau;
+    uint32_t k0, k1;
+    int push;
+    const StepScalars* sc;
+    const float4* G;
+    Buf src, dst;
+    Layout L;
+    const Item* items;
+    unsigned long long* acc;
+    int* status;
+    int do_deposit, do_move;
+};
+
+// Philox round keys: from the launch arguments (precomputed), or advanced by
+// the Weyl constants from the key (the ensemble kernel, whose runs have
+// keys of their own).
+struct KeysGiven {
+    const uint32_t (&rk)[20];
+    __device__ __forceinline__ uint4 operator()(uint4 c) const { return philox4x32_10(c, rk); }
+};
+struct KeysScheduled {
+    const StepView& v;
+    __device__ __forceinline__ uint4 operator()(uint4 c) const {
+        return philox4x32_10(c, v.k0, v.k1);
+    }
+};
+
+// Shared memory of the step kernels.
+template <int ORDER> struct StepShared {
+    int dep[DepBlock<ORDER>::N];          // node sums of the items since the last flush
+    long long dep64[DepBlock<ORDER>::N];  // node sums of the tile's items so far
+    float4 gblk[kBlock];                  // (dv/dx, dv/dy, dv/dz, w) on the tile's 9^3 nodes
+    int tslot[2];                         // capacity and first slot of the item tile's bucket
+};
+
+// Items [i_lo, i_hi) of one run: deposit of X^(n-1), gather, noise, push,
+// mass update and binning of every particle.  dep and dep64 are zero on entry
+// and on exit.
+template <int ORDER, class Keys>
+__device__ __forceinline__ void step_items(const StepView& v, const Keys& keys, int i_lo, int i_hi,
+                                           StepShared<ORDER>& sh) {
     using DB = DepBlock<ORDER>;
     // Item sums in 32 bits: the trilinear contributions are non-negative and
     // below 2^19.5 (the deposit scale's bound), so kFlushItems items (4096
     // particles) sum below 2^32 unsigned; R^(4)'s signed sums are moved to
     // the 64-bit tile sums after every item.
     constexpr int kFlushItems = ORDER == 2 ? 4 : 1;
-    __shared__ int dep[DB::N];              // node sums of the items since the last flush
-    __shared__ long long dep64[DB::N];      // node sums of the tile's items so far
-    __shared__ float4 gblk[kBlock];         // (dv/dx, dv/dy, dv/dz, w) on the tile's 9^3 nodes
-    __shared__ int tslot[2];                // capacity and first slot of the item tile's bucket
-    const int H = a.H, T = H >> 3;
+    int* dep = sh.dep;
+    long long* dep64 = sh.dep64;
+    float4* gblk = sh.gblk;
+    int* tslot = sh.tslot;
+    const int H = v.H, T = H >> 3;
     const float Hf = __int2float_rn(H);
-    const int total = *n_items;
-    const uint32_t step_n = sc->n;                 // Philox counter word 0 of this step
-    const float dscale = sc->deposit_scale;        // 2^S of the fixed-point deposit
-    const float dshift = static_cast<float>(sc->deposit_shift);
+    const uint32_t step_n = v.sc->n;               // Philox counter word 0 of this step
+    const float dscale = v.sc->deposit_scale;      // 2^S of the fixed-point deposit
+    const float dshift = static_cast<float>(v.sc->deposit_shift);
     // a contribution's mass in deposit units, a 2^S = 2^(dl log2 e + S), is
     // below 2^19.5 by the choice of S; the clamp keeps a corrupt log-mass
     // (NaN) inside the bound the item sums rely on
     constexpr float kMaxLog2Unit = 19.49f;
-    for (int i = threadIdx.x; i < DB::N; i += kNT) {
-        dep[i] = 0;
-        dep64[i] = 0;
-    }
-    // block b takes a contiguous run of items; consecutive items of one tile
-    // share the node block of the gather array and the deposit sums, which
-    // go to the grid accumulator once, when the tile changes
-    const int i_lo = static_cast<int>(static_cast<long long>(blockIdx.x) * total / gridDim.x);
-    const int i_hi = static_cast<int>(static_cast<long long>(blockIdx.x + 1) * total / gridDim.x);
+    const Buf& src = v.src;
+    const Buf& dst = v.dst;
+    const Layout& L = v.L;
+    unsigned long long* acc = v.acc;
+    const float4* G = v.G;
+    int* status = v.status;
+    const int do_deposit = v.do_deposit, do_move = v.do_move;
     int cur = -1, cx0 = 0, cy0 = 0, cz0 = 0;   // tile held in dep64 / gblk, its first cell
     int pending = 0;                           // items summed in dep since its last flush
     for (int item_idx = i_lo; item_idx <= i_hi; ++item_idx) {
-        const Item it = item_idx < i_hi ? items[item_idx] : Item{-1, 0, 0, 0, 0, 0, 0, 0};
+        const Item it = item_idx < i_hi ? v.items[item_idx] : Item{-1, 0, 0, 0, 0, 0, 0, 0};
         const int tile = it.tile;
         const bool change = tile != cur || tile < 0;
         // every thread moves its own nodes (j = threadIdx.x + k kNT) from dep
@@ -387,10 +423,10 @@ __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
         // its atomics
         if (do_deposit && pending > 0 && (change || pending == kFlushItems)) {
             for (int j = threadIdx.x; j < DB::N; j += kNT) {
-                const int v = dep[j];
-                if (v) {
-                    dep64[j] += ORDER == 2 ? static_cast<long long>(static_cast<unsigned>(v))
-                                           : static_cast<long long>(v);
+                const int d = dep[j];
+                if (d) {
+                    dep64[j] += ORDER == 2 ? static_cast<long long>(static_cast<unsigned>(d))
+                                           : static_cast<long long>(d);
                     dep[j] = 0;
                 }
             }
@@ -401,13 +437,13 @@ __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
                 // flush the finished tile's node block into the grid accumulator
                 // (two's complement sums)
                 for (int j = threadIdx.x; j < DB::N; j += kNT) {
-                    const long long v = dep64[j];
-                    if (v) {
+                    const long long d = dep64[j];
+                    if (d) {
                         const int lx = j % DB::B - DB::DO, ly = (j / DB::B) % DB::B - DB::DO;
                         const int lz = j / (DB::B * DB::B) - DB::DO;
                         const int nx = wrap_index(cx0 + lx, H), ny = wrap_index(cy0 + ly, H);
                         const int nz = wrap_index(cz0 + lz, H);
-                        atomicAdd(acc + (nz * H + ny) * H + nx, static_cast<unsigned long long>(v));
+                        atomicAdd(acc + (nz * H + ny) * H + nx, static_cast<unsigned long long>(d));
                         dep64[j] = 0;
                     }
                 }
@@ -417,7 +453,7 @@ __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
             cx0 = it.tx * 8;
             cy0 = it.ty * 8;
             cz0 = it.tz * 8;
-            if (do_move && a.push && tile >= 0) {
+            if (do_move && v.push && tile >= 0) {
                 // the tile's node block of the gather array (periodic), 9 float4 per row
                 for (int q = threadIdx.x; q < kBlock; q += kNT) {
                     const int lx = q % 9, ly = (q / 9) % 9, lz = q / 81;
@@ -531,29 +567,29 @@ __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
                     }
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
-                        const int side = k & 1, u = (k >> 1) & 1, v = k >> 2;
+                        const int side = k & 1, u = (k >> 1) & 1, w2 = k >> 2;
                         const int o = side ? 2 : -1;
-                        emit(o, u, v, __fmul_rn(ea, __fmul_rn(sx[side], __fmul_rn(wy[u], wz[v]))));
-                        emit(u, o, v, __fmul_rn(ea, __fmul_rn(sy[side], __fmul_rn(wx[u], wz[v]))));
-                        emit(u, v, o, __fmul_rn(ea, __fmul_rn(sz[side], __fmul_rn(wx[u], wy[v]))));
+                        emit(o, u, w2, __fmul_rn(ea, __fmul_rn(sx[side], __fmul_rn(wy[u], wz[w2]))));
+                        emit(u, o, w2, __fmul_rn(ea, __fmul_rn(sy[side], __fmul_rn(wx[u], wz[w2]))));
+                        emit(u, w2, o, __fmul_rn(ea, __fmul_rn(sz[side], __fmul_rn(wx[u], wy[w2]))));
                     }
                 }
             }
 
             if (do_move) {
-                if (a.push && valid) {
+                if (v.push && valid) {
                     const float4 g = in_tile ? gather4_block(gblk, c, (lz * 9 + ly) * 9 + lx)
                                              : gather4(G, c, H);
                     // mass factor 1 + tau (rho(w_H) - 1), rho(w) = 2w/(1+w) (Eq. u_hat_update)
                     const float rho = __fdividef(__fmul_rn(2.0f, g.w), __fadd_rn(1.0f, g.w));
-                    const float x = __fmul_rn(a.tau, __fsub_rn(rho, 1.0f));
-                    const float inc = a.tau <= 0.0625f ? log1p_small(x) : log1pf(x);
+                    const float x = __fmul_rn(v.tau, __fsub_rn(rho, 1.0f));
+                    const float inc = v.tau <= 0.0625f ? log1p_small(x) : log1pf(x);
                     pl = pl + f2d_bits(inc);
                     // Euler-Maruyama push in grid units
-                    const float3 nz = box_muller(philox4x32_10(make_uint4(step_n, 0u, pid, 0u), a.rk));
-                    px = __fmaf_rn(a.noise, nz.x, __fmaf_rn(a.drift, g.x, px));
-                    py = __fmaf_rn(a.noise, nz.y, __fmaf_rn(a.drift, g.y, py));
-                    pz = __fmaf_rn(a.noise, nz.z, __fmaf_rn(a.drift, g.z, pz));
+                    const float3 nz = box_muller(keys(make_uint4(step_n, 0u, pid, 0u)));
+                    px = __fmaf_rn(v.noise, nz.x, __fmaf_rn(v.drift, g.x, px));
+                    py = __fmaf_rn(v.noise, nz.y, __fmaf_rn(v.drift, g.y, py));
+                    pz = __fmaf_rn(v.noise, nz.z, __fmaf_rn(v.drift, g.z, pz));
                     wrap3(px, py, pz, Hf, &bad);
                 }
                 const int nt = valid ? tile_at(px, py, pz, T) : -1;
@@ -606,6 +642,28 @@ __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
     }
 }
 
+template <int ORDER>
+__global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
+    k_step(PushArgs a, const StepScalars* __restrict__ sc, const float4* __restrict__ G, Buf src,
+           Buf dst, Layout L, const Item* __restrict__ items, const int* __restrict__ n_items,
+           unsigned long long* __restrict__ acc, int do_deposit, int do_move,
+           int* __restrict__ status) {
+    __shared__ StepShared<ORDER> sh;
+    for (int i = threadIdx.x; i < DepBlock<ORDER>::N; i += kNT) {
+        sh.dep[i] = 0;
+        sh.dep64[i] = 0;
+    }
+    // block b takes a contiguous run of items; consecutive items of one tile
+    // share the node block of the gather array and the deposit sums, which
+    // go to the grid accumulator once, when the tile changes
+    const int total = *n_items;
+    const int i_lo = static_cast<int>(static_cast<long long>(blockIdx.x) * total / gridDim.x);
+    const int i_hi = static_cast<int>(static_cast<long long>(blockIdx.x + 1) * total / gridDim.x);
+    const StepView v{a.H, a.drift, a.noise, a.tau, a.k0, a.k1, a.push, sc, G, src, dst, L,
+                     items, acc, status, do_deposit, do_move};
+    step_items<ORDER>(v, KeysGiven{a.rk}, i_lo, i_hi, sh);
+}
+
 // ------------------------------------------------------------------ planning
 // Block-wide exclusive scan (one value per thread) of kPlanNT threads.
 constexpr int kPlanNT = 1024;
@@ -644,13 +702,13 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* smem, int* total
 // null, the bucket layout of the other buffer for the next step (capacity
 // count + count/8 + 32, rounded up to a multiple of 4) with its counters
 // reset; with next_sc, the next step's scalars from those of this step.
-__global__ void __launch_bounds__(kPlanNT)
-    k_plan(int ntiles, int T, const int* __restrict__ cnt, const int* __restrict__ cap,
-           const int* __restrict__ bstart, const int* __restrict__ ovf, int ovf_base, Item* items,
-           int* n_items, int* next_bstart, int* next_cap, int* next_cnt, int* next_ovf,
-           int* __restrict__ status, const StepScalars* __restrict__ cur_sc,
-           StepScalars* __restrict__ next_sc, double dt, double log2_maxrel, double exp_logref,
-           double h3) {
+__device__ __forceinline__ void plan_body(
+    int ntiles, int T, const int* __restrict__ cnt, const int* __restrict__ cap,
+    const int* __restrict__ bstart, const int* __restrict__ ovf, int ovf_base, Item* items,
+    int* n_items, int* next_bstart, int* next_cap, int* next_cnt, int* next_ovf,
+    int* __restrict__ status, const StepScalars* __restrict__ cur_sc,
+    StepScalars* __restrict__ next_sc, double dt, double log2_maxrel, double exp_logref,
+    double h3) {
     __shared__ int smem[33];
     const int per = (ntiles + kPlanNT - 1) / kPlanNT;
     const int t0 = threadIdx.x * per;
@@ -713,6 +771,73 @@ __global__ void __launch_bounds__(kPlanNT)
         if (next_sc)
             fill_step_scalars(next_sc, cur_sc->n + 1u, cur_sc->time + dt, log2_maxrel, exp_logref,
                               h3);
+    }
+}
+
+__global__ void __launch_bounds__(kPlanNT)
+    k_plan(int ntiles, int T, const int* __restrict__ cnt, const int* __restrict__ cap,
+           const int* __restrict__ bstart, const int* __restrict__ ovf, int ovf_base, Item* items,
+           int* n_items, int* next_bstart, int* next_cap, int* next_cnt, int* next_ovf,
+           int* __restrict__ status, const StepScalars* __restrict__ cur_sc,
+           StepScalars* __restrict__ next_sc, double dt, double log2_maxrel, double exp_logref,
+           double h3) {
+    plan_body(ntiles, T, cnt, cap, bstart, ovf, ovf_base, items, n_items, next_bstart, next_cap,
+              next_cnt, next_ovf, status, cur_sc, next_sc, dt, log2_maxrel, exp_logref, h3);
+}
+
+// The plan of every run of an ensemble after a batched step from buffer
+// `parity` (block r plans run r: items of the written buffer parity ^ 1,
+// layout of buffer parity, scalars of the next step).
+__global__ void __launch_bounds__(kPlanNT) k_plan_multi(const RunDesc* __restrict__ runs,
+                                                        int parity) {
+    const RunDesc& d = runs[blockIdx.x];
+    const int b = parity ^ 1, o = parity;
+    plan_body(d.ntiles, d.H / 8, d.cnt[b], d.cap[b], d.bstart[b], d.ovf[b], d.ovf_base, d.items,
+              d.n_items, d.bstart[o], d.cap[o], d.cnt[o], d.ovf[o], d.status, d.dsc + o,
+              d.dsc + b, d.dt, d.log2_maxrel, d.exp_logref, d.h3);
+}
+
+// One persistent launch over the items of all runs of an ensemble (all
+// reading buffer `parity`): the runs' item lists are concatenated, each
+// block takes a contiguous range and steps it run segment by run segment,
+// with the segment's run read from the table into shared memory (its
+// values are read from there where the single-run kernel has launch
+// arguments).  Trilinear assignment only.
+__global__ void __launch_bounds__(kNT, DepBlock<2>::MIN_BLOCKS)
+    k_step_multi(const RunDesc* __restrict__ runs, int nruns, int parity) {
+    __shared__ StepShared<2> sh;
+    __shared__ int prefix[kMaxRuns + 1];
+    __shared__ int scan_tmp[33];
+    __shared__ StepView view;
+    for (int i = threadIdx.x; i < DepBlock<2>::N; i += kNT) {
+        sh.dep[i] = 0;
+        sh.dep64[i] = 0;
+    }
+    const int cnt = threadIdx.x < nruns ? *runs[threadIdx.x].n_items : 0;
+    int total;
+    const int ex = block_exclusive_scan(cnt, scan_tmp, &total);
+    if (threadIdx.x < nruns) prefix[threadIdx.x] = ex;
+    if (threadIdx.x == 0) prefix[nruns] = total;
+    __syncthreads();
+    const int i_lo = static_cast<int>(static_cast<long long>(blockIdx.x) * total / gridDim.x);
+    const int i_hi = static_cast<int>(static_cast<long long>(blockIdx.x + 1) * total / gridDim.x);
+    const int b = parity, o = parity ^ 1;
+    for (int r = 0; r < nruns; ++r) {
+        const int lo = max(i_lo, prefix[r]) - prefix[r];
+        const int hi = min(i_hi, prefix[r + 1]) - prefix[r];
+        if (lo >= hi) continue;
+        if (threadIdx.x == 0) {
+            const RunDesc& d = runs[r];
+            view = StepView{d.H, d.drift, d.noise, d.tau, d.k0, d.k1, 1, d.dsc + b,
+                            reinterpret_cast<const float4*>(d.G),
+                            Buf{d.sx[b], d.sy[b], d.sz[b], d.dl[b], d.id[b]},
+                            Buf{d.sx[o], d.sy[o], d.sz[o], d.dl[o], d.id[o]},
+                            Layout{d.bstart[o], d.cap[o], d.cnt[o], d.ovf[o], d.ovf_base, d.ovf_cap},
+                            d.items, d.acc, d.status, 1, 1};
+        }
+        __syncthreads();
+        step_items<2>(view, KeysScheduled{view}, lo, hi, sh);
+        __syncthreads();
     }
 }
 
@@ -1141,6 +1266,57 @@ cudaError_t launch_plan(sipf_ctx* c, int b, int next_layout, cudaStream_t s, dou
         // b is the buffer the step just wrote: its slot is the next step's, o's the current one
         c->dsc + o, dt > 0.0 ? c->dsc + b : nullptr, dt, c->log2_maxrel, c->exp_logref, c->h3);
     return cudaGetLastError();
+}
+
+cudaError_t launch_step_multi(const RunDesc* runs, int n, int parity, cudaStream_t s) {
+    if (n < 1 || n > kMaxRuns) return cudaErrorInvalidValue;
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_multi, kNT, 0);
+    k_step_multi<<<nsm * (per_sm > 0 ? per_sm : 1), kNT, 0, s>>>(runs, n, parity);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plan_multi(const RunDesc* runs, int n, int parity, cudaStream_t s) {
+    if (n < 1) return cudaErrorInvalidValue;
+    k_plan_multi<<<n, kPlanNT, 0, s>>>(runs, parity);
+    return cudaGetLastError();
+}
+
+RunDesc run_desc(const sipf_ctx* c, double dt) {
+    RunDesc d{};
+    d.H = c->H;
+    d.ntiles = c->ntiles;
+    d.ovf_base = c->ovf_base;
+    d.ovf_cap = static_cast<int>(c->N);
+    d.drift = static_cast<float>(c->p.chi * dt / c->h);
+    d.noise = static_cast<float>(sqrt(2.0 * c->p.Du * dt) / c->h);
+    d.tau = static_cast<float>(dt);
+    d.k0 = static_cast<uint32_t>(c->p.seed);
+    d.k1 = static_cast<uint32_t>(c->p.seed >> 32);
+    for (int b = 0; b < 2; ++b) {
+        d.sx[b] = c->sx[b];
+        d.sy[b] = c->sy[b];
+        d.sz[b] = c->sz[b];
+        d.dl[b] = c->dl[b];
+        d.id[b] = c->id[b];
+        d.bstart[b] = c->bstart[b];
+        d.cap[b] = c->cap[b];
+        d.cnt[b] = c->cnt[b];
+        d.ovf[b] = c->ovf[b];
+    }
+    d.items = c->items;
+    d.n_items = c->n_items;
+    d.acc = reinterpret_cast<unsigned long long*>(c->acc);
+    d.G = c->G;
+    d.status = c->status;
+    d.dsc = c->dsc;
+    d.dt = dt;
+    d.log2_maxrel = c->log2_maxrel;
+    d.exp_logref = c->exp_logref;
+    d.h3 = c->h3;
+    return d;
 }
 
 cudaError_t launch_tile_count(sipf_ctx* c, int b, int* cnt) {

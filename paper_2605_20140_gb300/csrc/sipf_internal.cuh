@@ -137,6 +137,60 @@ struct SpectralArgs {
     int do_mw;             // transform m and w (0 in the initial transform)
 };
 
+// One run's data for the fused spectral passes (H <= 128).  The passes take
+// a batch of runs as a launch parameter: one run for a context's own step,
+// up to kMaxBatch runs of one grid size for an ensemble's batched step (the
+// run is then a grid dimension of the launch).
+struct SpecRun {
+    SpectralArgs a;
+    const float* v;
+    const float* m;
+    const float* w;
+    unsigned long long* acc;      // deposit accumulator (read and cleared by the forward pass)
+    float* v_out;
+    float* m_out;
+    float* w_out;
+    float* G;                     // gather array (dv/dx, dv/dy, dv/dz, w) per node
+    float2* specM;
+    float2* specW;
+    float2* specV;
+    float2* specB;
+    float2* specA;                // filtered v spectrum (filter on only)
+    const float2* twiddle;
+    float* voff;
+    const StepScalars* sc;        // scalars of the step (u_bar per accumulator unit)
+    const float* us;              // K_sigma * u_bar (sigma > 0 only)
+};
+constexpr int kMaxBatch = 64;
+
+// One ensemble member as the batched particle kernels see it (device table
+// written when the ensemble captures its step graph; both buffer parities).
+struct RunDesc {
+    int H, ntiles, ovf_base, ovf_cap;
+    float drift, noise, tau;            // push of this run's dt (grid units)
+    uint32_t k0, k1;                    // Philox key
+    float* sx[2];
+    float* sy[2];
+    float* sz[2];
+    double* dl[2];
+    uint32_t* id[2];
+    int* bstart[2];
+    int* cap[2];
+    int* cnt[2];
+    int* ovf[2];
+    Item* items;
+    int* n_items;
+    unsigned long long* acc;
+    const float* G;
+    int* status;
+    StepScalars* dsc;                   // [2], slot = parity of the source buffer
+    double dt, log2_maxrel, exp_logref, h3;
+};
+constexpr int kMaxRuns = 256;           // runs of one batched particle launch
+template <int NB> struct SpecBatch {
+    SpecRun run[NB];
+};
+
 }  // namespace sipf
 
 struct sipf_ctx {
@@ -264,6 +318,12 @@ cudaError_t launch_normals(const uint32_t* ids, int64_t N, uint32_t n, uint64_t 
                            uint32_t* bits, cudaStream_t s);
 cudaError_t launch_conv_check(const float* f, const double* d, int n, int* mismatches,
                               cudaStream_t s);
+// Batched particle kernels of an ensemble whose n <= kMaxRuns members all
+// read buffer `parity`: the step over the concatenated items of all runs
+// (one persistent launch), and the plan of every run (one block per run).
+cudaError_t launch_step_multi(const RunDesc* runs, int n, int parity, cudaStream_t s);
+cudaError_t launch_plan_multi(const RunDesc* runs, int n, int parity, cudaStream_t s);
+RunDesc run_desc(const sipf_ctx* c, double dt);
 // api.cu
 int run_steps_for(sipf_ctx* c, double dt, int64_t k);
 // sipf_create with every device array taken from `pool` on `stream`
@@ -279,6 +339,12 @@ int resample_device(sipf_ctx* c, int src, int dst, double ratio, int* done, std:
 // fft.cu
 cudaError_t launch_spectral_step(sipf_ctx* c, const SpectralArgs& a);
 cudaError_t launch_spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass);
+// The context's data for the fused spectral passes (its current buffer parity).
+SpecRun spec_run(const sipf_ctx* c, const SpectralArgs& a);
+// One fused spectral pass (0 forward, 1 z, 2 inverse) over n <= kMaxBatch
+// runs of grid size H <= 128, in one launch.
+cudaError_t launch_spectral_batch(int H, const SpecRun* runs, int n, int pass, int device,
+                                  cudaStream_t s);
 void fill_twiddles(int H, float2* host_out);
 
 }  // namespace sipf

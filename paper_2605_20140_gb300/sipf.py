@@ -25,6 +25,9 @@ SIPF_EINTERNAL = -7
 SIPF_HOST = 0
 SIPF_DEVICE = 1
 
+SIPF_ENSEMBLE_BATCHED = 0
+SIPF_ENSEMBLE_STREAMS = 1
+
 FIELD_U, FIELD_V, FIELD_M, FIELD_W, FIELD_GX, FIELD_GY, FIELD_GZ = (1, 2, 4, 8, 16, 32, 64)
 FIELD_NAMES = ("u", "v", "m", "w", "gx", "gy", "gz")
 
@@ -42,6 +45,7 @@ EXPORTED = (
     "sipf_server_submit", "sipf_server_advance", "sipf_server_poll", "sipf_server_collect",
     "sipf_server_stats", "sipf_server_last_error", "sipf_server_destroy",
     "sipf_server_set_limit", "sipf_server_fail_next_admission", "sipf_canonical_order",
+    "sipf_ensemble_set_mode", "sipf_ensemble_last_path",
 )
 PROFILE_GROUPS = 4
 
@@ -115,6 +119,8 @@ def load() -> ctypes.CDLL:
         "sipf_ensemble_sync": ([P], I32),
         "sipf_ensemble_last_error": ([P], ctypes.c_char_p),
         "sipf_ensemble_destroy": ([P], None),
+        "sipf_ensemble_set_mode": ([P, I32], I32),
+        "sipf_ensemble_last_path": ([P], I32),
         "sipf_context_bytes": ([ctypes.POINTER(sipf_grid), I64, ctypes.POINTER(sipf_params)], I64),
         "sipf_device_bytes": ([P], I64),
         "sipf_server_create": ([I64, ctypes.POINTER(P)], I32),
@@ -434,16 +440,24 @@ class Simulation:
 
 
 class Ensemble:
-    """Independent runs advanced together, one stream each; members are
-    Simulation views (owned by the ensemble)."""
+    """Independent runs advanced together (batched launches across members,
+    or one stream per member); members are Simulation views (owned by the
+    ensemble)."""
 
-    def __init__(self, specs):
+    def __init__(self, specs, mode: int = SIPF_ENSEMBLE_BATCHED):
         """specs: sequence of (H, L, origin, N, params)."""
         grids = [make_grid(H, L, origin) for H, L, origin, _, _ in specs]
         self.ens = sipf_ensemble_create(grids, [N for _, _, _, N, _ in specs],
                                         [make_params(p) for *_, p in specs])
         self.members = [Simulation(H, L, origin, N, None, _ctx=sipf_ensemble_member(self.ens, i))
                         for i, (H, L, origin, N, _) in enumerate(specs)]
+        self.set_mode(mode)
+
+    def set_mode(self, mode: int):
+        _check_ens(load().sipf_ensemble_set_mode(self.ens, int(mode)), self.ens)
+
+    def last_path(self) -> int:
+        return int(load().sipf_ensemble_last_path(self.ens))
 
     def step(self, dts, k=1):
         sipf_ensemble_step(self.ens, dts, k)

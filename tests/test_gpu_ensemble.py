@@ -34,16 +34,23 @@ def snapshot(sim):
     return f, s[o], loga[o]
 
 
-def test_members_equal_their_solo_runs():
+@pytest.mark.parametrize("mode,steps", [(sipf.SIPF_ENSEMBLE_BATCHED, 12),
+                                        (sipf.SIPF_ENSEMBLE_BATCHED, 13),
+                                        (sipf.SIPF_ENSEMBLE_STREAMS, 12)])
+def test_members_equal_their_solo_runs(mode, steps):
+    """Batched launches across members (one particle-step launch for all
+    runs, one launch per spectral pass and grid size, replayed as a graph;
+    an odd step count ends with one step enqueued launch by launch) or one
+    stream per member: every member ends bit for bit where its solo run ends."""
     runs = ensemble_workloads(6, seed=3, max_log2_N=16)
     assert len({w.H for w in runs}) > 1          # uneven grids
     dts = np.array([w.dt * (1.0 + 0.1 * i) for i, w in enumerate(runs)])
-    steps = 12
-    with sipf.Ensemble([(w.H, w.L, w.origin, w.N, w.params) for w in runs]) as ens:
+    with sipf.Ensemble([(w.H, w.L, w.origin, w.N, w.params) for w in runs], mode=mode) as ens:
         for sim, w in zip(ens.members, runs):
             sim.set_state(w.x, w.mass, w.ids, w.v, w.m, w.w)
         ens.step(dts, steps)
         ens.sync()
+        assert ens.last_path() == mode
         got = [snapshot(sim) for sim in ens.members]
         assert all(sim.diagnostics()["step"] == steps for sim in ens.members)
     for w, dt, (f, s, l) in zip(runs, dts, got):
@@ -93,3 +100,54 @@ def test_member_with_drawn_parameters_matches_oracle():
         errs = compare(ens.members[i], st, w)
     print(f"member {i} (H={w.H}, N={w.N}, chi={w.params.chi:.4f}, alpha={w.params.alpha:.2f}, "
           f"Du={w.params.Du:.2e}) rel-L2:", {k: f"{v:.1e}" for k, v in errs.items()})
+
+
+def test_batched_launches_split_above_the_batch_size():
+    """70 members of one grid size: the spectral passes take them in two
+    launches (64 + 6); every member still equals its solo run."""
+    from sipf_inputs import Params, workload
+    specs, states = [], []
+    for i in range(70):
+        w = workload("small", H=16, N=300 + 7 * i, seed=i)
+        w.params = Params(seed=1000 + i, chi=0.01 + 1e-4 * i)
+        specs.append((w.H, w.L, w.origin, w.N, w.params))
+        states.append(w)
+    with sipf.Ensemble(specs) as ens:
+        for sim, w in zip(ens.members, states):
+            sim.set_state(w.x, w.mass, w.ids, w.v, w.m, w.w)
+        ens.step([w.dt for w in states], 4)
+        ens.sync()
+        assert ens.last_path() == sipf.SIPF_ENSEMBLE_BATCHED
+        got = {i: snapshot(ens.members[i]) for i in (0, 63, 64, 69)}
+    for i, (f, s, l) in got.items():
+        w = states[i]
+        with sipf.Simulation(w.H, w.L, w.origin, w.N, w.params) as solo:
+            solo.set_state(w.x, w.mass, w.ids, w.v, w.m, w.w)
+            solo.step(w.dt, 4)
+            f0, s0, l0 = snapshot(solo)
+        for k in f0:
+            np.testing.assert_array_equal(f[k], f0[k], err_msg=f"member {i} {k}")
+        np.testing.assert_array_equal(s, s0)
+        np.testing.assert_array_equal(l, l0)
+
+
+def test_a_member_outside_the_batched_form_falls_back_to_streams():
+    """A member with the low-pass filter on cannot join the batched launches:
+    the ensemble steps one stream per member, with the same results."""
+    import dataclasses
+    runs = ensemble_workloads(3, seed=4, max_log2_N=14)
+    runs[1].params = dataclasses.replace(runs[1].params, H0=runs[1].H ** (8 / 13))
+    with sipf.Ensemble([(w.H, w.L, w.origin, w.N, w.params) for w in runs]) as ens:
+        for sim, w in zip(ens.members, runs):
+            sim.set_state(w.x, w.mass, w.ids, w.v, w.m, w.w)
+        ens.step([w.dt for w in runs], 3)
+        ens.sync()
+        assert ens.last_path() == sipf.SIPF_ENSEMBLE_STREAMS
+        f, s, l = snapshot(ens.members[1])
+    w = runs[1]
+    with sipf.Simulation(w.H, w.L, w.origin, w.N, w.params) as solo:
+        solo.set_state(w.x, w.mass, w.ids, w.v, w.m, w.w)
+        solo.step(w.dt, 3)
+        f0, s0, l0 = snapshot(solo)
+    for k in f0:
+        np.testing.assert_array_equal(f[k], f0[k], err_msg=k)
