@@ -190,6 +190,35 @@ int sipf_cell_start(sipf_ctx* ctx, int32_t* cell_start, int where);
  * pointers NULL, bad `where`, no state), SIPF_ECUDA. */
 int sipf_canonical_order(sipf_ctx* ctx, int32_t* cell_start, uint32_t* ids, int where);
 
+/* Tuning.  Launch choices that change speed, never results beyond float32
+ * rounding: radix_plan (0 or 1) selects between two Stockham plans of each
+ * transform length (e.g. 96 = 8 x 4 x 3 or 12 x 8; the results differ only
+ * by float32 rounding); step_blocks_per_sm (0 = the occupancy limit, else at
+ * most that many particle-step blocks per SM); bucket capacity = count +
+ * count / bucket_slack_div + bucket_slack_add per tile, 8 <= div <= 1024,
+ * 0 <= add <= 32 (smaller slack sends more particles to the overflow region;
+ * the particle results are bit for bit the same).  The autotuner
+ * (paper_2605_20140_gb300/autotune.py) times the candidates on the GPU and
+ * writes a table the library reads: sipf_create applies the first line of
+ * the table matching its (H, N); the table is the file named by the
+ * SIPF_TUNING environment variable, else sipf_tuning.txt next to
+ * libsipf.so, read at the first sipf_create (or sipf_tuning_lookup), or one
+ * loaded with sipf_tuning_load (NULL: empty table).
+ * sipf_set_tuning applies a choice to a context (dropping its captured step
+ * graphs; synchronises); sipf_get_tuning reads it back.  sipf_tuning_lookup
+ * returns 1 and fills *out when the table has a line for (H, N), else 0.
+ * Errors: SIPF_EINVAL (NULL, out of range, unreadable or malformed file). */
+typedef struct {
+    int32_t radix_plan;
+    int32_t step_blocks_per_sm;
+    int32_t bucket_slack_div;
+    int32_t bucket_slack_add;
+} sipf_tuning;
+int sipf_set_tuning(sipf_ctx* ctx, const sipf_tuning* tuning);
+int sipf_get_tuning(const sipf_ctx* ctx, sipf_tuning* tuning);
+int sipf_tuning_load(const char* path);
+int sipf_tuning_lookup(int32_t H, int64_t N, sipf_tuning* out);
+
 /* FP64 diagnostics of the current state; synchronises. */
 int sipf_diagnostics(sipf_ctx* ctx, sipf_diag* out);
 

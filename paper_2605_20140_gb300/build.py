@@ -23,7 +23,9 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
           "-I", INC]
 PER_FILE = {"particles.cu": ["-fmad=false"]}
-SOURCES = ["api.cu", "particles.cu", "fft.cu", "noalloc.cu", "resample.cu", "server.cu", "smooth.cu"]
+SOURCES = ["api.cu", "particles.cu", "fft.cu", "fft_fused_p0.cu", "fft_fused_p1.cu",
+           "fft_split_p0.cu", "fft_split_p1.cu", "noalloc.cu", "resample.cu", "server.cu",
+           "smooth.cu"]
 
 
 def _nvcc() -> str:

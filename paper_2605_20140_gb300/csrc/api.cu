@@ -6,8 +6,11 @@
 #include <stdio.h>
 #include <string.h>
 
-#include <new>
+#include <dlfcn.h>
+
 #include <algorithm>
+#include <mutex>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -33,6 +36,91 @@ int cuda_fail(sipf_ctx* c, cudaError_t e, const char* where) {
     } while (0)
 
 // Grid sides with a radix plan (2^a 3^b) that are multiples of the 8-cell tile.
+// ---------------------------------------------------------------- tuning table
+// Process-wide table of tuning choices by grid size and particle count,
+// read from a text file (the autotuner writes it): lines
+//   H  N_min  N_max  radix_plan  step_blocks_per_sm  bucket_slack_div  bucket_slack_add
+// ('#' starts a comment).  The first matching line applies to a new context.
+struct TuneEntry {
+    int H;
+    int64_t n_min, n_max;
+    sipf_tuning t;
+};
+std::mutex g_tune_mutex;
+std::vector<TuneEntry> g_tune;
+bool g_tune_loaded = false;
+
+bool tuning_valid(const sipf_tuning& t) {
+    return (t.radix_plan == 0 || t.radix_plan == 1) && t.step_blocks_per_sm >= 0 &&
+           t.step_blocks_per_sm <= 32 && t.bucket_slack_div >= 8 &&
+           t.bucket_slack_div <= 1024 && t.bucket_slack_add >= 0 && t.bucket_slack_add <= 32;
+}
+
+int parse_tuning_file(const char* path, std::vector<TuneEntry>* out) {
+    FILE* f = fopen(path, "r");
+    if (!f) return SIPF_EINVAL;
+    char line[512];
+    int rc = SIPF_OK;
+    while (fgets(line, sizeof line, f)) {
+        char* hash = strchr(line, '#');
+        if (hash) *hash = 0;
+        TuneEntry e{};
+        long long lo = 0, hi = 0;
+        const int got = sscanf(line, "%d %lld %lld %d %d %d %d", &e.H, &lo, &hi, &e.t.radix_plan,
+                               &e.t.step_blocks_per_sm, &e.t.bucket_slack_div,
+                               &e.t.bucket_slack_add);
+        if (got <= 0) continue;   // blank or comment
+        e.n_min = lo;
+        e.n_max = hi;
+        if (got != 7 || !tuning_valid(e.t) || lo > hi) {
+            rc = SIPF_EINVAL;
+            break;
+        }
+        out->push_back(e);
+    }
+    fclose(f);
+    return rc;
+}
+
+// The table next to the library (sipf_tuning.txt in the directory of
+// libsipf.so), or the file named by SIPF_TUNING, read on first use.
+void load_default_tuning_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    std::string path;
+    if (const char* env = getenv("SIPF_TUNING")) {
+        path = env;
+    } else {
+        Dl_info info;
+        if (dladdr(reinterpret_cast<void*>(&load_default_tuning_locked), &info) && info.dli_fname) {
+            path = info.dli_fname;
+            const size_t slash = path.rfind('/');
+            path = (slash == std::string::npos ? std::string(".") : path.substr(0, slash)) +
+                   "/sipf_tuning.txt";
+        }
+    }
+    std::vector<TuneEntry> t;
+    if (!path.empty() && parse_tuning_file(path.c_str(), &t) == SIPF_OK) g_tune = t;
+}
+
+bool lookup_tuning(int H, int64_t N, sipf_tuning* out) {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    load_default_tuning_locked();
+    for (const TuneEntry& e : g_tune)
+        if (e.H == H && N >= e.n_min && N <= e.n_max) {
+            *out = e.t;
+            return true;
+        }
+    return false;
+}
+
+void apply_tuning(sipf_ctx* c, const sipf_tuning& t) {
+    c->radix_plan = t.radix_plan;
+    c->step_bps = t.step_blocks_per_sm;
+    c->slack_div = t.bucket_slack_div;
+    c->slack_add = t.bucket_slack_add;
+}
+
 bool supported_H(int H) {
     switch (H) {
         case 8: case 16: case 24: case 32: case 48: case 64: case 72: case 96: case 128:
@@ -577,6 +665,8 @@ int create_in_pool(const sipf_grid* grid, int64_t N, const sipf_params* params,
         delete c;
         return SIPF_ECUDA;
     }
+    sipf_tuning tuned;
+    if (lookup_tuning(c->H, N, &tuned)) apply_tuning(c, tuned);
     c->step_blocks = step_grid(c);
     if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -810,6 +900,44 @@ int sipf_cell_start(sipf_ctx* c, int32_t* cell_start, int where) {
     r = copy_out(c, cell_start, c->cell_start, (H3 + 1) * sizeof(int32_t), where);
     if (r != SIPF_OK) return r;
     return check_status(c);
+}
+
+int sipf_set_tuning(sipf_ctx* c, const sipf_tuning* t) {
+    if (!c || !t) return SIPF_EINVAL;
+    if (!tuning_valid(*t)) return fail(c, SIPF_EINVAL, "tuning out of range");
+    // captured step graphs bake in the kernels and launch shapes
+    cudaStreamSynchronize(c->stream);
+    for (const auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
+    apply_tuning(c, *t);
+    c->step_blocks = step_grid(c);
+    return SIPF_OK;
+}
+
+int sipf_get_tuning(const sipf_ctx* c, sipf_tuning* t) {
+    if (!c || !t) return SIPF_EINVAL;
+    t->radix_plan = c->radix_plan;
+    t->step_blocks_per_sm = c->step_bps;
+    t->bucket_slack_div = c->slack_div;
+    t->bucket_slack_add = c->slack_add;
+    return SIPF_OK;
+}
+
+int sipf_tuning_load(const char* path) {
+    std::vector<TuneEntry> t;
+    if (path) {
+        const int r = parse_tuning_file(path, &t);
+        if (r != SIPF_OK) return r;
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune = t;
+    g_tune_loaded = true;
+    return SIPF_OK;
+}
+
+int sipf_tuning_lookup(int32_t H, int64_t N, sipf_tuning* out) {
+    if (!out) return SIPF_EINVAL;
+    return lookup_tuning(H, N, out) ? 1 : 0;
 }
 
 int sipf_canonical_order(sipf_ctx* c, int32_t* cell_start, uint32_t* ids, int where) {
@@ -1154,13 +1282,17 @@ int enqueue_batched_step(sipf_ensemble* e, const double* dt, const RunDesc* d_ru
     const int device = e->members[0]->device;
     for (int H : sizes) {
         std::vector<SpecRun> runs;
+        int plan = 0;   // the radix plan of the size's first member serves the batch
         for (int i = 0; i < n; ++i)
-            if (e->members[i]->H == H)
+            if (e->members[i]->H == H) {
+                if (runs.empty()) plan = e->members[i]->radix_plan;
                 runs.push_back(spec_run(e->members[i], spectral_args(e->members[i], dt[i], 1)));
+            }
         for (size_t b0 = 0; b0 < runs.size() && r == SIPF_OK; b0 += kMaxBatch) {
             const int nb = static_cast<int>(std::min<size_t>(kMaxBatch, runs.size() - b0));
             for (int pass = 0; pass < 3 && r == SIPF_OK; ++pass)
-                r = cuda(launch_spectral_batch(H, runs.data() + b0, nb, pass, device, e->main),
+                r = cuda(launch_spectral_batch(H, runs.data() + b0, nb, pass, plan, device,
+                                               e->main),
                          "batched spectral pass");
         }
     }

@@ -81,13 +81,58 @@ struct DftLevel {
     }
 };
 
+template <int R, int SIGN>
+__device__ __forceinline__ void dft(float2 (&v)[R]);
+
+// a^-1 mod m for coprime a, m (small, at compile time).
+__host__ __device__ constexpr int modinv(int a, int m) {
+    int x = 1;
+    while ((a * x) % m != 1) ++x;
+    return x;
+}
+
+// Prime-factor (Good-Thomas) DFT of length N = N1 N2 with gcd(N1, N2) = 1:
+// the input index n = (N2 n1 + N1 n2) mod N and the output index
+// k = (N2 (N2^-1 mod N1) k1 + N1 (N1^-1 mod N2) k2) mod N turn it into N2
+// DFTs of length N1 followed by N1 DFTs of length N2, with no twiddle
+// factors in between.
+template <int N1, int N2, int SIGN>
+__device__ __forceinline__ void dft_pfa(float2 (&v)[N1 * N2]) {
+    constexpr int N = N1 * N2;
+    constexpr int C1 = N2 * modinv(N2, N1), C2 = N1 * modinv(N1, N2);
+    float2 y[N1][N2];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) {
+        float2 t[N1];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) t[n1] = v[(N2 * n1 + N1 * n2) % N];
+        dft<N1, SIGN>(t);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) y[k1][n2] = t[k1];
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+        float2 t[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) t[n2] = y[k1][n2];
+        dft<N2, SIGN>(t);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) v[(C1 * k1 + C2 * k2) % N] = t[k2];
+    }
+}
+
 // In-register R-point DFT, sign -1 forward, +1 inverse.  R = 2, 4, 8, 16:
 // bit-reversal permutation, then log2 R radix-2 levels (decimation in time).
 // R = 3: X0 = a + b + c, X1 = a - (b + c)/2 + SIGN i (sqrt 3 / 2)(b - c),
-// X2 = a - (b + c)/2 - SIGN i (sqrt 3 / 2)(b - c).
+// X2 = a - (b + c)/2 - SIGN i (sqrt 3 / 2)(b - c).  R = 6 = 2 x 3 and
+// R = 12 = 3 x 4: the prime-factor form above.
 template <int R, int SIGN>
 __device__ __forceinline__ void dft(float2 (&v)[R]) {
-    if constexpr (R == 3) {
+    if constexpr (R == 6) {
+        dft_pfa<2, 3, SIGN>(v);
+    } else if constexpr (R == 12) {
+        dft_pfa<3, 4, SIGN>(v);
+    } else if constexpr (R == 3) {
         constexpr float s3 = 0.86602540378443865f;
         const float2 sum = cadd(v[1], v[2]), dif = csub(v[1], v[2]);
         const float2 mid = make_float2(v[0].x - 0.5f * sum.x, v[0].y - 0.5f * sum.y);
@@ -212,34 +257,54 @@ __device__ __forceinline__ void stage1_from(float2* out, Load load) {
     stage1_from_at<L, R, NTRANS, NT, SIGN>(out, Strided<TS, ES>{}, load);
 }
 
-// Radix plan of a length-L transform: two to four Stockham stages (R3, R4 =
-// 1: fewer).  Lengths are 2^a 3^b with 8 <= L <= 512.
-template <int L> struct Radix;
+// Radix plans of a length-L transform: two to four Stockham stages (R3, R4 =
+// 1: fewer).  Lengths are 2^a 3^b with 8 <= L <= 512.  Plan V = 0 and an
+// alternative V = 1 (fewer stages through the radix-6 and radix-12 DFTs, or
+// the stage order reversed); which one runs is a tuning choice per grid size.
+template <int L, int V = 0> struct Radix;
 template <int A, int B, int C = 1, int D = 1>
 struct RadixPlan { static constexpr int R1 = A, R2 = B, R3 = C, R4 = D; };
-template <> struct Radix<8> : RadixPlan<4, 2> {};
-template <> struct Radix<16> : RadixPlan<4, 4> {};
-template <> struct Radix<24> : RadixPlan<8, 3> {};
-template <> struct Radix<32> : RadixPlan<8, 4> {};
-template <> struct Radix<48> : RadixPlan<16, 3> {};
-template <> struct Radix<64> : RadixPlan<8, 8> {};
-template <> struct Radix<72> : RadixPlan<8, 3, 3> {};
-template <> struct Radix<96> : RadixPlan<8, 4, 3> {};
-template <> struct Radix<128> : RadixPlan<16, 8> {};
-template <> struct Radix<144> : RadixPlan<16, 3, 3> {};
-template <> struct Radix<192> : RadixPlan<16, 4, 3> {};
-template <> struct Radix<216> : RadixPlan<8, 3, 3, 3> {};
-template <> struct Radix<256> : RadixPlan<16, 16> {};
-template <> struct Radix<288> : RadixPlan<16, 3, 3, 2> {};
-template <> struct Radix<384> : RadixPlan<16, 8, 3> {};
-template <> struct Radix<432> : RadixPlan<16, 3, 3, 3> {};
-template <> struct Radix<512> : RadixPlan<8, 8, 8> {};
+template <> struct Radix<8, 0> : RadixPlan<4, 2> {};
+template <> struct Radix<16, 0> : RadixPlan<4, 4> {};
+template <> struct Radix<24, 0> : RadixPlan<8, 3> {};
+template <> struct Radix<32, 0> : RadixPlan<8, 4> {};
+template <> struct Radix<48, 0> : RadixPlan<16, 3> {};
+template <> struct Radix<64, 0> : RadixPlan<8, 8> {};
+template <> struct Radix<72, 0> : RadixPlan<8, 3, 3> {};
+template <> struct Radix<96, 0> : RadixPlan<8, 4, 3> {};
+template <> struct Radix<128, 0> : RadixPlan<16, 8> {};
+template <> struct Radix<144, 0> : RadixPlan<16, 3, 3> {};
+template <> struct Radix<192, 0> : RadixPlan<16, 4, 3> {};
+template <> struct Radix<216, 0> : RadixPlan<8, 3, 3, 3> {};
+template <> struct Radix<256, 0> : RadixPlan<16, 16> {};
+template <> struct Radix<288, 0> : RadixPlan<16, 3, 3, 2> {};
+template <> struct Radix<384, 0> : RadixPlan<16, 8, 3> {};
+template <> struct Radix<432, 0> : RadixPlan<16, 3, 3, 3> {};
+template <> struct Radix<512, 0> : RadixPlan<8, 8, 8> {};
+template <> struct Radix<8, 1> : RadixPlan<2, 4> {};
+template <> struct Radix<16, 1> : RadixPlan<8, 2> {};
+template <> struct Radix<24, 1> : RadixPlan<12, 2> {};
+template <> struct Radix<32, 1> : RadixPlan<4, 8> {};
+template <> struct Radix<48, 1> : RadixPlan<12, 4> {};
+template <> struct Radix<64, 1> : RadixPlan<16, 4> {};
+template <> struct Radix<72, 1> : RadixPlan<12, 6> {};
+template <> struct Radix<96, 1> : RadixPlan<12, 8> {};
+template <> struct Radix<128, 1> : RadixPlan<8, 16> {};
+template <> struct Radix<144, 1> : RadixPlan<12, 12> {};
+template <> struct Radix<192, 1> : RadixPlan<16, 12> {};
+template <> struct Radix<216, 1> : RadixPlan<6, 6, 6> {};
+template <> struct Radix<256, 1> : RadixPlan<8, 8, 4> {};
+template <> struct Radix<288, 1> : RadixPlan<8, 6, 6> {};
+template <> struct Radix<384, 1> : RadixPlan<8, 8, 6> {};
+template <> struct Radix<432, 1> : RadixPlan<12, 6, 6> {};
+template <> struct Radix<512, 1> : RadixPlan<16, 8, 4> {};
 
 // The stages after the first of a batched length-L FFT, the last one into a
 // sink (see stage_sink_at).
-template <int L, int NTRANS, int NT, int SIGN, class At, class Sink>
+template <int L, int V, int NTRANS, int NT, int SIGN, class At, class Sink>
 __device__ __forceinline__ void fft_rest_sink_at(float2* buf, const float2* tw, At at, Sink sink) {
-    constexpr int R1 = Radix<L>::R1, R2 = Radix<L>::R2, R3 = Radix<L>::R3, R4 = Radix<L>::R4;
+    using P = Radix<L, V>;
+    constexpr int R1 = P::R1, R2 = P::R2, R3 = P::R3, R4 = P::R4;
     static_assert(R1 * R2 * R3 * R4 == L, "radix plan");
     if constexpr (R3 == 1) {
         stage_sink_at<L, R2, R1, NTRANS, NT, SIGN>(buf, tw, at, sink);
@@ -254,32 +319,32 @@ __device__ __forceinline__ void fft_rest_sink_at(float2* buf, const float2* tw, 
 }
 
 // The stages after the first, in place.
-template <int L, int NTRANS, int NT, int SIGN, class At>
+template <int L, int V, int NTRANS, int NT, int SIGN, class At>
 __device__ __forceinline__ void fft_rest_at(float2* buf, const float2* tw, At at) {
-    fft_rest_sink_at<L, NTRANS, NT, SIGN>(
+    fft_rest_sink_at<L, V, NTRANS, NT, SIGN>(
         buf, tw, at, [=](int t, int p, float2 v) { buf[at(t, p)] = v; });
 }
 
-template <int L, int NTRANS, int ES, int TS, int NT, int SIGN>
+template <int L, int V, int NTRANS, int ES, int TS, int NT, int SIGN>
 __device__ __forceinline__ void fft_rest(float2* buf, const float2* tw) {
-    fft_rest_at<L, NTRANS, NT, SIGN>(buf, tw, Strided<TS, ES>{});
+    fft_rest_at<L, V, NTRANS, NT, SIGN>(buf, tw, Strided<TS, ES>{});
 }
 
-template <int L, int NTRANS, int ES, int TS, int NT, int SIGN, class Sink>
+template <int L, int V, int NTRANS, int ES, int TS, int NT, int SIGN, class Sink>
 __device__ __forceinline__ void fft_rest_sink(float2* buf, const float2* tw, Sink sink) {
-    fft_rest_sink_at<L, NTRANS, NT, SIGN>(buf, tw, Strided<TS, ES>{}, sink);
+    fft_rest_sink_at<L, V, NTRANS, NT, SIGN>(buf, tw, Strided<TS, ES>{}, sink);
 }
 
-// Batched length-L FFT along one axis, in place.
-template <int L, int NTRANS, int NT, int SIGN, class At>
+// Batched length-L FFT along one axis, in place (radix plan V).
+template <int L, int V, int NTRANS, int NT, int SIGN, class At>
 __device__ __forceinline__ void fft_axis_at(float2* buf, const float2* tw, At at) {
-    stage_at<L, Radix<L>::R1, 1, NTRANS, NT, SIGN>(buf, tw, at);
-    fft_rest_at<L, NTRANS, NT, SIGN>(buf, tw, at);
+    stage_at<L, Radix<L, V>::R1, 1, NTRANS, NT, SIGN>(buf, tw, at);
+    fft_rest_at<L, V, NTRANS, NT, SIGN>(buf, tw, at);
 }
 
-template <int L, int NTRANS, int ES, int TS, int NT, int SIGN>
+template <int L, int V, int NTRANS, int ES, int TS, int NT, int SIGN>
 __device__ __forceinline__ void fft_axis(float2* buf, const float2* tw) {
-    fft_axis_at<L, NTRANS, NT, SIGN>(buf, tw, Strided<TS, ES>{});
+    fft_axis_at<L, V, NTRANS, NT, SIGN>(buf, tw, Strided<TS, ES>{});
 }
 
 }  // namespace fftk

@@ -700,15 +700,17 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* smem, int* total
 // (tile buckets split into kItem chunks, then the overflow region) with
 // their offsets in the compacted particle order; and, when next_cnt is not
 // null, the bucket layout of the other buffer for the next step (capacity
-// count + count/8 + 32, rounded up to a multiple of 4) with its counters
-// reset; with next_sc, the next step's scalars from those of this step.
+// count + count/slack_div + slack_add, rounded up to a multiple of 4; the
+// context's buffers hold at least slack_div = 8, slack_add = 32) with its
+// counters reset; with next_sc, the next step's scalars from those of this
+// step.
 __device__ __forceinline__ void plan_body(
     int ntiles, int T, const int* __restrict__ cnt, const int* __restrict__ cap,
     const int* __restrict__ bstart, const int* __restrict__ ovf, int ovf_base, Item* items,
     int* n_items, int* next_bstart, int* next_cap, int* next_cnt, int* next_ovf,
     int* __restrict__ status, const StepScalars* __restrict__ cur_sc,
     StepScalars* __restrict__ next_sc, double dt, double log2_maxrel, double exp_logref,
-    double h3) {
+    double h3, int slack_div, int slack_add) {
     __shared__ int smem[33];
     const int per = (ntiles + kPlanNT - 1) / kPlanNT;
     const int t0 = threadIdx.x * per;
@@ -720,7 +722,7 @@ __device__ __forceinline__ void plan_body(
         const int f = min(c, cap[t]);
         my_items += (f + kItem - 1) / kItem;
         my_fill += f;
-        if (next_cnt) my_cap += ((c + c / 8 + 32) + 3) & ~3;
+        if (next_cnt) my_cap += ((c + c / slack_div + slack_add) + 3) & ~3;
     }
     int tot_items, tot_fill, tot_cap;
     int item0 = block_exclusive_scan(my_items, smem, &tot_items);
@@ -745,7 +747,7 @@ __device__ __forceinline__ void plan_body(
         }
         out0 += f;
         if (next_cnt) {
-            const int cp = ((c + c / 8 + 32) + 3) & ~3;
+            const int cp = ((c + c / slack_div + slack_add) + 3) & ~3;
             next_bstart[t] = cap0;
             next_cap[t] = cp;
             next_cnt[t] = 0;
@@ -780,9 +782,10 @@ __global__ void __launch_bounds__(kPlanNT)
            int* n_items, int* next_bstart, int* next_cap, int* next_cnt, int* next_ovf,
            int* __restrict__ status, const StepScalars* __restrict__ cur_sc,
            StepScalars* __restrict__ next_sc, double dt, double log2_maxrel, double exp_logref,
-           double h3) {
+           double h3, int slack_div, int slack_add) {
     plan_body(ntiles, T, cnt, cap, bstart, ovf, ovf_base, items, n_items, next_bstart, next_cap,
-              next_cnt, next_ovf, status, cur_sc, next_sc, dt, log2_maxrel, exp_logref, h3);
+              next_cnt, next_ovf, status, cur_sc, next_sc, dt, log2_maxrel, exp_logref, h3,
+              slack_div, slack_add);
 }
 
 // The plan of every run of an ensemble after a batched step from buffer
@@ -794,7 +797,7 @@ __global__ void __launch_bounds__(kPlanNT) k_plan_multi(const RunDesc* __restric
     const int b = parity ^ 1, o = parity;
     plan_body(d.ntiles, d.H / 8, d.cnt[b], d.cap[b], d.bstart[b], d.ovf[b], d.ovf_base, d.items,
               d.n_items, d.bstart[o], d.cap[o], d.cnt[o], d.ovf[o], d.status, d.dsc + o,
-              d.dsc + b, d.dt, d.log2_maxrel, d.exp_logref, d.h3);
+              d.dsc + b, d.dt, d.log2_maxrel, d.exp_logref, d.h3, d.slack_div, d.slack_add);
 }
 
 // One persistent launch over the items of all runs of an ensemble (all
@@ -1238,6 +1241,8 @@ int step_grid(sipf_ctx* c) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<4>, kNT, 0);
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<2>, kNT, 0);
+    // a tuning may ask for fewer blocks per SM than the occupancy limit
+    if (c->step_bps > 0 && c->step_bps < per_sm) per_sm = c->step_bps;
     int g = nsm * (per_sm > 0 ? per_sm : 1);
     // no more blocks than items can exist: a small run leaves the rest of the
     // GPU to the runs beside it
@@ -1264,7 +1269,8 @@ cudaError_t launch_plan(sipf_ctx* c, int b, int next_layout, cudaStream_t s, dou
         next_layout ? c->cap[o] : nullptr, next_layout ? c->cnt[o] : nullptr,
         next_layout ? c->ovf[o] : nullptr, c->status,
         // b is the buffer the step just wrote: its slot is the next step's, o's the current one
-        c->dsc + o, dt > 0.0 ? c->dsc + b : nullptr, dt, c->log2_maxrel, c->exp_logref, c->h3);
+        c->dsc + o, dt > 0.0 ? c->dsc + b : nullptr, dt, c->log2_maxrel, c->exp_logref, c->h3,
+        c->slack_div, c->slack_add);
     return cudaGetLastError();
 }
 
@@ -1316,6 +1322,8 @@ RunDesc run_desc(const sipf_ctx* c, double dt) {
     d.log2_maxrel = c->log2_maxrel;
     d.exp_logref = c->exp_logref;
     d.h3 = c->h3;
+    d.slack_div = c->slack_div;
+    d.slack_add = c->slack_add;
     return d;
 }
 

@@ -185,6 +185,7 @@ struct RunDesc {
     int* status;
     StepScalars* dsc;                   // [2], slot = parity of the source buffer
     double dt, log2_maxrel, exp_logref, h3;
+    int slack_div, slack_add;           // bucket capacity count + count/slack_div + slack_add
 };
 constexpr int kMaxRuns = 256;           // runs of one batched particle launch
 template <int NB> struct SpecBatch {
@@ -204,6 +205,12 @@ struct sipf_ctx {
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_join = nullptr;
     int device = 0;
+    // tuning choices (sipf_set_tuning): radix plan of the spectral passes,
+    // particle-step blocks per SM (0: occupancy limit), bucket slack
+    int radix_plan = 0;
+    int step_bps = 0;
+    int slack_div = 8;
+    int slack_add = 32;
     cudaMemPool_t pool = nullptr;        // stream-ordered allocation from this pool (null: cudaMalloc)
 
     // particle store, ping-pong; positions in grid units, log-mass relative
@@ -343,8 +350,8 @@ cudaError_t launch_spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass);
 SpecRun spec_run(const sipf_ctx* c, const SpectralArgs& a);
 // One fused spectral pass (0 forward, 1 z, 2 inverse) over n <= kMaxBatch
 // runs of grid size H <= 128, in one launch.
-cudaError_t launch_spectral_batch(int H, const SpecRun* runs, int n, int pass, int device,
-                                  cudaStream_t s);
+cudaError_t launch_spectral_batch(int H, const SpecRun* runs, int n, int pass, int plan,
+                                  int device, cudaStream_t s);
 void fill_twiddles(int H, float2* host_out);
 
 }  // namespace sipf

@@ -62,14 +62,14 @@ __global__ void __launch_bounds__(smooth_threads<H, kPairsX>())
         buf[t * RP + x] = make_float2(plane[y * H + x], plane[(y + 1) * H + x]);
     }
     __syncthreads();
-    fft_axis<H, P, 1, RP, kSmNT, -1>(buf, tw);
+    fft_axis<H, 0, P, 1, RP, kSmNT, -1>(buf, tw);
     for (int q = threadIdx.x; q < P * H; q += kSmNT) {
         const int t = q / H, j = q % H;
         const float2 e = buf[t * RP + j];
         buf[t * RP + j] = make_float2(e.x * gs[j], e.y * gs[j]);
     }
     __syncthreads();
-    fft_axis<H, P, 1, RP, kSmNT, +1>(buf, tw);
+    fft_axis<H, 0, P, 1, RP, kSmNT, +1>(buf, tw);
     for (int q = threadIdx.x; q < P * H; q += kSmNT) {
         const int t = q / H, x = q % H, y = 2 * (p0 + t);
         const float2 e = buf[t * RP + x];
@@ -104,14 +104,14 @@ __global__ void __launch_bounds__(smooth_threads<H, kPairsYZ>())
                                 : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    fft_axis<H, P, PP, 1, kSmNT, -1>(buf, tw);
+    fft_axis<H, 0, P, PP, 1, kSmNT, -1>(buf, tw);
     for (int q = threadIdx.x; q < H * P; q += kSmNT) {
         const int j = q / P, t = q % P;
         const float2 e = buf[j * PP + t];
         buf[j * PP + t] = make_float2(e.x * gs[j], e.y * gs[j]);
     }
     __syncthreads();
-    fft_axis<H, P, PP, 1, kSmNT, +1>(buf, tw);
+    fft_axis<H, 0, P, PP, 1, kSmNT, +1>(buf, tw);
     for (int q = threadIdx.x; q < H * P; q += kSmNT) {
         const int j = q / P, t = q % P, x = x0 + 2 * t;
         if (x < H) *reinterpret_cast<float2*>(u + at(j, x)) = buf[j * PP + t];

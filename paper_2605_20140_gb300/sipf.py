@@ -45,7 +45,8 @@ EXPORTED = (
     "sipf_server_submit", "sipf_server_advance", "sipf_server_poll", "sipf_server_collect",
     "sipf_server_stats", "sipf_server_last_error", "sipf_server_destroy",
     "sipf_server_set_limit", "sipf_server_fail_next_admission", "sipf_canonical_order",
-    "sipf_ensemble_set_mode", "sipf_ensemble_last_path",
+    "sipf_ensemble_set_mode", "sipf_ensemble_last_path", "sipf_set_tuning", "sipf_get_tuning",
+    "sipf_tuning_load", "sipf_tuning_lookup",
 )
 PROFILE_GROUPS = 4
 
@@ -61,6 +62,11 @@ class sipf_params(ctypes.Structure):
                 ("v_update", ctypes.c_int32), ("H0", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("p2g_order", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("sigma", ctypes.c_double)]
+
+
+class sipf_tuning(ctypes.Structure):
+    _fields_ = [("radix_plan", ctypes.c_int32), ("step_blocks_per_sm", ctypes.c_int32),
+                ("bucket_slack_div", ctypes.c_int32), ("bucket_slack_add", ctypes.c_int32)]
 
 
 class sipf_diag(ctypes.Structure):
@@ -120,6 +126,10 @@ def load() -> ctypes.CDLL:
         "sipf_ensemble_last_error": ([P], ctypes.c_char_p),
         "sipf_ensemble_destroy": ([P], None),
         "sipf_ensemble_set_mode": ([P, I32], I32),
+        "sipf_set_tuning": ([P, ctypes.POINTER(sipf_tuning)], I32),
+        "sipf_get_tuning": ([P, ctypes.POINTER(sipf_tuning)], I32),
+        "sipf_tuning_load": ([ctypes.c_char_p], I32),
+        "sipf_tuning_lookup": ([I32, I64, ctypes.POINTER(sipf_tuning)], I32),
         "sipf_ensemble_last_path": ([P], I32),
         "sipf_context_bytes": ([ctypes.POINTER(sipf_grid), I64, ctypes.POINTER(sipf_params)], I64),
         "sipf_device_bytes": ([P], I64),
@@ -212,6 +222,31 @@ def sipf_cell_start(ctx, dst, where=SIPF_HOST):
 
 def sipf_canonical_order(ctx, cell_start=None, ids=None, where=SIPF_HOST):
     _check(load().sipf_canonical_order(ctx, _ptr(cell_start), _ptr(ids), where), ctx)
+
+
+def sipf_set_tuning(ctx, radix_plan=0, step_blocks_per_sm=0, bucket_slack_div=8,
+                    bucket_slack_add=32):
+    t = sipf_tuning(radix_plan, step_blocks_per_sm, bucket_slack_div, bucket_slack_add)
+    _check(load().sipf_set_tuning(ctx, ctypes.byref(t)), ctx)
+
+
+def sipf_get_tuning(ctx) -> dict:
+    t = sipf_tuning()
+    _check(load().sipf_get_tuning(ctx, ctypes.byref(t)), ctx)
+    return {k: getattr(t, k) for k, _ in sipf_tuning._fields_}
+
+
+def sipf_tuning_load(path):
+    _check(load().sipf_tuning_load(None if path is None else str(path).encode()))
+
+
+def sipf_tuning_lookup(H: int, N: int):
+    """The table's tuning for (H, N) as a dict, or None."""
+    t = sipf_tuning()
+    found = load().sipf_tuning_lookup(int(H), int(N), ctypes.byref(t))
+    if found < 0:
+        _check(found)
+    return {k: getattr(t, k) for k, _ in sipf_tuning._fields_} if found == 1 else None
 
 
 def sipf_diagnostics(ctx) -> dict:
@@ -357,6 +392,7 @@ class Simulation:
 
     def __init__(self, H, L, origin, N, params, stream: int = 0, _ctx=None):
         self.H, self.L, self.N = H, L, N
+        self.stream = stream
         self.ctx = _ctx if _ctx is not None else sipf_create(make_grid(H, L, origin), N,
                                                              make_params(params), stream)
 

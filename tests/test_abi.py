@@ -191,3 +191,38 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         sipf.load()
     with pytest.raises(RuntimeError, match="missing"):
         sipf.Simulation(16, 1.0, (0.0, 0.0, 0.0), 64, Params())
+
+
+def test_tuning_table_is_parsed_and_looked_up(lib, tmp_path):
+    """The autotuner's table (host only): the first line matching (H, N)
+    applies; malformed or out-of-range lines are refused; NULL empties it."""
+    good = tmp_path / "t.txt"
+    good.write_text("# comment\n128 1000 5000000 1 4 16 16   # ms\n\n96 1 999 0 0 32 8\n"
+                    "128 1 999 0 3 8 32\n")
+    sipf.sipf_tuning_load(good)
+    assert sipf.sipf_tuning_lookup(128, 4194304) == {
+        "radix_plan": 1, "step_blocks_per_sm": 4, "bucket_slack_div": 16, "bucket_slack_add": 16}
+    assert sipf.sipf_tuning_lookup(128, 500)["step_blocks_per_sm"] == 3
+    assert sipf.sipf_tuning_lookup(96, 1000) is None
+    assert sipf.sipf_tuning_lookup(64, 10) is None
+    for text in ("128 1 10 2 0 8 32\n", "128 1 10 0 0 4 32\n", "128 1 10 0 0 8 64\n",
+                 "128 10 1 0 0 8 32\n", "128 1 10 0\n"):
+        bad = tmp_path / "bad.txt"
+        bad.write_text(text)
+        with pytest.raises(sipf.SipfError):
+            sipf.sipf_tuning_load(bad)
+    with pytest.raises(sipf.SipfError):
+        sipf.sipf_tuning_load(tmp_path / "missing.txt")
+    sipf.sipf_tuning_load(None)
+    assert sipf.sipf_tuning_lookup(128, 4194304) is None
+
+
+def test_autotuner_candidates_are_valid():
+    from paper_2605_20140_gb300 import autotune
+    cands = autotune.candidates()
+    assert len(cands) == len({tuple(sorted(c.items())) for c in cands}) >= 12
+    for c in cands:
+        assert c["radix_plan"] in (0, 1) and 0 <= c["step_blocks_per_sm"] <= 32
+        assert 8 <= c["bucket_slack_div"] <= 1024 and 0 <= c["bucket_slack_add"] <= 32
+    for H, lo, hi, rep, recipe in autotune.TARGETS:
+        assert lo <= rep <= hi and recipe in ("headline", "large")

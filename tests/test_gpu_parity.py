@@ -55,8 +55,12 @@ def _library():
     sipf.load()
 
 
-def run_gpu(wl, steps, p=None, x=None, mass=None, v=None, m=None, w=None, dt=None):
+def run_gpu(wl, steps, p=None, x=None, mass=None, v=None, m=None, w=None, dt=None, plan=None):
     sim = sipf.Simulation(wl.H, wl.L, wl.origin, wl.N, p or wl.params)
+    if plan is not None:
+        t = sipf.sipf_get_tuning(sim.ctx)
+        t["radix_plan"] = plan
+        sipf.sipf_set_tuning(sim.ctx, **t)
     sim.set_state(wl.x if x is None else x, wl.mass if mass is None else mass, wl.ids,
                   wl.v if v is None else v, wl.m if m is None else m, wl.w if w is None else w)
     if steps:
@@ -245,10 +249,14 @@ def test_fourth_order_deposit_matches_oracle(name, H, N):
         assert u.min() < 0       # the negative star weights survive the integer path
 
 
+@pytest.mark.parametrize("plan", [0, 1])
 @pytest.mark.parametrize("H", [8, 16, 24, 32, 48, 64, 72, 96, 128, 144, 192, 216, 256])
-def test_initial_spectral_gradient(H):
+def test_initial_spectral_gradient(H, plan):
+    """grad v^(0) against the oracle's spectral gradient, with either radix
+    plan of the transforms (plan 1: the radix-6 and radix-12 stages, or the
+    stage order reversed)."""
     wl = workload("small", H=H, N=1024)
-    sim = run_gpu(wl, 0)
+    sim = run_gpu(wl, 0, plan=plan)
     f = sim.fields(sipf.FIELD_GX | sipf.FIELD_GY | sipf.FIELD_GZ)
     sim.close()
     g = O.spectral_gradient(wl.v.astype(np.float64), wl.L)
@@ -274,9 +282,10 @@ def test_gradient_of_a_sine_mode_closed_form():
         assert np.max(np.abs(f[name] - ref)) <= 1e-5 * np.abs(ref).max(), name
 
 
+@pytest.mark.parametrize("plan", [0, 1])
 @pytest.mark.parametrize("mode,H", [(0, 32), (1, 32), (0, 256), (0, 48), (1, 72), (0, 96),
                                     (0, 144), (1, 192)])
-def test_single_mode_decay(mode, H):
+def test_single_mode_decay(mode, H, plan):
     """Massless particles, gamma = alpha = 0: one step multiplies a Fourier
     mode of m by 1/(1 + tau beta + tau Dm |k|^2) (or the exponential) and of
     w by 1/(1 + tau + tau Dw |k|^2)."""
@@ -288,7 +297,8 @@ def test_single_mode_decay(mode, H):
     mf = np.cos(2 * np.pi * (qv[0] * X + qv[1] * Y + qv[2] * Z) / L)
     wl = workload("small", H=H, N=256)
     sim = run_gpu(wl, 3, p=p, mass=np.zeros(256), m=(1.5 * mf).astype(np.float32),
-                  w=(0.25 * mf).astype(np.float32), v=np.ones((H, H, H), np.float32), dt=tau)
+                  w=(0.25 * mf).astype(np.float32), v=np.ones((H, H, H), np.float32), dt=tau,
+                  plan=plan)
     f = sim.fields(sipf.FIELD_M | sipf.FIELD_W | sipf.FIELD_V | sipf.FIELD_U)
     sim.close()
     k2 = (2 * np.pi / L) ** 2 * np.sum(qv ** 2)
@@ -331,11 +341,13 @@ def test_hundred_steps_match_oracle_small_workload():
     print("rel-L2 after 100 steps:", {k: f"{v:.2e}" for k, v in errs.items()})
 
 
+@pytest.mark.parametrize("plan", [0, 1])
 @pytest.mark.parametrize("H", [24, 48, 96])
-def test_steps_match_oracle_radix3_grids(H):
-    """Grids 2^a 3^b (radix-3 DFT stages): ten steps against the oracle."""
+def test_steps_match_oracle_radix3_grids(H, plan):
+    """Grids 2^a 3^b (radix-3 DFT stages, or with plan 1 the radix-6 and
+    radix-12 ones): ten steps against the oracle."""
     wl = workload("small", H=H, N=1 << 15)
-    sim = run_gpu(wl, 10)
+    sim = run_gpu(wl, 10, plan=plan)
     st = O.run(oracle_state(wl), wl.dt, 10)
     compare(sim, st, wl)
     sim.close()
@@ -656,8 +668,10 @@ def _plane_wave(H, L, qv):
     return np.cos(ph).astype(np.float32), np.sin(ph).astype(np.float32)
 
 
-@pytest.mark.parametrize("H,mode", [(216, 0), (288, 1), (384, 0), (432, 1), (512, 0)])
-def test_large_grids_single_mode_decay_and_gradient(H, mode):
+@pytest.mark.parametrize("H,mode,plan", [(216, 0, 0), (288, 1, 0), (384, 0, 0), (432, 1, 0),
+                                         (512, 0, 0), (216, 1, 1), (288, 0, 1), (384, 1, 1),
+                                         (432, 0, 1), (512, 1, 1)])
+def test_large_grids_single_mode_decay_and_gradient(H, mode, plan):
     """Grids above 256 (four-stage radix plans, per-axis pipeline): the
     spectral gradient of a plane wave and its decay over two steps against
     the closed forms (massless particles, gamma = alpha = 0).
@@ -675,6 +689,9 @@ def test_large_grids_single_mode_decay_and_gradient(H, mode):
     x = rng.random((256, 3)).astype(np.float32)
     v = (1.0 + 0.3 * sw).astype(np.float32)
     sim = sipf.Simulation(H, L, (0.0, 0.0, 0.0), 256, p)
+    t = sipf.sipf_get_tuning(sim.ctx)
+    t["radix_plan"] = plan
+    sipf.sipf_set_tuning(sim.ctx, **t)
     sim.set_state(x, np.zeros(256), None, v, (1.5 * cw).astype(np.float32),
                   (0.25 * cw).astype(np.float32))
     g = sim.fields(sipf.FIELD_GX | sipf.FIELD_GY | sipf.FIELD_GZ)
@@ -763,3 +780,36 @@ def test_non_finite_field_is_reported_and_the_context_recovers():
     d = sim.diagnostics()
     assert d["nonfinite"] == 0 and d["step"] == 2
     sim.close()
+
+
+def test_tuning_of_slack_and_blocks_leaves_results_bit_identical():
+    """Bucket slack and particle-step blocks per SM change where particles sit
+    (tile buckets or the overflow region) and which block steps them, never
+    the arithmetic: ten steps give bit-identical fields, positions and
+    log-masses; the radix plans agree to float32 rounding."""
+    wl = workload("headline", H=64, N=1 << 17)
+    stream = torch.cuda.Stream()
+
+    def run(**t):
+        sim = sipf.Simulation(wl.H, wl.L, wl.origin, wl.N, wl.params, stream=stream.cuda_stream)
+        if t:
+            sipf.sipf_set_tuning(sim.ctx, **t)
+            assert sipf.sipf_get_tuning(sim.ctx) == t
+        sim.set_state(wl.x, wl.mass, wl.ids, wl.v, wl.m, wl.w)
+        sim.step(wl.dt, 10)
+        f = sim.fields()
+        s_, l_, i_ = by_id(*sim.particle_state())
+        sim.close()
+        return f, s_, l_
+
+    base = run(radix_plan=0, step_blocks_per_sm=0, bucket_slack_div=8, bucket_slack_add=32)
+    for t in (dict(radix_plan=0, step_blocks_per_sm=3, bucket_slack_div=32, bucket_slack_add=8),
+              dict(radix_plan=0, step_blocks_per_sm=1, bucket_slack_div=1024, bucket_slack_add=0)):
+        f, s_, l_ = run(**t)
+        for k in base[0]:
+            np.testing.assert_array_equal(f[k], base[0][k], err_msg=f"{t} {k}")
+        np.testing.assert_array_equal(s_, base[1])
+        np.testing.assert_array_equal(l_, base[2])
+    f, _, _ = run(radix_plan=1, step_blocks_per_sm=0, bucket_slack_div=8, bucket_slack_add=32)
+    for k in ("v", "m", "w"):
+        assert rel_l2(f[k], base[0][k].astype(np.float64)) <= 1e-6, k
