@@ -402,17 +402,6 @@ const char* sipf_last_error(const sipf_ctx* ctx);
 int sipf_brownian_normals(const uint32_t* ids, int64_t N, uint32_t n, uint64_t seed,
                           float* z, uint32_t* bits, void* stream);
 
-/* Self-check of the integer-arithmetic float<->double conversions the step
- * kernel uses instead of the FP64 pipe: for each i < n compares the
- * conversion of f[i] to double and of d[i] to float (round to nearest even)
- * with the hardware conversions, bit for bit; mismatches[0] and
- * mismatches[1] (device int32) receive the two mismatch counts.  f, d and
- * mismatches are device pointers; synchronises `stream`.  Errors:
- * SIPF_EINVAL, SIPF_ECUDA.  (Not an operation of the paper: it checks this
- * implementation.) */
-int sipf_check_conversions(const float* f, const double* d, int64_t n, int32_t* mismatches,
-                           void* stream);
-
 /* Tracing.  sipf_profile(ctx, 1) starts recording CUDA events (on the
  * context's stream) between the kernel groups of each subsequent step, for
  * at most 4096 steps; sipf_profile(ctx, 0) stops; enabling again clears the

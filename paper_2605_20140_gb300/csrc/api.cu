@@ -1592,17 +1592,6 @@ const char* sipf_profile_name(int k) {
     return (k >= 0 && k < kProfGroups) ? names[k] : "";
 }
 
-int sipf_check_conversions(const float* f, const double* d, int64_t n, int32_t* mismatches,
-                           void* stream) {
-    if (!f || !d || !mismatches || n < 1 || n >= (int64_t{1} << 31)) return SIPF_EINVAL;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (cudaMemsetAsync(mismatches, 0, 2 * sizeof(int32_t), s) != cudaSuccess) return SIPF_ECUDA;
-    if (launch_conv_check(f, d, static_cast<int>(n), mismatches, s) != cudaSuccess)
-        return SIPF_ECUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return SIPF_ECUDA;
-    return SIPF_OK;
-}
-
 int sipf_brownian_normals(const uint32_t* ids, int64_t N, uint32_t n, uint64_t seed, float* z,
                           uint32_t* bits, void* stream) {
     if (!ids || !z || N < 1 || N >= (int64_t{1} << 31)) return SIPF_EINVAL;

@@ -135,54 +135,43 @@ __device__ __forceinline__ float3 brownian(uint32_t id, uint32_t n, uint32_t k0,
     return box_muller(b);
 }
 
-// ------------------------------------------------------------------ float <-> double by bits
-// The exact IEEE conversions, done with integer operations so that they do
-// not occupy the (narrow) FP64 pipe.  Zeros, subnormals, infinities and NaN
-// take the hardware conversion.
-__device__ __forceinline__ double f2d_bits(float f) {
-    const uint32_t u = __float_as_uint(f);
-    const uint32_t e = (u >> 23) & 0xFFu;
-    if (e == 0u || e == 0xFFu) return static_cast<double>(f);
-    const uint32_t hi = (u & 0x80000000u) | ((e + (1023u - 127u)) << 20) | ((u & 0x7FFFFFu) >> 3);
-    const uint32_t lo = u << 29;
-    return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
-}
-
-// Round to nearest, ties to even.
-__device__ __forceinline__ float d2f_bits(double d) {
-    const uint32_t hi = static_cast<uint32_t>(__double2hiint(d));
-    const uint32_t lo = static_cast<uint32_t>(__double2loint(d));
-    const int e = static_cast<int>((hi >> 20) & 0x7FFu) - 1023 + 127;
-    if (e < 1 || e > 254) return __double2float_rn(d);
-    uint32_t m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);     // 23 mantissa bits
-    const uint32_t rem = lo & 0x1FFFFFFFu;                  // 29 dropped bits
-    uint32_t bits = (hi & 0x80000000u) | (static_cast<uint32_t>(e) << 23) | m;
-    if (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) bits += 1u;   // carries into e
-    if (((bits >> 23) & 0xFFu) == 0xFFu) return __double2float_rn(d);
-    return __uint_as_float(bits);
-}
-
 // ------------------------------------------------------------------ cells
 struct Cell {
     int cx, cy, cz;      // cell of the particle
     float fx, fy, fz;    // fractional position in the cell
 };
 
-// Positions are in [0, H).  For 0 <= s < 2^23, 2^23 + s rounded toward zero
-// is 2^23 + floor(s): its low mantissa bits are the cell and subtracting
-// 2^23 gives floor(s) as a float, both exact (no conversion instructions).
-// The cell is clamped to [0, H) whatever s is.
+// Positions are in [0, H): every position a buffer holds went through the
+// periodic wrap (non-finite values become 0).  For 0 <= s < 2^23, 2^23 + s
+// rounded toward zero is 2^23 + floor(s): its low mantissa bits are the cell
+// and subtracting 2^23 gives floor(s) as a float, both exact (no conversion
+// instructions).  The paths that index global memory by the cell clamp it
+// (clamp_cell); the tile paths check the cell against the tile.
 __device__ __forceinline__ void split_cell(float s, int H, int& cell, float& frac) {
     const float t = __fadd_rz(s, 8388608.0f);
-    cell = min(max(static_cast<int>(__float_as_uint(t) - 0x4B000000u), 0), H - 1);
+    cell = static_cast<int>(__float_as_uint(t) - 0x4B000000u);
     frac = __fsub_rn(s, __fsub_rn(t, 8388608.0f));
 }
+
+__device__ __forceinline__ int clamp_cell(int c, int H) { return min(max(c, 0), H - 1); }
+
+// The cell with its indices clamped to [0, H) (for kernels that index
+// per-cell or per-tile arrays by it).
+__device__ __forceinline__ Cell locate_clamped(float x, float y, float z, int H);
 
 __device__ __forceinline__ Cell locate(float x, float y, float z, int H) {
     Cell c;
     split_cell(x, H, c.cx, c.fx);
     split_cell(y, H, c.cy, c.fy);
     split_cell(z, H, c.cz, c.fz);
+    return c;
+}
+
+__device__ __forceinline__ Cell locate_clamped(float x, float y, float z, int H) {
+    Cell c = locate(x, y, z, H);
+    c.cx = clamp_cell(c.cx, H);
+    c.cy = clamp_cell(c.cy, H);
+    c.cz = clamp_cell(c.cz, H);
     return c;
 }
 
@@ -207,15 +196,16 @@ __device__ __forceinline__ uint32_t cell_key(int cx, int cy, int cz, int T) {
 // Trilinear interpolation of the float4 field (dv/dx, dv/dy, dv/dz, w)
 // (K_h = h^3 R_h, Alg. 2): along x, then y, then z, with explicit rounding.
 __device__ __forceinline__ float4 gather4(const float4* __restrict__ G, const Cell& c, int H) {
-    const int x1 = c.cx + 1 < H ? c.cx + 1 : 0;
-    const int y1 = c.cy + 1 < H ? c.cy + 1 : 0;
-    const int z1 = c.cz + 1 < H ? c.cz + 1 : 0;
-    const int r00 = (c.cz * H + c.cy) * H, r10 = (c.cz * H + y1) * H;
-    const int r01 = (z1 * H + c.cy) * H, r11 = (z1 * H + y1) * H;
-    const float4 a000 = __ldg(G + r00 + c.cx), a100 = __ldg(G + r00 + x1);
-    const float4 a010 = __ldg(G + r10 + c.cx), a110 = __ldg(G + r10 + x1);
-    const float4 a001 = __ldg(G + r01 + c.cx), a101 = __ldg(G + r01 + x1);
-    const float4 a011 = __ldg(G + r11 + c.cx), a111 = __ldg(G + r11 + x1);
+    const int cx = clamp_cell(c.cx, H), cy = clamp_cell(c.cy, H), cz = clamp_cell(c.cz, H);
+    const int x1 = cx + 1 < H ? cx + 1 : 0;
+    const int y1 = cy + 1 < H ? cy + 1 : 0;
+    const int z1 = cz + 1 < H ? cz + 1 : 0;
+    const int r00 = (cz * H + cy) * H, r10 = (cz * H + y1) * H;
+    const int r01 = (z1 * H + cy) * H, r11 = (z1 * H + y1) * H;
+    const float4 a000 = __ldg(G + r00 + cx), a100 = __ldg(G + r00 + x1);
+    const float4 a010 = __ldg(G + r10 + cx), a110 = __ldg(G + r10 + x1);
+    const float4 a001 = __ldg(G + r01 + cx), a101 = __ldg(G + r01 + x1);
+    const float4 a011 = __ldg(G + r11 + cx), a111 = __ldg(G + r11 + x1);
     const float wx0 = __fsub_rn(1.0f, c.fx), wy0 = __fsub_rn(1.0f, c.fy),
                 wz0 = __fsub_rn(1.0f, c.fz);
 #define SIPF_TRI(f)                                                                      \
@@ -501,7 +491,8 @@ __device__ __forceinline__ void step_items(const StepView& v, const Keys& keys, 
                 const float wz0 = __fsub_rn(1.0f, c.fz);
                 if constexpr (ORDER == 2) {
                     const float ea = exp2_approx(
-                        fminf(__fmaf_rn(d2f_bits(pl), 1.4426950408889634f, dshift), kMaxLog2Unit));
+                        fminf(__fmaf_rn(__double2float_rn(pl), 1.4426950408889634f, dshift),
+                              kMaxLog2Unit));
                     const float e0 = __fmul_rn(ea, wz0), e1 = __fmul_rn(ea, c.fz);
                     const float xy[4] = {__fmul_rn(wx0, wy0), __fmul_rn(c.fx, wy0),
                                          __fmul_rn(wx0, c.fy), __fmul_rn(c.fx, c.fy)};
@@ -519,13 +510,15 @@ __device__ __forceinline__ void step_items(const StepView& v, const Keys& keys, 
                         for (int k = 0; k < 8; ++k)
                             atomicAdd(depu + (k & 1) + ((k >> 1) & 1) * 9 + (k >> 2) * 81, q[k]);
                     } else {
-                        const int x1 = c.cx + 1 < H ? c.cx + 1 : 0;
-                        const int y1 = c.cy + 1 < H ? c.cy + 1 : 0;
-                        const int z1 = c.cz + 1 < H ? c.cz + 1 : 0;
+                        const int cx = clamp_cell(c.cx, H), cy = clamp_cell(c.cy, H);
+                        const int cz = clamp_cell(c.cz, H);
+                        const int x1 = cx + 1 < H ? cx + 1 : 0;
+                        const int y1 = cy + 1 < H ? cy + 1 : 0;
+                        const int z1 = cz + 1 < H ? cz + 1 : 0;
 #pragma unroll
                         for (int k = 0; k < 8; ++k) {
-                            const int nx = (k & 1) ? x1 : c.cx, ny = ((k >> 1) & 1) ? y1 : c.cy;
-                            const int nz = (k >> 2) ? z1 : c.cz;
+                            const int nx = (k & 1) ? x1 : cx, ny = ((k >> 1) & 1) ? y1 : cy;
+                            const int nz = (k >> 2) ? z1 : cz;
                             if (q[k])
                                 atomicAdd(acc + (nz * H + ny) * H + nx,
                                           static_cast<unsigned long long>(q[k]));
@@ -536,7 +529,7 @@ __device__ __forceinline__ void step_items(const StepView& v, const Keys& keys, 
                     // g = 1 + sum_j f_j (1 - f_j) / 2; along axis j the nodes c_j - 1 and
                     // c_j + 2 carry -f (1 - f)(2 - f) / 6 and -f (1 - f)(1 + f) / 6 times
                     // the bilinear weight of the other two axes (cases of R_h^(4))
-                    const float ea = fminf(__fmul_rn(expf(d2f_bits(pl)), dscale), 741455.0f);
+                    const float ea = fminf(__fmul_rn(expf(__double2float_rn(pl)), dscale), 741455.0f);
                     const float fx = c.fx, fy = c.fy, fz = c.fz;
                     const float bx = __fmul_rn(fx, wx0), by = __fmul_rn(fy, wy0), bz = __fmul_rn(fz, wz0);
                     const float g = __fadd_rn(1.0f, __fmul_rn(0.5f, __fadd_rn(__fadd_rn(bx, by), bz)));
@@ -554,8 +547,9 @@ __device__ __forceinline__ void step_items(const StepView& v, const Keys& keys, 
                         if (in_tile) {
                             atomicAdd(dep + DB::idx(lx + ox, ly + oy, lz + oz), q);
                         } else {
-                            const int nx = wrap_index(c.cx + ox, H), ny = wrap_index(c.cy + oy, H);
-                            const int nz = wrap_index(c.cz + oz, H);
+                            const int nx = wrap_index(clamp_cell(c.cx, H) + ox, H);
+                            const int ny = wrap_index(clamp_cell(c.cy, H) + oy, H);
+                            const int nz = wrap_index(clamp_cell(c.cz, H) + oz, H);
                             atomicAdd(acc + (nz * H + ny) * H + nx,
                                       static_cast<unsigned long long>(static_cast<long long>(q)));
                         }
@@ -584,7 +578,7 @@ __device__ __forceinline__ void step_items(const StepView& v, const Keys& keys, 
                     const float rho = __fdividef(__fmul_rn(2.0f, g.w), __fadd_rn(1.0f, g.w));
                     const float x = __fmul_rn(v.tau, __fsub_rn(rho, 1.0f));
                     const float inc = v.tau <= 0.0625f ? log1p_small(x) : log1pf(x);
-                    pl = pl + f2d_bits(inc);
+                    pl = pl + static_cast<double>(inc);
                     // Euler-Maruyama push in grid units
                     const float3 nz = box_muller(keys(make_uint4(step_n, 0u, pid, 0u)));
                     px = __fmaf_rn(v.noise, nz.x, __fmaf_rn(v.drift, g.x, px));
@@ -850,7 +844,7 @@ __global__ void k_tile_count(const float* __restrict__ sx, const float* __restri
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     int t = -1;
     if (i < N) {
-        const Cell c = locate(sx[i], sy[i], sz[i], H);
+        const Cell c = locate_clamped(sx[i], sy[i], sz[i], H);
         t = tile_of(c.cx, c.cy, c.cz, H >> 3);
     }
     const unsigned peers = __match_any_sync(kFull, t);
@@ -895,7 +889,7 @@ __global__ void k_cell_count(const float* __restrict__ sx, const float* __restri
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t key = 0xffffffffu;
     if (i < N) {
-        const Cell c = locate(sx[i], sy[i], sz[i], H);
+        const Cell c = locate_clamped(sx[i], sy[i], sz[i], H);
         key = cell_key(c.cx, c.cy, c.cz, H >> 3);
     }
     const unsigned peers = __match_any_sync(kFull, key);
@@ -978,7 +972,7 @@ __global__ void k_canon_scatter(const float* __restrict__ sx, const float* __res
                                 uint32_t* __restrict__ ids_tmp) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const Cell c = locate(sx[i], sy[i], sz[i], H);
+    const Cell c = locate_clamped(sx[i], sy[i], sz[i], H);
     const uint32_t key = cell_key(c.cx, c.cy, c.cz, H >> 3);
     const int slot = cell_start[key] + atomicAdd(fill + key, 1);
     keys_tmp[slot] = key;
@@ -1203,21 +1197,6 @@ __global__ void k_normals(const uint32_t* __restrict__ ids, int64_t N, uint32_t 
         bits[2 * N + i] = raw.z;
         bits[3 * N + i] = raw.w;
     }
-}
-
-// Bit-exactness check of the integer float<->double conversions.
-__global__ void k_conv_check(const float* __restrict__ f, const double* __restrict__ d, int n,
-                             int* __restrict__ mismatches) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double a = f2d_bits(f[i]);
-    const double b = static_cast<double>(f[i]);
-    const float c = d2f_bits(d[i]);
-    const float e = __double2float_rn(d[i]);
-    const bool same_ab = __double_as_longlong(a) == __double_as_longlong(b) || (isnan(a) && isnan(b));
-    const bool same_ce = __float_as_uint(c) == __float_as_uint(e) || (isnan(c) && isnan(e));
-    if (!same_ab) atomicAdd(mismatches, 1);
-    if (!same_ce) atomicAdd(mismatches + 1, 1);
 }
 
 inline int blocks_for(int64_t n, int nt) { return static_cast<int>((n + nt - 1) / nt); }
@@ -1450,12 +1429,6 @@ cudaError_t launch_normals(const uint32_t* ids, int64_t N, uint32_t n, uint64_t 
     k_normals<<<blocks_for(N, 256), 256, 0, s>>>(ids, N, n,
                                                  static_cast<uint32_t>(seed),
                                                  static_cast<uint32_t>(seed >> 32), z, bits);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_conv_check(const float* f, const double* d, int n, int* mismatches,
-                              cudaStream_t s) {
-    k_conv_check<<<blocks_for(n, 256), 256, 0, s>>>(f, d, n, mismatches);
     return cudaGetLastError();
 }
 

@@ -323,8 +323,6 @@ cudaError_t launch_component(sipf_ctx* c, int comp, float* dst);
 cudaError_t launch_diagnostics(sipf_ctx* c, int b, double acc_to_u);
 cudaError_t launch_normals(const uint32_t* ids, int64_t N, uint32_t n, uint64_t seed, float* z,
                            uint32_t* bits, cudaStream_t s);
-cudaError_t launch_conv_check(const float* f, const double* d, int n, int* mismatches,
-                              cudaStream_t s);
 // Batched particle kernels of an ensemble whose n <= kMaxRuns members all
 // read buffer `parity`: the step over the concatenated items of all runs
 // (one persistent launch), and the plan of every run (one block per run).

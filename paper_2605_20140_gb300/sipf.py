@@ -37,7 +37,7 @@ EXPORTED = (
     "sipf_create", "sipf_set_state", "sipf_step", "sipf_fields", "sipf_particles",
     "sipf_particle_state", "sipf_cell_start", "sipf_diagnostics", "sipf_sync",
     "sipf_destroy", "sipf_strerror", "sipf_last_error", "sipf_brownian_normals",
-    "sipf_profile", "sipf_profile_read", "sipf_profile_name", "sipf_check_conversions",
+    "sipf_profile", "sipf_profile_read", "sipf_profile_name",
     "sipf_deposit_noalloc", "sipf_save", "sipf_load",
     "sipf_describe", "sipf_resample", "sipf_ensemble_create", "sipf_ensemble_member",
     "sipf_ensemble_step", "sipf_ensemble_sync", "sipf_ensemble_last_error",
@@ -115,7 +115,6 @@ def load() -> ctypes.CDLL:
         "sipf_profile": ([P, I32], I32),
         "sipf_profile_read": ([P, P, P, I32], I32),
         "sipf_profile_name": ([I32], ctypes.c_char_p),
-        "sipf_check_conversions": ([P, P, I64, P, P], I32),
         "sipf_deposit_noalloc": ([ctypes.POINTER(sipf_grid), P, P, I64, P, P], I32),
         "sipf_save": ([P, ctypes.c_char_p], I32),
         "sipf_resample": ([P, ctypes.c_double, ctypes.POINTER(ctypes.c_int32)], I32),
@@ -333,11 +332,6 @@ def sipf_describe(ctx) -> dict:
 def sipf_brownian_normals(ids_dev, N: int, n: int, seed: int, z_dev, bits_dev=None, stream=0):
     _check(load().sipf_brownian_normals(_ptr(ids_dev), int(N), int(n), int(seed), _ptr(z_dev),
                                         _ptr(bits_dev), ctypes.c_void_p(stream or None)))
-
-
-def sipf_check_conversions(f_dev, d_dev, n: int, mism_dev, stream=0):
-    _check(load().sipf_check_conversions(_ptr(f_dev), _ptr(d_dev), int(n), _ptr(mism_dev),
-                                         ctypes.c_void_p(stream or None)))
 
 
 def sipf_deposit_noalloc(grid: sipf_grid, x_dev, mass_dev, N: int, u_dev, stream=0):
