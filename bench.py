@@ -2,7 +2,7 @@
 """Throughput of the SIPF-W step on the 128^3-grid / 2^22-particle workload.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sipf|reference]
-                    [--workload headline|ensemble|serve [--rate R]]
+                    [--workload headline|large|ensemble|serve [--rate R | --rates a,b,..]]
 
 One step = one pass of the whole hot path (the particle step: deposit,
 gather, push, mass update and binning; the bucket plan; three spectral
@@ -13,6 +13,8 @@ Prints one JSON line on rank 0.  Under torchrun (N > 1) every rank runs an
 independent replica on its own GPU (no data-path collective); the timed
 region is bracketed by a barrier and the slowest rank's time is used.
 
+--workload large times the 256^3-grid / 2^25-particle run the same way
+(chi 0.02, dt 2.5e-4; no CPU baseline);
 --workload ensemble instead times 64 uneven independent runs advanced
 together (one stream each) against the same runs one at a time (runs/s);
 --workload serve times continuous batching of Poisson-arriving requests
@@ -43,6 +45,9 @@ if ROOT not in sys.path:
 METRIC = "particle-steps/s at 128^3 grid, 4M particles"
 UNIT = "particle-steps/s"
 WORKLOAD = "headline: 128^3 grid, 2^22 particles, 3 Gaussian seeds (sigma 0.04), dt 5e-4"
+METRIC_LARGE = "particle-steps/s at 256^3 grid, 32M particles"
+WORKLOAD_LARGE = ("large: 256^3 grid, 2^25 particles, 3 Gaussian seeds (sigma 0.04), chi 0.02, "
+                  "dt 2.5e-4")
 # Algorithmic bytes (what the method must move): per particle-step read X
 # (12 B) + log a (8 B), write X' (12 B) + log a' (8 B); per node-step the 15
 # float32 field touches of the reaction, solve, gather and deposit.
@@ -154,7 +159,7 @@ def _peaks():
 # valid only while the kernel's source is the one captured.
 NCU_TRAFFIC = {"particle_step": (("paper_2605_20140_gb300/csrc/particles.cu",
                                   "paper_2605_20140_gb300/csrc/sipf_internal.cuh"),
-                                 "25baa52bdeb1b600", 154.6e6)}
+                                 "fb96818b02f6b187", 154.0e6)}
 
 
 def _ncu_traffic(group):
@@ -280,7 +285,8 @@ def run_sipf(args, rank, world, local):
         from paper_2605_20140_gb300 import build
         build.build()
     sipf.load()
-    wl = workload("headline", seed=rank)
+    large = args.workload == "large"
+    wl = workload("large" if large else "headline", seed=rank)
     N, H, dt = wl.N, wl.H, wl.dt
     stream = torch.cuda.Stream()
     sim = sipf.Simulation(H, wl.L, wl.origin, N, wl.params, stream=stream.cuda_stream)
@@ -394,17 +400,19 @@ def run_sipf(args, rank, world, local):
 
     if rank != 0:
         return 0
-    cpu = None if args.no_cpu_baseline else _cpu_baseline(lambda: workload("headline"))
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+    cpu = None if (args.no_cpu_baseline or large) else _cpu_baseline(lambda: workload("headline"))
+    out = {"metric": METRIC_LARGE if large else METRIC, "value": value, "unit": UNIT,
+           "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32 (f64 log-mass and reductions)", "data": "synthetic",
            "repeats": {"n": len(reps), "ms_per_step": [r / args.steps for r in reps],
                        "spread": (max(reps) - min(reps)) / ms_total,
                        "value_is": "median of the timed regions"},
-           "config": {"workload": WORKLOAD, "H": H, "N": N, "dt": dt,
+           "config": {"workload": WORKLOAD_LARGE if large else WORKLOAD, "H": H, "N": N, "dt": dt,
                       "parallelism": f"replicas x{world}",
-                      "l2": "no flush: the step's working set (~300 MB) exceeds the 129 MB L2",
+                      "l2": f"no flush: the step's working set (~{step_bytes / 1e6:.0f} MB of "
+                            "algorithmic traffic) exceeds the 129 MB L2",
                       "diagnostics": f"FP64 diagnostics read back every {DIAG_EVERY} steps, "
                                      "inside the timed region"},
            "roofline": roofline, "step_roofline": step_roofline, "kernels": kernels,
@@ -626,7 +634,8 @@ def run_serve(args, rank, world, local):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--workload", choices=["headline", "ensemble", "serve"], default="headline")
+    ap.add_argument("--workload", choices=["headline", "large", "ensemble", "serve"],
+                    default="headline")
     ap.add_argument("--rate", type=float, default=100.0, help="serve: arrivals per second")
     ap.add_argument("--rates", default=None,
                     help="serve: comma-separated arrival rates to sweep (overrides --rate)")
@@ -641,7 +650,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.steps is None:
-        args.steps = 200 if args.workload == "ensemble" else 1000
+        args.steps = {"ensemble": 200, "large": 100}.get(args.workload, 1000)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     rank, world, local = _dist_init(args.gpus)
