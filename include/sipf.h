@@ -191,9 +191,12 @@ int sipf_cell_start(sipf_ctx* ctx, int32_t* cell_start, int where);
 int sipf_canonical_order(sipf_ctx* ctx, int32_t* cell_start, uint32_t* ids, int where);
 
 /* Tuning.  Launch choices that change speed, never results beyond float32
- * rounding: radix_plan (0 or 1) selects between two Stockham plans of each
- * transform length (e.g. 96 = 8 x 4 x 3 or 12 x 8; the results differ only
- * by float32 rounding); step_blocks_per_sm (0 = the occupancy limit, else at
+ * rounding: radix_plan selects how the spectral step transforms: 0 or 1,
+ * two Stockham plans of each transform length in the plane passes (e.g.
+ * 96 = 8 x 4 x 3 or 12 x 8); 2, the per-axis pipeline of transforms held by
+ * groups of lanes (H = 64, 128, 256; other sizes take plan 0 instead); the
+ * plans' results differ only by float32 rounding;
+ * step_blocks_per_sm (0 = the occupancy limit, else at
  * most that many particle-step blocks per SM); bucket capacity = count +
  * count / bucket_slack_div + bucket_slack_add per tile, 8 <= div <= 1024,
  * 0 <= add <= 32 (smaller slack sends more particles to the overflow region;

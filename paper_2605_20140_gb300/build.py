@@ -24,7 +24,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relax
           "-I", INC]
 PER_FILE = {"particles.cu": ["-fmad=false"]}
 SOURCES = ["api.cu", "particles.cu", "fft.cu", "fft_fused_p0.cu", "fft_fused_p1.cu",
-           "fft_split_p0.cu", "fft_split_p1.cu", "noalloc.cu", "resample.cu", "server.cu",
+           "fft_split_p0.cu", "fft_split_p1.cu", "fft_warp.cu", "noalloc.cu", "resample.cu", "server.cu",
            "smooth.cu"]
 
 

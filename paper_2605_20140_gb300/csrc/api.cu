@@ -51,7 +51,7 @@ std::vector<TuneEntry> g_tune;
 bool g_tune_loaded = false;
 
 bool tuning_valid(const sipf_tuning& t) {
-    return (t.radix_plan == 0 || t.radix_plan == 1) && t.step_blocks_per_sm >= 0 &&
+    return t.radix_plan >= 0 && t.radix_plan <= 2 && t.step_blocks_per_sm >= 0 &&
            t.step_blocks_per_sm <= 32 && t.bucket_slack_div >= 8 &&
            t.bucket_slack_div <= 1024 && t.bucket_slack_add >= 0 && t.bucket_slack_add <= 32;
 }
@@ -115,7 +115,8 @@ bool lookup_tuning(int H, int64_t N, sipf_tuning* out) {
 }
 
 void apply_tuning(sipf_ctx* c, const sipf_tuning& t) {
-    c->radix_plan = t.radix_plan;
+    // plan 2 (the warp pipeline) where the grid size has it, else plan 0
+    c->radix_plan = t.radix_plan == 2 && !has_warp_pipeline(c->H) ? 0 : t.radix_plan;
     c->step_bps = t.step_blocks_per_sm;
     c->slack_div = t.bucket_slack_div;
     c->slack_add = t.bucket_slack_add;
@@ -199,7 +200,7 @@ size_t ctx_device_bytes(int H, int64_t N, bool filter, bool smoothing) {
     b += diag_scratch_doubles() * sizeof(double) + diag_scratch_ll() * sizeof(long long) +
          8 * sizeof(double);
     if (filter) b += z.spec * sizeof(float2);
-    if (H > 128) b += 2 * z.spec * sizeof(float2);
+    if (H > 128 || has_warp_pipeline(H)) b += 2 * z.spec * sizeof(float2);
     if (smoothing) b += z.H3 * sizeof(float) + static_cast<size_t>(H) * sizeof(float);
     return b;
 }
@@ -628,7 +629,7 @@ int create_in_pool(const sipf_grid* grid, int64_t N, const sipf_params* params,
          da(&c->diag_out, 8) == cudaSuccess;
     const bool filter = params->H0 > 0.0 && params->H0 < grid->H;
     if (ok && filter) ok = da(&c->specA, spec) == cudaSuccess;
-    if (ok && c->H > 128)
+    if (ok && (c->H > 128 || has_warp_pipeline(c->H)))
         ok = da(&c->specDx, spec) == cudaSuccess && da(&c->specDy, spec) == cudaSuccess;
     if (ok && params->sigma > 0.0)
         ok = da(&c->us, H3) == cudaSuccess && da(&c->ksig, static_cast<size_t>(c->H)) == cudaSuccess;

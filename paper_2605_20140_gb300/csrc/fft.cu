@@ -39,8 +39,10 @@ cudaError_t fused_dispatch_p1(int H, const SpecRun* runs, int n, int pass, int d
                               cudaStream_t s);
 cudaError_t split_dispatch_p0(sipf_ctx* c, const SpectralArgs& a, int pass);
 cudaError_t split_dispatch_p1(sipf_ctx* c, const SpectralArgs& a, int pass);
+cudaError_t warp_dispatch(int H, const SpecRun& run, int pass, int device, cudaStream_t s);
 
 cudaError_t launch_spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass) {
+    if (c->radix_plan == 2) return warp_dispatch(c->H, spec_run(c, a), pass, c->device, c->stream);
     if (c->H <= 128) {
         const SpecRun one = spec_run(c, a);
         return c->radix_plan ? fused_dispatch_p1(c->H, &one, 1, pass, c->device, c->stream)
@@ -52,7 +54,15 @@ cudaError_t launch_spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass) {
 cudaError_t launch_spectral_batch(int H, const SpecRun* runs, int n, int pass, int plan,
                                   int device, cudaStream_t s) {
     if (n < 1 || n > kMaxBatch || H > 128) return cudaErrorInvalidValue;
-    return plan ? fused_dispatch_p1(H, runs, n, pass, device, s)
+    if (plan == 2) {
+        // the warp pipeline's lines are independent of the run: one launch set per run
+        for (int i = 0; i < n; ++i) {
+            const cudaError_t e = warp_dispatch(H, runs[i], pass, device, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    return plan == 1 ? fused_dispatch_p1(H, runs, n, pass, device, s)
                 : fused_dispatch_p0(H, runs, n, pass, device, s);
 }
 
@@ -72,6 +82,8 @@ SpecRun spec_run(const sipf_ctx* c, const SpectralArgs& a) {
     r.specV = c->specV;
     r.specB = c->specB;
     r.specA = c->specA;
+    r.specDx = c->specDx;
+    r.specDy = c->specDy;
     r.twiddle = c->twiddle;
     r.voff = c->voff;
     r.sc = c->dsc + c->cur;

@@ -6,6 +6,7 @@
 // parallel.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -176,18 +177,25 @@ __global__ void __launch_bounds__(Cfg<H>::NT1)
     fft_axis<H, V, H / 2, 1, RP, NT, -1>(Vb, tw);
     {
         // split each transformed row pair z = x1 + i x2 (rows p, p + H/2) into
-        // X1, X2 (kx <= H/2)
-        constexpr int NS = (H / 2) * HK, SPT = (NS + NT - 1) / NT;
+        // the half rows X1, X2 (kx <= H/2).  X(0) and X(H/2) of a real row are
+        // real: column 0 holds X(0) + i X(H/2), so H/2 columns remain
+        constexpr int HH = H / 2, NS = HH * HH, SPT = (NS + NT - 1) / NT;
         float2 x1[SPT], x2[SPT];
 #pragma unroll
         for (int s = 0; s < SPT; ++s) {
             const int idx = threadIdx.x + s * NT;
             if (idx < NS) {
-                const int p = idx / HK, k = idx % HK;
+                const int p = idx / HH, k = idx % HH;
                 const float2 zp = Vb[p * RP + k];
-                const float2 zm = Vb[p * RP + neg_mod<H>(k)];
-                x1[s] = make_float2(0.5f * (zp.x + zm.x), 0.5f * (zp.y - zm.y));
-                x2[s] = make_float2(0.5f * (zp.y + zm.y), -0.5f * (zp.x - zm.x));
+                const float2 zm = Vb[p * RP + (k == 0 ? HH : H - k)];
+                if (k == 0) {
+                    // zm is z(H/2) here: X1(0) = Re z(0), X1(H/2) = Re z(H/2), X2 from Im
+                    x1[s] = make_float2(zp.x, zm.x);
+                    x2[s] = make_float2(zp.y, zm.y);
+                } else {
+                    x1[s] = make_float2(0.5f * (zp.x + zm.x), 0.5f * (zp.y - zm.y));
+                    x2[s] = make_float2(0.5f * (zp.y + zm.y), -0.5f * (zp.x - zm.x));
+                }
             }
         }
         __syncthreads();
@@ -195,15 +203,15 @@ __global__ void __launch_bounds__(Cfg<H>::NT1)
         for (int s = 0; s < SPT; ++s) {
             const int idx = threadIdx.x + s * NT;
             if (idx < NS) {
-                const int p = idx / HK, k = idx % HK;
+                const int p = idx / HH, k = idx % HH;
                 Vb[p * KXP + k] = x1[s];
-                Vb[(p + H / 2) * KXP + k] = x2[s];
+                Vb[(p + HH) * KXP + k] = x2[s];
             }
         }
         __syncthreads();
     }
     if (a.do_mw) fft_axis<H, V, H, RP, 1, NT, -1>(Z, tw);
-    fft_axis<H, V, HK, KXP, 1, NT, -1>(Vb, tw);
+    fft_axis<H, V, H / 2, KXP, 1, NT, -1>(Vb, tw);
     // half spectra, rows of KXP (the last slot, kx = H/2 + 1, is zero); M, W
     // separated from the 2D spectrum of m* + i w*; one mode per thread
     constexpr int NP = H * KXP;
@@ -216,7 +224,15 @@ __global__ void __launch_bounds__(Cfg<H>::NT1)
             const float2 zc = Z[neg_mod<H>(ky) * RP + neg_mod<H>(k)];
             M = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y - zc.y));
             W = make_float2(0.5f * (zk.y + zc.y), -0.5f * (zk.x - zc.x));
-            Vk = Vb[ky * KXP + k];
+            if (k == 0 || k == H / 2) {
+                // the packed column P = V(0, .) + i V(H/2, .): V(0, ky) =
+                // (P(ky) + conj P(-ky))/2, V(H/2, ky) = (P(ky) - conj P(-ky))/(2i)
+                const float2 pk = Vb[ky * KXP], pc = Vb[neg_mod<H>(ky) * KXP];
+                Vk = k == 0 ? make_float2(0.5f * (pk.x + pc.x), 0.5f * (pk.y - pc.y))
+                            : make_float2(0.5f * (pk.y + pc.y), -0.5f * (pk.x - pc.x));
+            } else {
+                Vk = Vb[ky * KXP + k];
+            }
         }
         if (a.do_mw) {
             gM[sbase + idx] = M;
@@ -224,6 +240,227 @@ __global__ void __launch_bounds__(Cfg<H>::NT1)
         }
         gV[sbase + idx] = Vk;
     }
+}
+
+// ---------------------------------------------------------------- pass 1, cluster pair form
+// The forward plane pass split over a cluster of two CTAs per z-plane, with
+// half the threads and shared memory of the single-block form each, so that
+// two CTAs share an SM and every plane runs at once.  CTA r reacts and
+// transforms along x the rows y in [r H/2, (r + 1) H/2) (v^n paired as
+// adjacent rows); after a cluster barrier it takes half of the columns for
+// the y transform, whose first stage reads the peer's rows through
+// distributed shared memory, and a second barrier orders those reads before
+// either CTA overwrites its rows with its columns.  M and W pair each mode
+// with its conjugate, which may lie in the peer's columns; V's packed
+// columns are written by the CTA that holds them.
+template <int H> constexpr bool has_pair_forward() { return false; }
+
+template <int H> struct PairSmem {
+    static constexpr int RH = H / 2, RP = rowp<H>(), KXP = kxp<H>();
+    static constexpr int ZCP = H / 2, VCP = H / 4;          // column-layout pitches
+    static constexpr int ZN = RH * RP > H * ZCP ? RH * RP : H * ZCP;
+    static constexpr int VN0 = (RH / 2) * RP > RH * KXP ? (RH / 2) * RP : RH * KXP;
+    static constexpr int VN = VN0 > H * VCP ? VN0 : H * VCP;
+    static constexpr size_t bytes = static_cast<size_t>(ZN + VN + H) * sizeof(float2);
+};
+
+// First Stockham stage (NS = 1) from a loader that may read the peer CTA's
+// shared memory: a cluster barrier (instead of a block barrier) separates
+// the loads from the writes, so that neither CTA overwrites what the other
+// still reads.
+template <int L, int R, int NTRANS, int NT, int SIGN, class At, class Load>
+__device__ __forceinline__ void stage1_from_cluster(float2* out, At at, Load load) {
+    constexpr int NB = NTRANS * (L / R);
+    constexpr int BPT = (NB + NT - 1) / NT;
+    float2 v[BPT][R];
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        const int b = threadIdx.x + i * NT;
+        if (b < NB) {
+            const int t = b % NTRANS, j = b / NTRANS;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[i][r] = load(t, j + r * (L / R));
+            dft<R, SIGN>(v[i]);
+        }
+    }
+    cooperative_groups::this_cluster().sync();
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        const int b = threadIdx.x + i * NT;
+        if (b < NB) {
+            const int t = b % NTRANS, j = b / NTRANS;
+#pragma unroll
+            for (int r = 0; r < R; ++r) out[at(t, j * R + r)] = v[i][r];
+        }
+    }
+    __syncthreads();
+}
+
+template <int H, int NB, int V>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Cfg<H>::NT1 / 2)
+    k_forward_xy_pair(const __grid_constant__ SpecBatch<NB> batch) {
+    namespace cg = cooperative_groups;
+    using PS = PairSmem<H>;
+    const SpecRun& R = batch.run[NB == 1 ? 0 : blockIdx.y];
+    const SpectralArgs& a = R.a;
+    const float* v = R.v;
+    const float* __restrict__ m = R.m;
+    const float* __restrict__ w = R.w;
+    unsigned long long* __restrict__ acc = R.acc;
+    float* v_out = R.v_out;
+    const float* __restrict__ us = R.us;
+    constexpr int NT = Cfg<H>::NT1 / 2, KXP = PS::KXP, HK = H / 2 + 1, RP = PS::RP;
+    constexpr int RH = PS::RH, HH = H / 2, ZCP = PS::ZCP, VCP = PS::VCP, VC = H / 4;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int r = static_cast<int>(cluster.block_rank());
+    const int z = blockIdx.x >> 1;
+    extern __shared__ float2 sm[];
+    float2* Z = sm;               // rows [RH][RP] (m* + i w*), then columns [H][ZCP]
+    float2* Vb = Z + PS::ZN;      // row pairs [RH/2][RP], half rows [RH][KXP], columns [H][VCP]
+    float2* tw = Vb + PS::VN;
+    for (int i = threadIdx.x; i < H; i += NT) tw[i] = R.twiddle[i];
+    const float u_scale = R.sc->u_scale;   // u_bar per accumulator unit
+    const float c0 = *R.voff;   // the v spectrum only feeds derivatives: remove a constant
+    const size_t row0 = (static_cast<size_t>(z) * H + static_cast<size_t>(r) * RH) * H;
+    {
+        // node pairs (2q, x), (2q + 1, x) of the CTA's rows; all loads of a
+        // batch are issued first
+        constexpr int NPR = (RH / 2) * H, ITER = (NPR + NT - 1) / NT, CH = ITER < 2 ? ITER : 2;
+#pragma unroll 1
+        for (int i0 = 0; i0 < ITER; i0 += CH) {
+            float rv[CH][2], rm[CH][2], rw[CH][2], ru[CH][2];
+            unsigned long long ra[CH][2];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int q = threadIdx.x + (i0 + c) * NT;
+                if (i0 + c < ITER && q < NPR) {
+                    const int pq = q / H, x = q % H;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const size_t o = row0 + static_cast<size_t>(2 * pq + h) * H + x;
+                        rv[c][h] = v[o];
+                        rm[c][h] = m[o];
+                        rw[c][h] = w[o];
+                        ra[c][h] = acc[o];
+                        ru[c][h] = us ? us[o] : 0.f;
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int q = threadIdx.x + (i0 + c) * NT;
+                if (!(i0 + c < ITER && q < NPR)) continue;
+                const int pq = q / H, x = q % H;
+                float vn[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const size_t o = row0 + static_cast<size_t>(2 * pq + h) * H + x;
+                    acc[o] = 0ull;
+                    float ms, ws;
+                    const float u = acc_to_float(ra[c][h]) * u_scale;
+                    react(a, rv[c][h], rm[c][h], rw[c][h], u, us ? ru[c][h] : u, ms, ws, vn[h]);
+                    Z[(2 * pq + h) * RP + x] = make_float2(ms, ws);
+                    if (a.write_v) v_out[o] = vn[h];
+                }
+                Vb[pq * RP + x] = make_float2(vn[0] - c0, vn[1] - c0);
+            }
+        }
+    }
+    __syncthreads();
+    if (a.do_mw) fft_axis<H, V, RH, 1, RP, NT, -1>(Z, tw);
+    fft_axis<H, V, RH / 2, 1, RP, NT, -1>(Vb, tw);
+    {
+        // split each transformed row pair into the half rows of rows 2q and
+        // 2q + 1, packed: entry 0 = X(0) + i X(H/2), both real
+        constexpr int NS = (RH / 2) * HH, SPT = (NS + NT - 1) / NT;
+        float2 x1[SPT], x2[SPT];
+#pragma unroll
+        for (int s = 0; s < SPT; ++s) {
+            const int idx = threadIdx.x + s * NT;
+            if (idx < NS) {
+                const int p = idx / HH, k = idx % HH;
+                const float2 zp = Vb[p * RP + k];
+                const float2 zm = Vb[p * RP + (k == 0 ? HH : H - k)];
+                if (k == 0) {
+                    x1[s] = make_float2(zp.x, zm.x);
+                    x2[s] = make_float2(zp.y, zm.y);
+                } else {
+                    x1[s] = make_float2(0.5f * (zp.x + zm.x), 0.5f * (zp.y - zm.y));
+                    x2[s] = make_float2(0.5f * (zp.y + zm.y), -0.5f * (zp.x - zm.x));
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < SPT; ++s) {
+            const int idx = threadIdx.x + s * NT;
+            if (idx < NS) {
+                const int p = idx / HH, k = idx % HH;
+                Vb[(2 * p) * KXP + k] = x1[s];
+                Vb[(2 * p + 1) * KXP + k] = x2[s];
+            }
+        }
+    }
+    cluster.sync();   // both CTAs' rows are transformed
+    const float2* Z0 = cluster.map_shared_rank(Z, 0);
+    const float2* Z1 = cluster.map_shared_rank(Z, 1);
+    const float2* V0 = cluster.map_shared_rank(Vb, 0);
+    const float2* V1 = cluster.map_shared_rank(Vb, 1);
+    constexpr int R1 = Radix<H, V>::R1;
+    if (a.do_mw) {
+        // columns kx in [r H/2, (r + 1) H/2) of m* + i w*
+        const int k0 = r * HH;
+        stage1_from_cluster<H, R1, HH, NT, -1>(Z, Strided<1, ZCP>{}, [&](int t, int y) {
+            return (y < RH ? Z0 : Z1)[(y % RH) * RP + k0 + t];
+        });
+        fft_rest<H, V, HH, ZCP, 1, NT, -1>(Z, tw);
+    }
+    {
+        // packed v columns [r H/4, (r + 1) H/4)
+        const int k0 = r * VC;
+        stage1_from_cluster<H, R1, VC, NT, -1>(Vb, Strided<1, VCP>{}, [&](int t, int y) {
+            return (y < RH ? V0 : V1)[(y % RH) * KXP + k0 + t];
+        });
+        fft_rest<H, V, VC, VCP, 1, NT, -1>(Vb, tw);
+    }
+    cluster.sync();   // both CTAs' columns are transformed
+    const size_t sbase = static_cast<size_t>(z) * H * KXP;
+    if (a.do_mw) {
+        // M, W for the modes ky in [r H/2, (r + 1) H/2), all kx < H/2 + 2
+        constexpr int NP = RH * KXP;
+        for (int idx = threadIdx.x; idx < NP; idx += NT) {
+            const int ky = r * RH + idx / KXP, k = idx % KXP;
+            float2 M = make_float2(0.f, 0.f), W = M;
+            if (k < HK) {
+                const int kc = neg_mod<H>(k), yc = neg_mod<H>(ky);
+                const float2 zk = (k < HH ? Z0 : Z1)[ky * ZCP + k % HH];
+                const float2 zc = (kc < HH ? Z0 : Z1)[yc * ZCP + kc % HH];
+                M = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y - zc.y));
+                W = make_float2(0.5f * (zk.y + zc.y), -0.5f * (zk.x - zc.x));
+            }
+            R.specM[sbase + static_cast<size_t>(ky) * KXP + k] = M;
+            R.specW[sbase + static_cast<size_t>(ky) * KXP + k] = W;
+        }
+    }
+    {
+        // V: the CTA's packed columns; packed column 0 holds V(0, .) + i V(H/2, .)
+        for (int idx = threadIdx.x; idx < H * VC; idx += NT) {
+            const int ky = idx / VC, cl = idx % VC, c = r * VC + cl;
+            float2* row = R.specV + sbase + static_cast<size_t>(ky) * KXP;
+            if (c != 0) {
+                row[c] = Vb[ky * VCP + cl];
+            } else {
+                const float2 pk = Vb[ky * VCP], pc = Vb[neg_mod<H>(ky) * VCP];
+                row[0] = make_float2(0.5f * (pk.x + pc.x), 0.5f * (pk.y - pc.y));
+                row[HH] = make_float2(0.5f * (pk.y + pc.y), -0.5f * (pk.x - pc.x));
+            }
+        }
+        if (r == 1) {
+            for (int ky = threadIdx.x; ky < H; ky += NT)
+                R.specV[sbase + static_cast<size_t>(ky) * KXP + HK] = make_float2(0.f, 0.f);
+        }
+    }
+    cluster.sync();   // the peer may still read this CTA's columns
 }
 
 // ---------------------------------------------------------------- pass 2
@@ -301,6 +538,15 @@ __global__ void __launch_bounds__(Cfg<H>::NT2)
         if (k0 + t < KXP) dst[at(t, zz)] = val;
     });
 }
+
+// Shapes of the lane-group transforms of the warp pipeline (below): P lanes
+// per line; exchange tiles of PITCH float2 per row and TILE float2 per group,
+// chosen so that the exchanges are free of bank conflicts.
+template <int H> struct LaneShape;
+template <> struct LaneShape<64> { static constexpr int P = 8, PITCH = 9, TILE = 72; };
+template <> struct LaneShape<128> { static constexpr int P = 8, PITCH = 18, TILE = 145; };
+template <> struct LaneShape<256> { static constexpr int P = 16, PITCH = 17, TILE = 272; };
+constexpr int kLaneWarps = 8;   // warps per block of the warp pipeline
 
 // ---------------------------------------------------------------- pass 3
 // Build the full-length complex row Z[kx] = X1[kx] + i X2[kx] of two real
@@ -436,6 +682,329 @@ __global__ void __launch_bounds__(Cfg<H>::NT3)
             Gp[4 * i + 2] = (upper ? f.y : f.x) * sz_;
         }
     }
+}
+
+// ---------------------------------------------------------------- warp per-axis pipeline
+// For the grid sizes with a LaneShape shape the whole spectral step can run as
+// five passes over lines held in registers by groups of P lanes (WarpFFT),
+// with the half spectra in global memory (L2) between them and no block
+// barrier inside a transform:
+//   wx_forward: row pairs (z, y), (z, y + H/2): reaction; m* + i w* per row
+//               and v^n of the two rows as one complex row, x DFT, split into
+//               half rows -> M, W, V
+//   wy (SIGN -1): columns (z, kx) of M, W, V: y DFT in place
+//   z:          the block z pass (k_z_multiply; its tiles read whole rows)
+//   wy (SIGN +1): columns of M, W, B in place, V (or its filtered copy) ->
+//               i k_x V, i k_y V
+//   wx_inverse: rows: (m, w), (dv/dx, dv/dy), and dv/dz row pairs, packed
+//               two real outputs per complex row, inverse x DFT; a block
+//               writes whole rows of the gather array.
+// Lines are assigned to groups in a flat order, so that a warp's groups read
+// and write neighbouring memory.
+
+// Split a transformed complex row X = X1 + i X2 of two real rows, held in
+// the spectral layout, into their half rows (kx < H/2 + 2, the last one the
+// zero padding): X1(k) = (X(k) + conj X(-k))/2, X2(k) = (X(k) - conj X(-k))/(2i).
+template <int H, class F>
+__device__ __forceinline__ void split_store(const float2 (&v)[F::Q], int l, float2* ex,
+                                            float2* d1, float2* d2) {
+    constexpr int P = F::Q / F::S, S = F::S, Q = F::Q, KXP = kxp<H>(), HK = H / 2 + 1;
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+#pragma unroll
+        for (int k2 = 0; k2 < P; ++k2) ex[S * l + s + Q * k2] = v[s * P + k2];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < (KXP + P - 1) / P; ++j) {
+        const int k = l + P * j;
+        if (k < KXP) {
+            float2 a1 = make_float2(0.f, 0.f), a2 = a1;
+            if (k < HK) {
+                const float2 zp = ex[k], zm = ex[neg_mod<H>(k)];
+                a1 = make_float2(0.5f * (zp.x + zm.x), 0.5f * (zp.y - zm.y));
+                a2 = make_float2(0.5f * (zp.y + zm.y), -0.5f * (zp.x - zm.x));
+            }
+            d1[k] = a1;
+            if (d2) d2[k] = a2;
+        }
+    }
+}
+
+template <int H, int NB>
+__global__ void __launch_bounds__(32 * kLaneWarps)
+    k_wx_forward(const __grid_constant__ SpecBatch<NB> batch) {
+    using C = LaneShape<H>;
+    using F = WarpFFT<H, C::P, C::PITCH>;
+    constexpr int P = C::P, Q = F::Q, G = 32 / P, KXP = kxp<H>(), HH = H / 2;
+    __shared__ float2 tw[H];
+    __shared__ float2 exch[kLaneWarps][G * C::TILE];
+    const SpecRun& R = batch.run[NB == 1 ? 0 : blockIdx.z];
+    const SpectralArgs& a = R.a;
+    for (int i = threadIdx.x; i < H; i += blockDim.x) tw[i] = R.twiddle[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane / P, l = lane % P;
+    const int task = (blockIdx.x * kLaneWarps + warp) * G + g;   // (z, y < H/2)
+    if (task >= H * HH) return;    // whole groups; H * H/2 is a multiple of every group count
+    const int z = task / HH, y = task % HH;
+    float2* ex = &exch[warp][g * C::TILE];
+    const float u_scale = R.sc->u_scale;   // u_bar per accumulator unit
+    const float c0 = *R.voff;   // the v spectrum only feeds derivatives: remove a constant
+    const size_t row0 = (static_cast<size_t>(z) * H + y) * H;
+    const size_t row1 = row0 + static_cast<size_t>(HH) * H;
+    const float gamma_v = a.alpha * a.tau;
+    {
+        // v^n of the two rows as one complex row (reads v and m only)
+        float2 zv[Q];
+#pragma unroll
+        for (int m = 0; m < Q; ++m) {
+            const int x = l + P * m;
+            float vn[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const size_t o = (h ? row1 : row0) + x;
+                const float vv = R.v[o], mm = R.m[o];
+                vn[h] = (a.v_update == SIPF_V_IMPLICIT) ? __fdividef(vv, 1.0f + gamma_v * mm)
+                                                        : vv * (1.0f - gamma_v * mm);
+            }
+            zv[m] = make_float2(vn[0] - c0, vn[1] - c0);
+        }
+        F::template to_spectral<-1>(zv, l, ex, tw);
+        const size_t s0 = (static_cast<size_t>(z) * H + y) * KXP;
+        split_store<H, F>(zv, l, ex, R.specV + s0, R.specV + s0 + static_cast<size_t>(HH) * KXP);
+    }
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+        // the reaction on row y + h H/2: m* + i w*, v^n, the accumulator cleared
+        const size_t row = h ? row1 : row0;
+        float2 zr[Q];
+        // chunks of CH elements: all loads of a chunk before its stores (the
+        // stores may alias later loads, so they would otherwise wait)
+        constexpr int CH = 4;
+#pragma unroll
+        for (int m0 = 0; m0 < Q; m0 += CH) {
+            float vv[CH], mm[CH], ww[CH], uu[CH];
+            unsigned long long qq[CH];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const size_t o = row + l + P * (m0 + c);
+                vv[c] = R.v[o];
+                mm[c] = R.m[o];
+                ww[c] = R.w[o];
+                qq[c] = R.acc[o];
+                uu[c] = R.us ? R.us[o] : 0.f;
+            }
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const size_t o = row + l + P * (m0 + c);
+                R.acc[o] = 0ull;
+                const float u = acc_to_float(qq[c]) * u_scale;
+                float ms, ws, vn;
+                react(a, vv[c], mm[c], ww[c], u, R.us ? uu[c] : u, ms, ws, vn);
+                zr[m0 + c] = make_float2(ms, ws);
+                if (a.write_v) R.v_out[o] = vn;
+            }
+        }
+        if (a.do_mw) {
+            F::template to_spectral<-1>(zr, l, ex, tw);
+            const size_t s = (static_cast<size_t>(z) * H + y + h * HH) * KXP;
+            split_store<H, F>(zr, l, ex, R.specM + s, R.specW + s);
+        }
+    }
+}
+
+// y DFT of columns (z, kx) of the half spectra.  SIGN -1: M, W, V in place
+// (spatial layout in, spectral out).  SIGN +1: M, W, B in place, and V (or
+// its filtered copy) -> i k_x V, i k_y V (spectral layout in, spatial out).
+template <int H, int SIGN, int NB>
+__global__ void __launch_bounds__(32 * kLaneWarps) k_wy(const __grid_constant__ SpecBatch<NB> batch) {
+    using C = LaneShape<H>;
+    using F = WarpFFT<H, C::P, C::PITCH>;
+    constexpr int P = C::P, Q = F::Q, S = F::S, G = 32 / P, KXP = kxp<H>();
+    __shared__ float2 tw[H];
+    __shared__ float2 exch[kLaneWarps][G * C::TILE];
+    const SpecRun& R = batch.run[NB == 1 ? 0 : blockIdx.z];
+    const SpectralArgs& a = R.a;
+    const int field = blockIdx.y;   // 0 M, 1 W, 2 V or B, 3 -> i k_x V, 4 -> i k_y V
+    if (field < 2 && !a.do_mw) return;
+    for (int i = threadIdx.x; i < H; i += blockDim.x) tw[i] = R.twiddle[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane / P, l = lane % P;
+    const int col = (blockIdx.x * kLaneWarps + warp) * G + g;   // (z, kx)
+    if (col >= H * KXP) return;    // whole groups
+    const int z = col / KXP, kx = col % KXP;
+    float2* ex = &exch[warp][g * C::TILE];
+    const float2* vsrc = a.filter ? R.specA : R.specV;
+    const float2* src = field == 0 ? R.specM : field == 1 ? R.specW
+                      : field == 2 ? (SIGN < 0 ? R.specV : R.specB) : vsrc;
+    float2* dst = field == 0 ? R.specM : field == 1 ? R.specW
+                : field == 2 ? (SIGN < 0 ? R.specV : R.specB) : field == 3 ? R.specDx : R.specDy;
+    const size_t base = static_cast<size_t>(z) * H * KXP + kx;
+    float2 v[Q];
+    if constexpr (SIGN < 0) {
+#pragma unroll
+        for (int m = 0; m < Q; ++m) v[m] = src[base + static_cast<size_t>(l + P * m) * KXP];
+        F::template to_spectral<-1>(v, l, ex, tw);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+#pragma unroll
+            for (int k2 = 0; k2 < P; ++k2)
+                dst[base + static_cast<size_t>(S * l + s + Q * k2) * KXP] = v[s * P + k2];
+        }
+    } else {
+        const float kxs_ = (kx >= H / 2) ? 0.0f : a.two_pi_over_L * static_cast<float>(kx);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+#pragma unroll
+            for (int k2 = 0; k2 < P; ++k2) {
+                const int ky = S * l + s + Q * k2;
+                float2 val = src[base + static_cast<size_t>(ky) * KXP];
+                if (field >= 3) {
+                    float k;
+                    if (field == 3) {
+                        k = kxs_;
+                    } else {
+                        const int qy = signed_mode(ky, H);
+                        k = (qy == -H / 2) ? 0.0f : a.two_pi_over_L * static_cast<float>(qy);
+                    }
+                    val = make_float2(-k * val.y, k * val.x);
+                }
+                v[s * P + k2] = val;
+            }
+        }
+        F::template to_spatial<+1>(v, l, ex, tw);
+#pragma unroll
+        for (int m = 0; m < Q; ++m) dst[base + static_cast<size_t>(l + P * m) * KXP] = v[m];
+    }
+}
+
+// Inverse x DFT of packed rows: (m, w) rows, (dv/dx, dv/dy) rows and dv/dz
+// row pairs (y, y + H/2); scaled outputs.  A block takes PB row pairs
+// (y0 + t, y0 + t + H/2), t < PB, of one plane: 2 PB (m, w) rows, 2 PB
+// (dv/dx, dv/dy) rows and PB dv/dz pairs, each warp of one kind, so that the
+// four components of each node of the gather array are written close
+// together in time (they are written by three kinds of tasks).
+template <int H> struct WxInv {
+    static constexpr int G = 32 / LaneShape<H>::P;          // lines per warp
+    static constexpr int PB = 2 * G;                        // row pairs per block
+    static constexpr int WMW = 2 * PB / G, WD = 2 * PB / G, WB = PB / G;
+    static constexpr int WARPS = WMW + WD + WB;             // 10
+};
+
+template <int H, int NB>
+__global__ void __launch_bounds__(32 * WxInv<H>::WARPS)
+    k_wx_inverse(const __grid_constant__ SpecBatch<NB> batch) {
+    using C = LaneShape<H>;
+    using F = WarpFFT<H, C::P, C::PITCH>;
+    using X = WxInv<H>;
+    constexpr int P = C::P, Q = F::Q, S = F::S, G = X::G, PB = X::PB, KXP = kxp<H>(), HH = H / 2;
+    static_assert(HH % PB == 0, "whole blocks of row pairs");
+    __shared__ float2 tw[H];
+    __shared__ float2 exch[X::WARPS][G * C::TILE];
+    const SpecRun& R = batch.run[NB == 1 ? 0 : blockIdx.z];
+    const SpectralArgs& a = R.a;
+    for (int i = threadIdx.x; i < H; i += blockDim.x) tw[i] = R.twiddle[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane / P, l = lane % P;
+    constexpr int YB = HH / PB;                     // blocks of PB row pairs per plane
+    const int z = blockIdx.x / YB, y0 = (blockIdx.x % YB) * PB;
+    int kind, y;
+    if (warp < X::WMW) {
+        kind = 0;
+        const int t = warp * G + g;                 // 0 .. 2 PB - 1
+        y = y0 + (t % PB) + (t / PB) * HH;
+    } else if (warp < X::WMW + X::WD) {
+        kind = 1;
+        const int t = (warp - X::WMW) * G + g;
+        y = y0 + (t % PB) + (t / PB) * HH;
+    } else {
+        kind = 2;
+        y = y0 + (warp - X::WMW - X::WD) * G + g;   // pair (y, y + H/2)
+    }
+    if (kind == 0 && !a.do_mw) return;              // whole warps
+    float2* ex = &exch[warp][g * C::TILE];
+    const size_t r0 = (static_cast<size_t>(z) * H + y) * KXP;
+    const float2* p1;
+    const float2* p2;
+    if (kind == 0) {
+        p1 = R.specM + r0;
+        p2 = R.specW + r0;
+    } else if (kind == 1) {
+        p1 = R.specDx + r0;
+        p2 = R.specDy + r0;
+    } else {
+        p1 = R.specB + r0;
+        p2 = R.specB + r0 + static_cast<size_t>(HH) * KXP;
+    }
+    float2 v[Q];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+#pragma unroll
+        for (int k2 = 0; k2 < P; ++k2) v[s * P + k2] = pack_two<H>(p1, p2, S * l + s + Q * k2);
+    }
+    F::template to_spatial<+1>(v, l, ex, tw);
+    const size_t node0 = (static_cast<size_t>(z) * H + y) * H;
+    if (kind == 0) {
+        const float sc = a.out_scale;
+#pragma unroll
+        for (int m = 0; m < Q; ++m) {
+            const size_t node = node0 + l + P * m;
+            const float wv = v[m].y * sc;
+            R.m_out[node] = v[m].x * sc;
+            R.w_out[node] = wv;
+            R.G[4 * node + 3] = wv;
+        }
+    } else if (kind == 1) {
+        const float sxy = a.out_scale_xy;
+#pragma unroll
+        for (int m = 0; m < Q; ++m) {
+            const size_t node = node0 + l + P * m;
+            *reinterpret_cast<float2*>(R.G + 4 * node) = make_float2(v[m].x * sxy, v[m].y * sxy);
+        }
+    } else {
+        const float sc = a.out_scale;
+        const size_t node1 = node0 + static_cast<size_t>(HH) * H;
+#pragma unroll
+        for (int m = 0; m < Q; ++m) {
+            R.G[4 * (node0 + l + P * m) + 2] = v[m].x * sc;
+            R.G[4 * (node1 + l + P * m) + 2] = v[m].y * sc;
+        }
+    }
+}
+
+// Blocks covering n lines (groups of 32 / P lanes in kLaneWarps warps).
+template <int H> constexpr int warp_blocks(int n) {
+    constexpr int per_block = kLaneWarps * (32 / LaneShape<H>::P);
+    return (n + per_block - 1) / per_block;
+}
+
+// The warp pipeline's passes, grouped like the fused ones.
+template <int H, int NB>
+cudaError_t warp_pass(const SpecBatch<NB>& batch, int nb, int pass, int device, cudaStream_t s) {
+    constexpr int KXP = kxp<H>(), NT = 32 * kLaneWarps, KB = zcols<H>();
+    constexpr size_t smz = (static_cast<size_t>(H) * KB + H) * sizeof(float2);
+    static int configured_device = -1;
+    if (configured_device != device) {
+        cudaFuncSetAttribute(k_z_multiply<H, NB, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smz));
+        configured_device = device;
+    }
+    if (pass == 0) {
+        k_wx_forward<H, NB><<<dim3(warp_blocks<H>(H * (H / 2)), 1, nb), NT, 0, s>>>(batch);
+        k_wy<H, -1, NB><<<dim3(warp_blocks<H>(H * KXP), 3, nb), NT, 0, s>>>(batch);
+    } else if (pass == 1) {
+        k_z_multiply<H, NB, 0><<<dim3(H, 4, NB == 1 ? (KXP + KB - 1) / KB : nb), Cfg<H>::NT2, smz,
+                                 s>>>(batch);
+    } else {
+        k_wy<H, +1, NB><<<dim3(warp_blocks<H>(H * KXP), 5, nb), NT, 0, s>>>(batch);
+        k_wx_inverse<H, NB><<<dim3(H * (H / 2 / WxInv<H>::PB), 1, nb), 32 * WxInv<H>::WARPS, 0,
+                              s>>>(batch);
+    }
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- per-axis passes (H > 128)
@@ -673,7 +1242,7 @@ cudaError_t spectral_pass_split_v(sipf_ctx* c, const SpectralArgs& a, int pass) 
         SpecBatch<1> one;
         one.run[0] = spec_run(c, a);
         k_z_multiply<H, 1, V><<<dim3(H, 4, (KXP + zcols<H>() - 1) / zcols<H>()), Cfg<H>::NT2, smz,
-                             c->stream>>>(one);
+                               c->stream>>>(one);
     } else {
         // inverse y: M, W and B in place; V (or its filtered copy) -> i k_x V, i k_y V
         k_sx_columns<H, +1, V><<<gy, kSxNT, smy2, c->stream>>>(
@@ -700,6 +1269,10 @@ void configure_fused(int device) {
     if (configured_device == device) return;
     cudaFuncSetAttribute(k_forward_xy<H, NB, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(FusedSmem<H>::fwd));
+    if constexpr (has_pair_forward<H>())
+        cudaFuncSetAttribute(k_forward_xy_pair<H, NB, V>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(PairSmem<H>::bytes));
     cudaFuncSetAttribute(k_z_multiply<H, NB, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(FusedSmem<H>::z));
     cudaFuncSetAttribute(k_inverse_xy<H, NB, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -713,7 +1286,12 @@ cudaError_t fused_pass(const SpecBatch<NB>& batch, int nb, int pass, int device,
     configure_fused<H, NB, V>(device);
     constexpr int KXP = kxp<H>();
     if (pass == 0) {
-        k_forward_xy<H, NB, V><<<dim3(H, nb), Cfg<H>::NT1, FusedSmem<H>::fwd, s>>>(batch);
+        if constexpr (has_pair_forward<H>()) {
+            k_forward_xy_pair<H, NB, V>
+                <<<dim3(2 * H, nb), Cfg<H>::NT1 / 2, PairSmem<H>::bytes, s>>>(batch);
+        } else {
+            k_forward_xy<H, NB, V><<<dim3(H, nb), Cfg<H>::NT1, FusedSmem<H>::fwd, s>>>(batch);
+        }
     } else if (pass == 1) {
         const int kt = (KXP + zcols<H>() - 1) / zcols<H>();
         k_z_multiply<H, NB, V><<<dim3(H, 4, NB == 1 ? kt : nb), Cfg<H>::NT2, FusedSmem<H>::z, s>>>(

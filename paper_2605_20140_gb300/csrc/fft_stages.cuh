@@ -347,5 +347,70 @@ __device__ __forceinline__ void fft_axis(float2* buf, const float2* tw) {
     fft_axis_at<L, V, NTRANS, NT, SIGN>(buf, tw, Strided<TS, ES>{});
 }
 
+// A length-L DFT spread over a group of P lanes of one warp (Q = L / P
+// elements per lane, S = Q / P), as the two factors of L = P Q
+// (Cooley-Tukey) with one exchange through the group's shared-memory tile:
+//  * spatial layout: lane l holds n = l + P m in v[m], m < Q;
+//  * spectral layout: lane l holds k = k1 + Q k2 with k1 = S l + s in
+//    v[s P + k2], s < S, k2 < P.
+// to_spectral: DFT_Q over m, twiddle w_L^(l k1), exchange, DFT_P over l.
+// to_spatial reverses it: DFT_P over k2, twiddle w_L^(n1 k1), exchange,
+// DFT_Q over k1.  The tile holds P rows of PITCH float2; __syncwarp orders
+// the exchange, so no block barrier is involved.
+template <int L, int P, int PITCH>
+struct WarpFFT {
+    static constexpr int Q = L / P, S = Q / P;
+    static_assert(Q % P == 0 && PITCH >= Q, "warp FFT shape");
+
+    template <int SIGN>
+    static __device__ __forceinline__ float2 twiddle(const float2* tw, int j) {
+        float2 w = tw[j];
+        if (SIGN > 0) w.y = -w.y;
+        return w;
+    }
+
+    template <int SIGN>
+    static __device__ __forceinline__ void to_spectral(float2 (&v)[Q], int l, float2* ex,
+                                                       const float2* tw) {
+        dft<Q, SIGN>(v);
+#pragma unroll
+        for (int k1 = 1; k1 < Q; ++k1) v[k1] = cmul(v[k1], twiddle<SIGN>(tw, l * k1));
+        __syncwarp();
+#pragma unroll
+        for (int k1 = 0; k1 < Q; ++k1) ex[l * PITCH + k1] = v[k1];
+        __syncwarp();
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            float2 u[P];
+#pragma unroll
+            for (int j = 0; j < P; ++j) u[j] = ex[j * PITCH + S * l + s];
+            dft<P, SIGN>(u);
+#pragma unroll
+            for (int k2 = 0; k2 < P; ++k2) v[s * P + k2] = u[k2];
+        }
+    }
+
+    template <int SIGN>
+    static __device__ __forceinline__ void to_spatial(float2 (&v)[Q], int l, float2* ex,
+                                                      const float2* tw) {
+        __syncwarp();
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            float2 u[P];
+#pragma unroll
+            for (int k2 = 0; k2 < P; ++k2) u[k2] = v[s * P + k2];
+            dft<P, SIGN>(u);
+            const int k1 = S * l + s;
+            ex[k1] = u[0];
+#pragma unroll
+            for (int j = 1; j < P; ++j) ex[j * PITCH + k1] = cmul(u[j], twiddle<SIGN>(tw, j * k1));
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k1 = 0; k1 < Q; ++k1) v[k1] = ex[l * PITCH + k1];
+        dft<Q, SIGN>(v);
+    }
+};
+
 }  // namespace fftk
 }  // namespace sipf

@@ -74,29 +74,50 @@ __device__ __forceinline__ float neg2_log_unit(float u) {
 // sqrt(x) for 0 < x < 2^126: x times the hardware reciprocal square root.
 __device__ __forceinline__ float sqrt_pos(float x) { return __fmul_rn(x, rsqrtf(x)); }
 
-// (cos 2 pi u, sin 2 pi u) for u in [0, 1): 8u = n + f with n = round(8u),
-// exact because u has at most 24 significant bits; phi = f pi/4 lies in
-// [-pi/8, pi/8], where the Taylor series to phi^7 (sine) and phi^6 (cosine)
-// leave remainders below 2e-8; then a rotation by n eighths of a turn.
+// cos 2 pi u and sin 2 pi u for u in (0, 1) with at most 24 significant
+// bits.  a = min(u, 1 - u) and b = min(a, 1/2 - a) are exact, and with
+// theta = 2 pi b in [0, pi/2]: cos 2 pi u = cos theta, negated for a > 1/4,
+// and sin 2 pi u = sin theta, negated for u > 1/2.  cos theta and
+// sin theta / b come from their Taylor series to theta^12 and theta^13,
+// evaluated in b^2 (remainders below 7e-9).
+struct QuarterTurn {
+    float b, p;          // b in [0, 1/4], p = b^2
+    bool neg_cos;        // a > 1/4
+};
+__device__ __forceinline__ QuarterTurn quarter_turn(float u) {
+    const float a = fminf(u, __fsub_rn(1.0f, u));
+    QuarterTurn q;
+    q.b = fminf(a, __fsub_rn(0.5f, a));
+    q.p = __fmul_rn(q.b, q.b);
+    q.neg_cos = a > 0.25f;
+    return q;
+}
+__device__ __forceinline__ float cos_series(float p) {
+    float c = __fmaf_rn(p, 7.903536371318465f, -26.426256783374388f);
+    c = __fmaf_rn(p, c, 60.24464137187664f);
+    c = __fmaf_rn(p, c, -85.45681720669371f);
+    c = __fmaf_rn(p, c, 64.93939402266828f);
+    c = __fmaf_rn(p, c, -19.739208802178716f);
+    return __fmaf_rn(p, c, 1.0f);
+}
+__device__ __forceinline__ float sin_series(float b, float p) {
+    float c = __fmaf_rn(p, 3.8199525848482803f, -15.094642576822984f);
+    c = __fmaf_rn(p, c, 42.058693944897634f);
+    c = __fmaf_rn(p, c, -76.70585975306136f);
+    c = __fmaf_rn(p, c, 81.60524927607504f);
+    c = __fmaf_rn(p, c, -41.341702240399755f);
+    c = __fmaf_rn(p, c, 6.283185307179586f);
+    return __fmul_rn(b, c);
+}
+__device__ __forceinline__ float cos_2pi(float u) {
+    const QuarterTurn q = quarter_turn(u);
+    const float c = cos_series(q.p);
+    return q.neg_cos ? -c : c;
+}
 __device__ __forceinline__ float2 cis_2pi(float u) {
-    const float t = __fmul_rn(u, 8.0f);
-    const float r = __fadd_rn(t, 12582912.0f);          // 1.5 2^23 + round(t)
-    const int n = __float_as_int(r) - 0x4B400000;
-    const float phi = __fmul_rn(__fsub_rn(t, __fsub_rn(r, 12582912.0f)), 0.78539816339744831f);
-    const float p = __fmul_rn(phi, phi);
-    const float qs = __fmaf_rn(p, __fmaf_rn(p, -1.0f / 5040.0f, 1.0f / 120.0f), -1.0f / 6.0f);
-    const float sn = __fmaf_rn(__fmul_rn(phi, p), qs, phi);
-    const float qc = __fmaf_rn(p, __fmaf_rn(p, -1.0f / 720.0f, 1.0f / 24.0f), -0.5f);
-    const float cs = __fmaf_rn(p, qc, 1.0f);
-    // odd n: rotate by pi/4 first
-    const bool odd = n & 1;
-    const float ca = odd ? __fmul_rn(__fsub_rn(cs, sn), 0.70710678118654752f) : cs;
-    const float sa = odd ? __fmul_rn(__fadd_rn(cs, sn), 0.70710678118654752f) : sn;
-    // quarter turns q: (c, s) -> (c, s), (-s, c), (-c, -s), (s, -c)
-    const int q = (n >> 1) & 3;
-    const float c2 = (q & 1) ? sa : ca;
-    const float s2 = (q & 1) ? ca : sa;
-    return make_float2(((q + 1) & 2) ? -c2 : c2, (q & 2) ? -s2 : s2);
+    const QuarterTurn q = quarter_turn(u);
+    const float c = cos_series(q.p), sn = sin_series(q.b, q.p);
+    return make_float2(q.neg_cos ? -c : c, u > 0.5f ? -sn : sn);
 }
 
 // Box-Muller on the four words of one Philox block: three standard normals,
@@ -105,8 +126,8 @@ __device__ __forceinline__ float3 box_muller(const uint4 b) {
     const float r01 = sqrt_pos(neg2_log_unit(unit_open(b.x)));
     const float r23 = sqrt_pos(neg2_log_unit(unit_open(b.z)));
     const float2 e1 = cis_2pi(unit_open(b.y));
-    const float2 e3 = cis_2pi(unit_open(b.w));
-    return make_float3(__fmul_rn(r01, e1.x), __fmul_rn(r01, e1.y), __fmul_rn(r23, e3.x));
+    const float c3 = cos_2pi(unit_open(b.w));
+    return make_float3(__fmul_rn(r01, e1.x), __fmul_rn(r01, e1.y), __fmul_rn(r23, c3));
 }
 
 // 2^x (hardware approximation, relative error about 2^-22).
@@ -116,10 +137,9 @@ __device__ __forceinline__ float exp2_approx(float x) {
     return y;
 }
 
-// ln(1 + x) for |x| <= 1/16: 2 atanh(s), s = x/(2 + x), |s| <= 0.0323,
+// ln(1 + x) = 2 atanh(s) with s = x/(2 + x), for |x| <= 1/16 (|s| <= 0.0323),
 // summed to s^7 (remainder below 1e-12 relative).
-__device__ __forceinline__ float log1p_small(float x) {
-    const float s = __fdividef(x, __fadd_rn(2.0f, x));
+__device__ __forceinline__ float log1p_from_s(float s) {
     const float z = __fmul_rn(s, s);
     return __fmul_rn(s, __fmaf_rn(z, __fmaf_rn(z, __fmaf_rn(z, 2.0f / 7.0f, 2.0f / 5.0f),
                                                 2.0f / 3.0f),
@@ -178,12 +198,6 @@ __device__ __forceinline__ Cell locate_clamped(float x, float y, float z, int H)
 // i mod H for -H <= i < 2H.
 __device__ __forceinline__ int wrap_index(int i, int H) { return i < 0 ? i + H : (i >= H ? i - H : i); }
 
-// round(v) for 0 <= v < 2^22, ties to even (as __float2uint_rn): the low
-// mantissa bits of 2^23 + v.
-__device__ __forceinline__ uint32_t round_small(float v) {
-    return __float_as_uint(__fadd_rn(v, 8388608.0f)) - 0x4B000000u;
-}
-
 __device__ __forceinline__ int tile_of(int cx, int cy, int cz, int T) {
     return ((cz >> 3) * T + (cy >> 3)) * T + (cx >> 3);
 }
@@ -193,52 +207,59 @@ __device__ __forceinline__ uint32_t cell_key(int cx, int cy, int cz, int T) {
            static_cast<uint32_t>(((cz & 7) << 6) | ((cy & 7) << 3) | (cx & 7));
 }
 
-// Trilinear interpolation of the float4 field (dv/dx, dv/dy, dv/dz, w)
-// (K_h = h^3 R_h, Alg. 2): along x, then y, then z, with explicit rounding.
-__device__ __forceinline__ float4 gather4(const float4* __restrict__ G, const Cell& c, int H) {
+// The eight trilinear weights R_h(X - node) h^3 of a particle's cell corners
+// (Alg. 1, 2), corner k at offset (k & 1, (k >> 1) & 1, k >> 2): products of
+// (1 - f, f) along each axis.  The deposit and the gather share them.
+__device__ __forceinline__ void corner_weights(const Cell& c, float (&W)[8]) {
+    const float wx0 = __fsub_rn(1.0f, c.fx), wy0 = __fsub_rn(1.0f, c.fy);
+    const float wz0 = __fsub_rn(1.0f, c.fz);
+    const float xy[4] = {__fmul_rn(wx0, wy0), __fmul_rn(c.fx, wy0), __fmul_rn(wx0, c.fy),
+                         __fmul_rn(c.fx, c.fy)};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        W[k] = __fmul_rn(xy[k], wz0);
+        W[4 + k] = __fmul_rn(xy[k], c.fz);
+    }
+}
+
+// sum_k W[k] a[k] per component (K_h = h^3 R_h, Alg. 2).
+__device__ __forceinline__ float4 interpolate8(const float4 (&a)[8], const float (&W)[8]) {
+    float4 r = make_float4(__fmul_rn(W[0], a[0].x), __fmul_rn(W[0], a[0].y),
+                           __fmul_rn(W[0], a[0].z), __fmul_rn(W[0], a[0].w));
+#pragma unroll
+    for (int k = 1; k < 8; ++k) {
+        r.x = __fmaf_rn(W[k], a[k].x, r.x);
+        r.y = __fmaf_rn(W[k], a[k].y, r.y);
+        r.z = __fmaf_rn(W[k], a[k].z, r.z);
+        r.w = __fmaf_rn(W[k], a[k].w, r.w);
+    }
+    return r;
+}
+
+// Interpolation of the float4 field (dv/dx, dv/dy, dv/dz, w) from global
+// memory (periodic; the cell is clamped).
+__device__ __forceinline__ float4 gather4(const float4* __restrict__ G, const Cell& c, int H,
+                                          const float (&W)[8]) {
     const int cx = clamp_cell(c.cx, H), cy = clamp_cell(c.cy, H), cz = clamp_cell(c.cz, H);
     const int x1 = cx + 1 < H ? cx + 1 : 0;
     const int y1 = cy + 1 < H ? cy + 1 : 0;
     const int z1 = cz + 1 < H ? cz + 1 : 0;
-    const int r00 = (cz * H + cy) * H, r10 = (cz * H + y1) * H;
-    const int r01 = (z1 * H + cy) * H, r11 = (z1 * H + y1) * H;
-    const float4 a000 = __ldg(G + r00 + cx), a100 = __ldg(G + r00 + x1);
-    const float4 a010 = __ldg(G + r10 + cx), a110 = __ldg(G + r10 + x1);
-    const float4 a001 = __ldg(G + r01 + cx), a101 = __ldg(G + r01 + x1);
-    const float4 a011 = __ldg(G + r11 + cx), a111 = __ldg(G + r11 + x1);
-    const float wx0 = __fsub_rn(1.0f, c.fx), wy0 = __fsub_rn(1.0f, c.fy),
-                wz0 = __fsub_rn(1.0f, c.fz);
-#define SIPF_TRI(f)                                                                      \
-    __fmaf_rn(c.fz,                                                                      \
-              __fmaf_rn(c.fy, __fmaf_rn(c.fx, a111.f, __fmul_rn(wx0, a011.f)),           \
-                        __fmul_rn(wy0, __fmaf_rn(c.fx, a101.f, __fmul_rn(wx0, a001.f)))), \
-              __fmul_rn(wz0,                                                             \
-                        __fmaf_rn(c.fy, __fmaf_rn(c.fx, a110.f, __fmul_rn(wx0, a010.f)), \
-                                  __fmul_rn(wy0, __fmaf_rn(c.fx, a100.f, __fmul_rn(wx0, a000.f))))))
-    const float4 r = make_float4(SIPF_TRI(x), SIPF_TRI(y), SIPF_TRI(z), SIPF_TRI(w));
-#undef SIPF_TRI
-    return r;
+    float4 a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int nx = (k & 1) ? x1 : cx, ny = ((k >> 1) & 1) ? y1 : cy, nz = (k >> 2) ? z1 : cz;
+        a[k] = __ldg(G + (nz * H + ny) * H + nx);
+    }
+    return interpolate8(a, W);
 }
 
-// The same interpolation from a tile's 9^3 node block in shared memory
-// (node (lx, ly, lz) at (lz * 9 + ly) * 9 + lx).
-__device__ __forceinline__ float4 gather4_block(const float4* B, const Cell& c, int base) {
-    const float4 a000 = B[base], a100 = B[base + 1];
-    const float4 a010 = B[base + 9], a110 = B[base + 10];
-    const float4 a001 = B[base + 81], a101 = B[base + 82];
-    const float4 a011 = B[base + 90], a111 = B[base + 91];
-    const float wx0 = __fsub_rn(1.0f, c.fx), wy0 = __fsub_rn(1.0f, c.fy),
-                wz0 = __fsub_rn(1.0f, c.fz);
-#define SIPF_TRI(f)                                                                      \
-    __fmaf_rn(c.fz,                                                                      \
-              __fmaf_rn(c.fy, __fmaf_rn(c.fx, a111.f, __fmul_rn(wx0, a011.f)),           \
-                        __fmul_rn(wy0, __fmaf_rn(c.fx, a101.f, __fmul_rn(wx0, a001.f)))), \
-              __fmul_rn(wz0,                                                             \
-                        __fmaf_rn(c.fy, __fmaf_rn(c.fx, a110.f, __fmul_rn(wx0, a010.f)), \
-                                  __fmul_rn(wy0, __fmaf_rn(c.fx, a100.f, __fmul_rn(wx0, a000.f))))))
-    const float4 r = make_float4(SIPF_TRI(x), SIPF_TRI(y), SIPF_TRI(z), SIPF_TRI(w));
-#undef SIPF_TRI
-    return r;
+// The same from a tile's 9^3 node block in shared memory (node (lx, ly, lz)
+// at (lz * 9 + ly) * 9 + lx).
+__device__ __forceinline__ float4 gather4_block(const float4* B, int base, const float (&W)[8]) {
+    float4 a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = B[base + (k & 1) + ((k >> 1) & 1) * 9 + (k >> 2) * 81];
+    return interpolate8(a, W);
 }
 
 // Periodic wrap into [0, H); a result that rounds to H becomes 0.
@@ -300,7 +321,11 @@ __device__ __forceinline__ int round_signed_small(float v) {
 // Wrap of a pushed position, all three axes at once: positions normally stay
 // in [0, H), so the full periodic reduction runs only when one leaves it.
 __device__ __forceinline__ void wrap3(float& x, float& y, float& z, float Hf, int* bad) {
-    if (!(x >= 0.0f && x < Hf && y >= 0.0f && y < Hf && z >= 0.0f && z < Hf)) {
+    // [0, H) as bit patterns: non-negative floats order like their bits, and
+    // negative values, infinities and NaNs compare above H (-0 goes to wrap,
+    // which keeps it)
+    const uint32_t hb = __float_as_uint(Hf);
+    if (!(__float_as_uint(x) < hb && __float_as_uint(y) < hb && __float_as_uint(z) < hb)) {
         x = wrap(x, Hf, bad);
         y = wrap(y, Hf, bad);
         z = wrap(z, Hf, bad);
@@ -313,6 +338,19 @@ __device__ __forceinline__ int tile_at(float x, float y, float z, int T) {
     const int cy = static_cast<int>(__float_as_uint(__fadd_rz(y, 8388608.0f)) - 0x4B000000u);
     const int cz = static_cast<int>(__float_as_uint(__fadd_rz(z, 8388608.0f)) - 0x4B000000u);
     return ((cz >> 3) * T + (cy >> 3)) * T + (cx >> 3);
+}
+
+// Asks the copy engine to bring the 16-byte-aligned interior of elements
+// [beg, end) of a particle array into L2 (a bulk prefetch: no registers, no
+// completion to wait for).  The range lies inside the array.
+__device__ __forceinline__ void prefetch_l2(const void* base, size_t elem, int beg, int end) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(base);
+    const uintptr_t lo = (a + static_cast<size_t>(beg) * elem + 15) & ~static_cast<uintptr_t>(15);
+    const uintptr_t hi = (a + static_cast<size_t>(end) * elem) & ~static_cast<uintptr_t>(15);
+    if (hi > lo)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo),
+                     "r"(static_cast<uint32_t>(hi - lo))
+                     : "memory");
 }
 
 // Mask of the lanes below this one.
@@ -406,6 +444,18 @@ __device__ __forceinline__ void step_items(const StepView& v, const Keys& keys, 
     for (int item_idx = i_lo; item_idx <= i_hi; ++item_idx) {
         const Item it = item_idx < i_hi ? v.items[item_idx] : Item{-1, 0, 0, 0, 0, 0, 0, 0};
         const int tile = it.tile;
+        if (threadIdx.x < 5 && item_idx + 1 < i_hi) {
+            // the next item's particles are read in about one item's time: have
+            // them in L2 by then (one array per thread)
+            const Item nx = v.items[item_idx + 1];
+            const int k = threadIdx.x;
+            const void* arr = k == 0 ? static_cast<const void*>(src.sx)
+                            : k == 1 ? static_cast<const void*>(src.sy)
+                            : k == 2 ? static_cast<const void*>(src.sz)
+                            : k == 3 ? static_cast<const void*>(src.dl)
+                                     : static_cast<const void*>(src.id);
+            prefetch_l2(arr, k == 3 ? sizeof(double) : sizeof(float), nx.beg, nx.end);
+        }
         const bool change = tile != cur || tile < 0;
         // every thread moves its own nodes (j = threadIdx.x + k kNT) from dep
         // to dep64 and from dep64 to the grid, so no barrier is needed between
@@ -485,23 +535,20 @@ __device__ __forceinline__ void step_items(const StepView& v, const Keys& keys, 
             const bool in_tile = binned && ((lx | ly | lz) & ~7) == 0;
             if (binned && valid && !in_tile) bad |= 2;   // bucket does not match position
 
+            float W[8];
+            corner_weights(c, W);
             if (do_deposit && valid) {
                 // a_p R_h(X_p, node) h^3 in units of exp(logref) 2^-S as integers
-                const float wx0 = __fsub_rn(1.0f, c.fx), wy0 = __fsub_rn(1.0f, c.fy);
-                const float wz0 = __fsub_rn(1.0f, c.fz);
                 if constexpr (ORDER == 2) {
                     const float ea = exp2_approx(
                         fminf(__fmaf_rn(__double2float_rn(pl), 1.4426950408889634f, dshift),
                               kMaxLog2Unit));
-                    const float e0 = __fmul_rn(ea, wz0), e1 = __fmul_rn(ea, c.fz);
-                    const float xy[4] = {__fmul_rn(wx0, wy0), __fmul_rn(c.fx, wy0),
-                                         __fmul_rn(wx0, c.fy), __fmul_rn(c.fx, c.fy)};
+                    // round(ea W[k]) in one rounding: ea W[k] < 2^22, so the
+                    // fused 2^23 + ea W[k] has unit spacing
                     uint32_t q[8];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        q[k] = round_small(__fmul_rn(e0, xy[k]));
-                        q[4 + k] = round_small(__fmul_rn(e1, xy[k]));
-                    }
+                    for (int k = 0; k < 8; ++k)
+                        q[k] = __float_as_uint(__fmaf_rn(ea, W[k], 8388608.0f)) - 0x4B000000u;
                     if (in_tile) {
                         // particles of a bucket are in random cells of the tile, so lanes
                         // rarely collide: one shared 32-bit atomic per corner
@@ -531,6 +578,8 @@ __device__ __forceinline__ void step_items(const StepView& v, const Keys& keys, 
                     // the bilinear weight of the other two axes (cases of R_h^(4))
                     const float ea = fminf(__fmul_rn(expf(__double2float_rn(pl)), dscale), 741455.0f);
                     const float fx = c.fx, fy = c.fy, fz = c.fz;
+                    const float wx0 = __fsub_rn(1.0f, fx), wy0 = __fsub_rn(1.0f, fy);
+                    const float wz0 = __fsub_rn(1.0f, fz);
                     const float bx = __fmul_rn(fx, wx0), by = __fmul_rn(fy, wy0), bz = __fmul_rn(fz, wz0);
                     const float g = __fadd_rn(1.0f, __fmul_rn(0.5f, __fadd_rn(__fadd_rn(bx, by), bz)));
                     const float sx[2] = {__fmul_rn(__fmul_rn(bx, __fsub_rn(2.0f, fx)), -1.0f / 6.0f),
@@ -572,12 +621,19 @@ __device__ __forceinline__ void step_items(const StepView& v, const Keys& keys, 
 
             if (do_move) {
                 if (v.push && valid) {
-                    const float4 g = in_tile ? gather4_block(gblk, c, (lz * 9 + ly) * 9 + lx)
-                                             : gather4(G, c, H);
-                    // mass factor 1 + tau (rho(w_H) - 1), rho(w) = 2w/(1+w) (Eq. u_hat_update)
-                    const float rho = __fdividef(__fmul_rn(2.0f, g.w), __fadd_rn(1.0f, g.w));
-                    const float x = __fmul_rn(v.tau, __fsub_rn(rho, 1.0f));
-                    const float inc = v.tau <= 0.0625f ? log1p_small(x) : log1pf(x);
+                    const float4 g = in_tile ? gather4_block(gblk, (lz * 9 + ly) * 9 + lx, W)
+                                             : gather4(G, c, H, W);
+                    // mass factor 1 + x, x = tau (rho(w_H) - 1), rho(w) = 2w/(1+w)
+                    // (Eq. u_hat_update); ln(1 + x) = 2 atanh(x/(2 + x)) and
+                    // x/(2 + x) = n/(2(1 + w) + n) with n = tau (w - 1)
+                    float inc;
+                    if (v.tau <= 0.0625f) {
+                        const float n = __fmaf_rn(v.tau, g.w, -v.tau);
+                        inc = log1p_from_s(__fdividef(n, __fadd_rn(__fmaf_rn(2.0f, g.w, 2.0f), n)));
+                    } else {
+                        const float rho = __fdividef(__fmul_rn(2.0f, g.w), __fadd_rn(1.0f, g.w));
+                        inc = log1pf(__fmul_rn(v.tau, __fsub_rn(rho, 1.0f)));
+                    }
                     pl = pl + static_cast<double>(inc);
                     // Euler-Maruyama push in grid units
                     const float3 nz = box_muller(keys(make_uint4(step_n, 0u, pid, 0u)));

@@ -156,6 +156,8 @@ struct SpecRun {
     float2* specV;
     float2* specB;
     float2* specA;                // filtered v spectrum (filter on only)
+    float2* specDx;               // i k_x V and i k_y V after the inverse y pass
+    float2* specDy;               // (per-axis pipelines only)
     const float2* twiddle;
     float* voff;
     const StepScalars* sc;        // scalars of the step (u_bar per accumulator unit)
@@ -345,6 +347,7 @@ int resample_device(sipf_ctx* c, int src, int dst, double ratio, int* done, std:
 cudaError_t launch_spectral_step(sipf_ctx* c, const SpectralArgs& a);
 cudaError_t launch_spectral_pass(sipf_ctx* c, const SpectralArgs& a, int pass);
 // The context's data for the fused spectral passes (its current buffer parity).
+bool has_warp_pipeline(int H);
 SpecRun spec_run(const sipf_ctx* c, const SpectralArgs& a);
 // One fused spectral pass (0 forward, 1 z, 2 inverse) over n <= kMaxBatch
 // runs of grid size H <= 128, in one launch.

@@ -205,7 +205,7 @@ def test_tuning_table_is_parsed_and_looked_up(lib, tmp_path):
     assert sipf.sipf_tuning_lookup(128, 500)["step_blocks_per_sm"] == 3
     assert sipf.sipf_tuning_lookup(96, 1000) is None
     assert sipf.sipf_tuning_lookup(64, 10) is None
-    for text in ("128 1 10 2 0 8 32\n", "128 1 10 0 0 4 32\n", "128 1 10 0 0 8 64\n",
+    for text in ("128 1 10 3 0 8 32\n", "128 1 10 0 0 4 32\n", "128 1 10 0 0 8 64\n",
                  "128 10 1 0 0 8 32\n", "128 1 10 0\n"):
         bad = tmp_path / "bad.txt"
         bad.write_text(text)
@@ -222,7 +222,7 @@ def test_autotuner_candidates_are_valid():
     cands = autotune.candidates()
     assert len(cands) == len({tuple(sorted(c.items())) for c in cands}) >= 12
     for c in cands:
-        assert c["radix_plan"] in (0, 1) and 0 <= c["step_blocks_per_sm"] <= 32
+        assert c["radix_plan"] in (0, 1, 2) and 0 <= c["step_blocks_per_sm"] <= 32
         assert 8 <= c["bucket_slack_div"] <= 1024 and 0 <= c["bucket_slack_add"] <= 32
     for H, lo, hi, rep, recipe in autotune.TARGETS:
         assert lo <= rep <= hi and recipe in ("headline", "large")

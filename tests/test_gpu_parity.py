@@ -249,12 +249,18 @@ def test_fourth_order_deposit_matches_oracle(name, H, N):
         assert u.min() < 0       # the negative star weights survive the integer path
 
 
-@pytest.mark.parametrize("plan", [0, 1])
+WARP_PIPELINE_H = (64, 128, 256)
+
+
+@pytest.mark.parametrize("plan", [0, 1, 2])
 @pytest.mark.parametrize("H", [8, 16, 24, 32, 48, 64, 72, 96, 128, 144, 192, 216, 256])
 def test_initial_spectral_gradient(H, plan):
-    """grad v^(0) against the oracle's spectral gradient, with either radix
+    """grad v^(0) against the oracle's spectral gradient, with each radix
     plan of the transforms (plan 1: the radix-6 and radix-12 stages, or the
-    stage order reversed)."""
+    stage order reversed; plan 2: the per-axis pipeline of transforms held by
+    groups of lanes)."""
+    if plan == 2 and H not in WARP_PIPELINE_H:
+        pytest.skip("plan 2 exists for H = 64, 128, 256")
     wl = workload("small", H=H, N=1024)
     sim = run_gpu(wl, 0, plan=plan)
     f = sim.fields(sipf.FIELD_GX | sipf.FIELD_GY | sipf.FIELD_GZ)
@@ -282,13 +288,15 @@ def test_gradient_of_a_sine_mode_closed_form():
         assert np.max(np.abs(f[name] - ref)) <= 1e-5 * np.abs(ref).max(), name
 
 
-@pytest.mark.parametrize("plan", [0, 1])
+@pytest.mark.parametrize("plan", [0, 1, 2])
 @pytest.mark.parametrize("mode,H", [(0, 32), (1, 32), (0, 256), (0, 48), (1, 72), (0, 96),
-                                    (0, 144), (1, 192)])
+                                    (0, 144), (1, 192), (1, 64), (0, 128), (1, 256)])
 def test_single_mode_decay(mode, H, plan):
     """Massless particles, gamma = alpha = 0: one step multiplies a Fourier
     mode of m by 1/(1 + tau beta + tau Dm |k|^2) (or the exponential) and of
     w by 1/(1 + tau + tau Dw |k|^2)."""
+    if plan == 2 and H not in WARP_PIPELINE_H:
+        pytest.skip("plan 2 exists for H = 64, 128, 256")
     L, tau = 1.0, 0.01
     p = Params(chi=0.0, Du=0.0, Dm=0.03, Dw=0.07, alpha=0.0, beta=0.4, gamma=0.0, diffusion=mode)
     q = np.arange(H) * (L / H)
@@ -348,6 +356,19 @@ def test_steps_match_oracle_radix3_grids(H, plan):
     radix-12 ones): ten steps against the oracle."""
     wl = workload("small", H=H, N=1 << 15)
     sim = run_gpu(wl, 10, plan=plan)
+    st = O.run(oracle_state(wl), wl.dt, 10)
+    compare(sim, st, wl)
+    sim.close()
+
+
+@pytest.mark.parametrize("H,filtered", [(64, False), (64, True), (128, False)])
+def test_steps_match_oracle_warp_pipeline(H, filtered):
+    """The per-axis pipeline of lane-group transforms (radix plan 2): ten
+    steps against the oracle, with the low-pass filter off and on."""
+    wl = workload("small", H=H, N=1 << 16)
+    if filtered:
+        wl.params = dataclasses.replace(wl.params, H0=H ** (8 / 13))
+    sim = run_gpu(wl, 10, plan=2)
     st = O.run(oracle_state(wl), wl.dt, 10)
     compare(sim, st, wl)
     sim.close()
@@ -785,6 +806,8 @@ def test_tuning_of_slack_and_blocks_leaves_results_bit_identical():
             np.testing.assert_array_equal(f[k], base[0][k], err_msg=f"{t} {k}")
         np.testing.assert_array_equal(s_, base[1])
         np.testing.assert_array_equal(l_, base[2])
-    f, _, _ = run(radix_plan=1, step_blocks_per_sm=0, bucket_slack_div=8, bucket_slack_add=32)
-    for k in ("v", "m", "w"):
-        assert rel_l2(f[k], base[0][k].astype(np.float64)) <= 1e-6, k
+    for plan in (1, 2):
+        f, _, _ = run(radix_plan=plan, step_blocks_per_sm=0, bucket_slack_div=8,
+                      bucket_slack_add=32)
+        for k in ("v", "m", "w"):
+            assert rel_l2(f[k], base[0][k].astype(np.float64)) <= 1e-6, (plan, k)
