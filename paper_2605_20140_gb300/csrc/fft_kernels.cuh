@@ -6,7 +6,6 @@
 // parallel.
 #pragma once
 
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -240,227 +239,6 @@ __global__ void __launch_bounds__(Cfg<H>::NT1)
         }
         gV[sbase + idx] = Vk;
     }
-}
-
-// ---------------------------------------------------------------- pass 1, cluster pair form
-// The forward plane pass split over a cluster of two CTAs per z-plane, with
-// half the threads and shared memory of the single-block form each, so that
-// two CTAs share an SM and every plane runs at once.  CTA r reacts and
-// transforms along x the rows y in [r H/2, (r + 1) H/2) (v^n paired as
-// adjacent rows); after a cluster barrier it takes half of the columns for
-// the y transform, whose first stage reads the peer's rows through
-// distributed shared memory, and a second barrier orders those reads before
-// either CTA overwrites its rows with its columns.  M and W pair each mode
-// with its conjugate, which may lie in the peer's columns; V's packed
-// columns are written by the CTA that holds them.
-template <int H> constexpr bool has_pair_forward() { return false; }
-
-template <int H> struct PairSmem {
-    static constexpr int RH = H / 2, RP = rowp<H>(), KXP = kxp<H>();
-    static constexpr int ZCP = H / 2, VCP = H / 4;          // column-layout pitches
-    static constexpr int ZN = RH * RP > H * ZCP ? RH * RP : H * ZCP;
-    static constexpr int VN0 = (RH / 2) * RP > RH * KXP ? (RH / 2) * RP : RH * KXP;
-    static constexpr int VN = VN0 > H * VCP ? VN0 : H * VCP;
-    static constexpr size_t bytes = static_cast<size_t>(ZN + VN + H) * sizeof(float2);
-};
-
-// First Stockham stage (NS = 1) from a loader that may read the peer CTA's
-// shared memory: a cluster barrier (instead of a block barrier) separates
-// the loads from the writes, so that neither CTA overwrites what the other
-// still reads.
-template <int L, int R, int NTRANS, int NT, int SIGN, class At, class Load>
-__device__ __forceinline__ void stage1_from_cluster(float2* out, At at, Load load) {
-    constexpr int NB = NTRANS * (L / R);
-    constexpr int BPT = (NB + NT - 1) / NT;
-    float2 v[BPT][R];
-#pragma unroll
-    for (int i = 0; i < BPT; ++i) {
-        const int b = threadIdx.x + i * NT;
-        if (b < NB) {
-            const int t = b % NTRANS, j = b / NTRANS;
-#pragma unroll
-            for (int r = 0; r < R; ++r) v[i][r] = load(t, j + r * (L / R));
-            dft<R, SIGN>(v[i]);
-        }
-    }
-    cooperative_groups::this_cluster().sync();
-#pragma unroll
-    for (int i = 0; i < BPT; ++i) {
-        const int b = threadIdx.x + i * NT;
-        if (b < NB) {
-            const int t = b % NTRANS, j = b / NTRANS;
-#pragma unroll
-            for (int r = 0; r < R; ++r) out[at(t, j * R + r)] = v[i][r];
-        }
-    }
-    __syncthreads();
-}
-
-template <int H, int NB, int V>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Cfg<H>::NT1 / 2)
-    k_forward_xy_pair(const __grid_constant__ SpecBatch<NB> batch) {
-    namespace cg = cooperative_groups;
-    using PS = PairSmem<H>;
-    const SpecRun& R = batch.run[NB == 1 ? 0 : blockIdx.y];
-    const SpectralArgs& a = R.a;
-    const float* v = R.v;
-    const float* __restrict__ m = R.m;
-    const float* __restrict__ w = R.w;
-    unsigned long long* __restrict__ acc = R.acc;
-    float* v_out = R.v_out;
-    const float* __restrict__ us = R.us;
-    constexpr int NT = Cfg<H>::NT1 / 2, KXP = PS::KXP, HK = H / 2 + 1, RP = PS::RP;
-    constexpr int RH = PS::RH, HH = H / 2, ZCP = PS::ZCP, VCP = PS::VCP, VC = H / 4;
-    cg::cluster_group cluster = cg::this_cluster();
-    const int r = static_cast<int>(cluster.block_rank());
-    const int z = blockIdx.x >> 1;
-    extern __shared__ float2 sm[];
-    float2* Z = sm;               // rows [RH][RP] (m* + i w*), then columns [H][ZCP]
-    float2* Vb = Z + PS::ZN;      // row pairs [RH/2][RP], half rows [RH][KXP], columns [H][VCP]
-    float2* tw = Vb + PS::VN;
-    for (int i = threadIdx.x; i < H; i += NT) tw[i] = R.twiddle[i];
-    const float u_scale = R.sc->u_scale;   // u_bar per accumulator unit
-    const float c0 = *R.voff;   // the v spectrum only feeds derivatives: remove a constant
-    const size_t row0 = (static_cast<size_t>(z) * H + static_cast<size_t>(r) * RH) * H;
-    {
-        // node pairs (2q, x), (2q + 1, x) of the CTA's rows; all loads of a
-        // batch are issued first
-        constexpr int NPR = (RH / 2) * H, ITER = (NPR + NT - 1) / NT, CH = ITER < 2 ? ITER : 2;
-#pragma unroll 1
-        for (int i0 = 0; i0 < ITER; i0 += CH) {
-            float rv[CH][2], rm[CH][2], rw[CH][2], ru[CH][2];
-            unsigned long long ra[CH][2];
-#pragma unroll
-            for (int c = 0; c < CH; ++c) {
-                const int q = threadIdx.x + (i0 + c) * NT;
-                if (i0 + c < ITER && q < NPR) {
-                    const int pq = q / H, x = q % H;
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const size_t o = row0 + static_cast<size_t>(2 * pq + h) * H + x;
-                        rv[c][h] = v[o];
-                        rm[c][h] = m[o];
-                        rw[c][h] = w[o];
-                        ra[c][h] = acc[o];
-                        ru[c][h] = us ? us[o] : 0.f;
-                    }
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < CH; ++c) {
-                const int q = threadIdx.x + (i0 + c) * NT;
-                if (!(i0 + c < ITER && q < NPR)) continue;
-                const int pq = q / H, x = q % H;
-                float vn[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const size_t o = row0 + static_cast<size_t>(2 * pq + h) * H + x;
-                    acc[o] = 0ull;
-                    float ms, ws;
-                    const float u = acc_to_float(ra[c][h]) * u_scale;
-                    react(a, rv[c][h], rm[c][h], rw[c][h], u, us ? ru[c][h] : u, ms, ws, vn[h]);
-                    Z[(2 * pq + h) * RP + x] = make_float2(ms, ws);
-                    if (a.write_v) v_out[o] = vn[h];
-                }
-                Vb[pq * RP + x] = make_float2(vn[0] - c0, vn[1] - c0);
-            }
-        }
-    }
-    __syncthreads();
-    if (a.do_mw) fft_axis<H, V, RH, 1, RP, NT, -1>(Z, tw);
-    fft_axis<H, V, RH / 2, 1, RP, NT, -1>(Vb, tw);
-    {
-        // split each transformed row pair into the half rows of rows 2q and
-        // 2q + 1, packed: entry 0 = X(0) + i X(H/2), both real
-        constexpr int NS = (RH / 2) * HH, SPT = (NS + NT - 1) / NT;
-        float2 x1[SPT], x2[SPT];
-#pragma unroll
-        for (int s = 0; s < SPT; ++s) {
-            const int idx = threadIdx.x + s * NT;
-            if (idx < NS) {
-                const int p = idx / HH, k = idx % HH;
-                const float2 zp = Vb[p * RP + k];
-                const float2 zm = Vb[p * RP + (k == 0 ? HH : H - k)];
-                if (k == 0) {
-                    x1[s] = make_float2(zp.x, zm.x);
-                    x2[s] = make_float2(zp.y, zm.y);
-                } else {
-                    x1[s] = make_float2(0.5f * (zp.x + zm.x), 0.5f * (zp.y - zm.y));
-                    x2[s] = make_float2(0.5f * (zp.y + zm.y), -0.5f * (zp.x - zm.x));
-                }
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int s = 0; s < SPT; ++s) {
-            const int idx = threadIdx.x + s * NT;
-            if (idx < NS) {
-                const int p = idx / HH, k = idx % HH;
-                Vb[(2 * p) * KXP + k] = x1[s];
-                Vb[(2 * p + 1) * KXP + k] = x2[s];
-            }
-        }
-    }
-    cluster.sync();   // both CTAs' rows are transformed
-    const float2* Z0 = cluster.map_shared_rank(Z, 0);
-    const float2* Z1 = cluster.map_shared_rank(Z, 1);
-    const float2* V0 = cluster.map_shared_rank(Vb, 0);
-    const float2* V1 = cluster.map_shared_rank(Vb, 1);
-    constexpr int R1 = Radix<H, V>::R1;
-    if (a.do_mw) {
-        // columns kx in [r H/2, (r + 1) H/2) of m* + i w*
-        const int k0 = r * HH;
-        stage1_from_cluster<H, R1, HH, NT, -1>(Z, Strided<1, ZCP>{}, [&](int t, int y) {
-            return (y < RH ? Z0 : Z1)[(y % RH) * RP + k0 + t];
-        });
-        fft_rest<H, V, HH, ZCP, 1, NT, -1>(Z, tw);
-    }
-    {
-        // packed v columns [r H/4, (r + 1) H/4)
-        const int k0 = r * VC;
-        stage1_from_cluster<H, R1, VC, NT, -1>(Vb, Strided<1, VCP>{}, [&](int t, int y) {
-            return (y < RH ? V0 : V1)[(y % RH) * KXP + k0 + t];
-        });
-        fft_rest<H, V, VC, VCP, 1, NT, -1>(Vb, tw);
-    }
-    cluster.sync();   // both CTAs' columns are transformed
-    const size_t sbase = static_cast<size_t>(z) * H * KXP;
-    if (a.do_mw) {
-        // M, W for the modes ky in [r H/2, (r + 1) H/2), all kx < H/2 + 2
-        constexpr int NP = RH * KXP;
-        for (int idx = threadIdx.x; idx < NP; idx += NT) {
-            const int ky = r * RH + idx / KXP, k = idx % KXP;
-            float2 M = make_float2(0.f, 0.f), W = M;
-            if (k < HK) {
-                const int kc = neg_mod<H>(k), yc = neg_mod<H>(ky);
-                const float2 zk = (k < HH ? Z0 : Z1)[ky * ZCP + k % HH];
-                const float2 zc = (kc < HH ? Z0 : Z1)[yc * ZCP + kc % HH];
-                M = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y - zc.y));
-                W = make_float2(0.5f * (zk.y + zc.y), -0.5f * (zk.x - zc.x));
-            }
-            R.specM[sbase + static_cast<size_t>(ky) * KXP + k] = M;
-            R.specW[sbase + static_cast<size_t>(ky) * KXP + k] = W;
-        }
-    }
-    {
-        // V: the CTA's packed columns; packed column 0 holds V(0, .) + i V(H/2, .)
-        for (int idx = threadIdx.x; idx < H * VC; idx += NT) {
-            const int ky = idx / VC, cl = idx % VC, c = r * VC + cl;
-            float2* row = R.specV + sbase + static_cast<size_t>(ky) * KXP;
-            if (c != 0) {
-                row[c] = Vb[ky * VCP + cl];
-            } else {
-                const float2 pk = Vb[ky * VCP], pc = Vb[neg_mod<H>(ky) * VCP];
-                row[0] = make_float2(0.5f * (pk.x + pc.x), 0.5f * (pk.y - pc.y));
-                row[HH] = make_float2(0.5f * (pk.y + pc.y), -0.5f * (pk.x - pc.x));
-            }
-        }
-        if (r == 1) {
-            for (int ky = threadIdx.x; ky < H; ky += NT)
-                R.specV[sbase + static_cast<size_t>(ky) * KXP + HK] = make_float2(0.f, 0.f);
-        }
-    }
-    cluster.sync();   // the peer may still read this CTA's columns
 }
 
 // ---------------------------------------------------------------- pass 2
@@ -1269,10 +1047,6 @@ void configure_fused(int device) {
     if (configured_device == device) return;
     cudaFuncSetAttribute(k_forward_xy<H, NB, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(FusedSmem<H>::fwd));
-    if constexpr (has_pair_forward<H>())
-        cudaFuncSetAttribute(k_forward_xy_pair<H, NB, V>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(PairSmem<H>::bytes));
     cudaFuncSetAttribute(k_z_multiply<H, NB, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(FusedSmem<H>::z));
     cudaFuncSetAttribute(k_inverse_xy<H, NB, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1286,12 +1060,7 @@ cudaError_t fused_pass(const SpecBatch<NB>& batch, int nb, int pass, int device,
     configure_fused<H, NB, V>(device);
     constexpr int KXP = kxp<H>();
     if (pass == 0) {
-        if constexpr (has_pair_forward<H>()) {
-            k_forward_xy_pair<H, NB, V>
-                <<<dim3(2 * H, nb), Cfg<H>::NT1 / 2, PairSmem<H>::bytes, s>>>(batch);
-        } else {
-            k_forward_xy<H, NB, V><<<dim3(H, nb), Cfg<H>::NT1, FusedSmem<H>::fwd, s>>>(batch);
-        }
+        k_forward_xy<H, NB, V><<<dim3(H, nb), Cfg<H>::NT1, FusedSmem<H>::fwd, s>>>(batch);
     } else if (pass == 1) {
         const int kt = (KXP + zcols<H>() - 1) / zcols<H>();
         k_z_multiply<H, NB, V><<<dim3(H, 4, NB == 1 ? kt : nb), Cfg<H>::NT2, FusedSmem<H>::z, s>>>(
