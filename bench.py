@@ -157,16 +157,20 @@ def _peaks():
 # DRAM bytes (read + write) of one launch from an ncu capture of the same
 # workload (profiles/k_step_and_spectral_passes_headline_128cube_4M.md),
 # valid only while the kernel's source is the one captured.
-NCU_TRAFFIC = {"particle_step": (("paper_2605_20140_gb300/csrc/particles.cu",
-                                  "paper_2605_20140_gb300/csrc/sipf_internal.cuh"),
-                                 "fb96818b02f6b187", 154.0e6)}
+_STEP_SOURCES = ("paper_2605_20140_gb300/csrc/particles.cu",
+                 "paper_2605_20140_gb300/csrc/sipf_internal.cuh")
+# (kernel group, H, N) -> (sources, their digest, DRAM bytes per launch from
+# the ncu captures summarised under profiles/)
+NCU_TRAFFIC = {("particle_step", 128, 1 << 22): (_STEP_SOURCES, "82cc43698654817a", 149.9e6),
+               ("particle_step", 256, 1 << 25): (_STEP_SOURCES, "82cc43698654817a", 1651.0e6)}
 
 
-def _ncu_traffic(group):
-    """DRAM bytes per launch from the committed ncu capture, or None when the
-    kernel's sources changed since (sha256 over the files, first 16 hex)."""
+def _ncu_traffic(group, H, N):
+    """DRAM bytes per launch from the committed ncu capture of this workload,
+    or None when the kernel's sources changed since (sha256 over the files,
+    first 16 hex)."""
     import hashlib
-    entry = NCU_TRAFFIC.get(group)
+    entry = NCU_TRAFFIC.get((group, H, N))
     if not entry:
         return None
     paths, digest, traffic = entry
@@ -347,7 +351,7 @@ def run_sipf(args, rank, world, local):
         achieved = algo_bytes / per_launch_s / 1e9
         roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
-                    "traffic": _ncu_traffic(dom), "algorithmic_bytes": algo_bytes}
+                    "traffic": _ncu_traffic(dom, H, N), "algorithmic_bytes": algo_bytes}
     step_bytes = ALGO_B_PER_PARTICLE * N + ALGO_B_PER_NODE * H ** 3
     step_roofline = {"algorithmic_bytes": step_bytes,
                      "achieved": step_bytes / (ms_step * 1e-3) / 1e9,
