@@ -161,8 +161,8 @@ _STEP_SOURCES = ("paper_2605_20140_gb300/csrc/particles.cu",
                  "paper_2605_20140_gb300/csrc/sipf_internal.cuh")
 # (kernel group, H, N) -> (sources, their digest, DRAM bytes per launch from
 # the ncu captures summarised under profiles/)
-NCU_TRAFFIC = {("particle_step", 128, 1 << 22): (_STEP_SOURCES, "82cc43698654817a", 149.9e6),
-               ("particle_step", 256, 1 << 25): (_STEP_SOURCES, "82cc43698654817a", 1651.0e6)}
+NCU_TRAFFIC = {("particle_step", 128, 1 << 22): (_STEP_SOURCES, "8c8391fe650f832c", 151.3e6),
+               ("particle_step", 256, 1 << 25): (_STEP_SOURCES, "8c8391fe650f832c", 1650.8e6)}
 
 
 def _ncu_traffic(group, H, N):
@@ -326,9 +326,15 @@ def run_sipf(args, rank, world, local):
         _barrier(world)
         reps.append(_max_over_ranks(e0.elapsed_time(e1), world))
     ms_total = statistics.median(reps)
-    # ---- per-kernel-group times: further steps traced with CUDA events between
-    # the groups on the launching stream (tracing enqueues launch by launch)
-    n_prof = min(args.steps, 200)
+    # ---- per-kernel-group times over the timed region's own steps: the same
+    # trajectory again (initial state, the same warm-up), traced with CUDA
+    # events between the groups on the launching stream (tracing enqueues
+    # launch by launch); the particle step's cost grows as the seeds spread,
+    # so tracing later steps would describe other states than the ones timed
+    n_prof = min(args.steps, 1000)
+    sim.set_state(wl.x, wl.mass, wl.ids, wl.v, wl.m, wl.w)
+    sim.step(dt, args.warmup)
+    sipf.sipf_sync(sim.ctx)
     sipf.sipf_profile(sim.ctx, True)
     sim.step(dt, n_prof)
     torch.cuda.synchronize()

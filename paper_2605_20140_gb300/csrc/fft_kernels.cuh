@@ -404,7 +404,10 @@ __global__ void __launch_bounds__(Cfg<H>::NT3)
     float2* tw = B2 + H * KXS;
     float2* Z = sm;               // [H][RP] packed rows (aliases B0/B1)
     float2* Z2 = B2;              // [H/2][RP] rows y, y + H/2 of B2 packed (aliases B2)
-    const int z = blockIdx.x, group = 1 - blockIdx.y;
+    // the two groups of a plane are neighbouring blocks: their partial writes
+    // of the gather array's nodes (x, y, z components, then w) follow each
+    // other closely, while the lines are still in L2
+    const int z = blockIdx.x >> 1, group = 1 - static_cast<int>(blockIdx.x & 1);
     if (group == 0 && !a.do_mw) return;
     for (int i = threadIdx.x; i < H; i += NT) tw[i] = twg[i];
     __syncthreads();
@@ -1066,7 +1069,7 @@ cudaError_t fused_pass(const SpecBatch<NB>& batch, int nb, int pass, int device,
         k_z_multiply<H, NB, V><<<dim3(H, 4, NB == 1 ? kt : nb), Cfg<H>::NT2, FusedSmem<H>::z, s>>>(
             batch);
     } else {
-        k_inverse_xy<H, NB, V><<<dim3(H, 2, nb), Cfg<H>::NT3, FusedSmem<H>::inv, s>>>(batch);
+        k_inverse_xy<H, NB, V><<<dim3(2 * H, 1, nb), Cfg<H>::NT3, FusedSmem<H>::inv, s>>>(batch);
     }
     return cudaGetLastError();
 }

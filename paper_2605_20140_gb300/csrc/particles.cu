@@ -297,6 +297,7 @@ constexpr int kNT = 256;                  // threads of the step kernel
 constexpr int kPT = 4;                    // particles per thread and item
 constexpr int kItem = kNT * kPT;          // particles per item
 constexpr int kBlock = 9 * 9 * 9;         // nodes of a tile's gather block
+constexpr int kSparsePerTile = 256;       // below this mean tile occupancy, skip idle warps
 
 // Deposit node block of a tile for assignment order ORDER: local node
 // coordinates [-DO, 8 + DO] per axis (trilinear: the cells' corners 0..8;
@@ -410,7 +411,7 @@ template <int ORDER> struct StepShared {
 // Items [i_lo, i_hi) of one run: deposit of X^(n-1), gather, noise, push,
 // mass update and binning of every particle.  dep and dep64 are zero on entry
 // and on exit.
-template <int ORDER, class Keys>
+template <int ORDER, bool SKIP, class Keys>
 __device__ __forceinline__ void step_items(const StepView& v, const Keys& keys, int i_lo, int i_hi,
                                            StepShared<ORDER>& sh) {
     using DB = DepBlock<ORDER>;
@@ -514,7 +515,16 @@ __device__ __forceinline__ void step_items(const StepView& v, const Keys& keys, 
         }
         __syncthreads();
         int bad = 0;
-        for (int j = 0; j < kPT; ++j) {
+        // SKIP: only the iterations with an element for this warp (short items,
+        // common in small runs, leave whole warps idle; the count is
+        // warp-uniform, so the warp-wide votes below see whole warps).  Dense
+        // runs take all kPT iterations, which keeps a register free.
+        int jn = kPT;
+        if constexpr (SKIP) {
+            const int wfirst = it.beg + static_cast<int>(threadIdx.x & ~31u);
+            jn = it.end > wfirst ? min(kPT, (it.end - wfirst + kNT - 1) / kNT) : 0;
+        }
+        for (int j = 0; j < jn; ++j) {
             const int e = j * kNT + threadIdx.x;     // element of the item, coalesced
             const int i = it.beg + e;
             const bool valid = i < it.end;
@@ -692,7 +702,7 @@ __device__ __forceinline__ void step_items(const StepView& v, const Keys& keys, 
     }
 }
 
-template <int ORDER>
+template <int ORDER, bool SKIP>
 __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
     k_step(PushArgs a, const StepScalars* __restrict__ sc, const float4* __restrict__ G, Buf src,
            Buf dst, Layout L, const Item* __restrict__ items, const int* __restrict__ n_items,
@@ -711,7 +721,7 @@ __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
     const int i_hi = static_cast<int>(static_cast<long long>(blockIdx.x + 1) * total / gridDim.x);
     const StepView v{a.H, a.drift, a.noise, a.tau, a.k0, a.k1, a.push, sc, G, src, dst, L,
                      items, acc, status, do_deposit, do_move};
-    step_items<ORDER>(v, KeysGiven{a.rk}, i_lo, i_hi, sh);
+    step_items<ORDER, SKIP>(v, KeysGiven{a.rk}, i_lo, i_hi, sh);
 }
 
 // ------------------------------------------------------------------ planning
@@ -889,7 +899,7 @@ __global__ void __launch_bounds__(kNT, DepBlock<2>::MIN_BLOCKS)
                             d.items, d.acc, d.status, 1, 1};
         }
         __syncthreads();
-        step_items<2>(view, KeysScheduled{view}, lo, hi, sh);
+        step_items<2, true>(view, KeysScheduled{view}, lo, hi, sh);
         __syncthreads();
     }
 }
@@ -1273,9 +1283,9 @@ int step_grid(sipf_ctx* c) {
     int dev = c->device, nsm = 0, per_sm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (c->p.p2g_order == 4)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<4>, kNT, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<4, false>, kNT, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<2>, kNT, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<2, false>, kNT, 0);
     // a tuning may ask for fewer blocks per SM than the occupancy limit
     if (c->step_bps > 0 && c->step_bps < per_sm) per_sm = c->step_bps;
     int g = nsm * (per_sm > 0 ? per_sm : 1);
@@ -1287,7 +1297,11 @@ int step_grid(sipf_ctx* c) {
 
 cudaError_t launch_step_kernel(sipf_ctx* c, const PushArgs& a, int do_deposit, int do_move) {
     const int b = c->cur;
-    auto kernel = c->p.p2g_order == 4 ? k_step<4> : k_step<2>;
+    // runs with fewer than kSparsePerTile particles per tile on average have
+    // many short items: they take the form that skips idle warps
+    const bool sparse = c->N < static_cast<int64_t>(kSparsePerTile) * c->ntiles;
+    auto kernel = c->p.p2g_order == 4 ? (sparse ? k_step<4, true> : k_step<4, false>)
+                                      : (sparse ? k_step<2, true> : k_step<2, false>);
     kernel<<<c->step_blocks, kNT, 0, c->stream>>>(
         a, c->dsc + b, reinterpret_cast<const float4*>(c->G), buf_of(c, b), buf_of(c, b ^ 1),
         layout_of(c, b ^ 1), c->items, c->n_items,

@@ -193,6 +193,13 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         sipf.Simulation(16, 1.0, (0.0, 0.0, 0.0), 64, Params())
 
 
+def _restore_shipped_table():
+    """Put back the table that ships next to the library (later tests in the
+    same process create contexts with it, as bench.py does)."""
+    shipped = os.path.join(os.path.dirname(sipf.LIB_PATH), "sipf_tuning.txt")
+    sipf.sipf_tuning_load(shipped if os.path.exists(shipped) else None)
+
+
 def test_tuning_table_is_parsed_and_looked_up(lib, tmp_path):
     """The autotuner's table (host only): the first line matching (H, N)
     applies; malformed or out-of-range lines are refused; NULL empties it."""
@@ -215,6 +222,7 @@ def test_tuning_table_is_parsed_and_looked_up(lib, tmp_path):
         sipf.sipf_tuning_load(tmp_path / "missing.txt")
     sipf.sipf_tuning_load(None)
     assert sipf.sipf_tuning_lookup(128, 4194304) is None
+    _restore_shipped_table()
 
 
 def test_autotuner_candidates_are_valid():
@@ -226,3 +234,25 @@ def test_autotuner_candidates_are_valid():
         assert 8 <= c["bucket_slack_div"] <= 1024 and 0 <= c["bucket_slack_add"] <= 32
     for H, lo, hi, rep, recipe in autotune.TARGETS:
         assert lo <= rep <= hi and recipe in ("headline", "large")
+
+
+def test_autotuner_partial_table_keeps_the_other_sizes(tmp_path):
+    """A re-tune of some grid sizes (--only) rewrites their lines and keeps
+    the others; the result parses."""
+    from paper_2605_20140_gb300 import autotune
+    path = tmp_path / "t.txt"
+    path.write_text("# old table\n128 1 10 0 0 8 32   # 0.2 (0.2)\n256 1 10 1 0 16 16   # 2.0\n"
+                    "96 1 10 1 3 16 16   # 0.05\n")
+    best = dict(radix_plan=2, step_blocks_per_sm=0, bucket_slack_div=16, bucket_slack_add=16)
+    autotune.write_table(str(path), [(256, 1, 10, best, 1.5, 1.9)], keep={128, 96})
+    lines = [ln.split("#")[0].split() for ln in path.read_text().splitlines()]
+    rows = [ln for ln in lines if ln]
+    assert sorted(int(r[0]) for r in rows) == [96, 128, 256]
+    assert [r for r in rows if r[0] == "256"] == [["256", "1", "10", "2", "0", "16", "16"]]
+    assert [r for r in rows if r[0] == "128"] == [["128", "1", "10", "0", "0", "8", "32"]]
+    sipf.sipf_tuning_load(path)
+    try:
+        assert sipf.sipf_tuning_lookup(256, 5)["radix_plan"] == 2
+        assert sipf.sipf_tuning_lookup(96, 5)["step_blocks_per_sm"] == 3
+    finally:
+        _restore_shipped_table()
