@@ -9,6 +9,7 @@
 #include <dlfcn.h>
 
 #include <algorithm>
+#include <utility>
 #include <mutex>
 #include <new>
 #include <string>
@@ -1275,20 +1276,21 @@ int enqueue_batched_step(sipf_ensemble* e, const double* dt, const RunDesc* d_ru
     if (r == SIPF_OK) r = cuda(cudaStreamWaitEvent(e->side, e->ev_fork, 0), "cudaStreamWaitEvent");
     if (r == SIPF_OK) r = cuda(launch_plan_multi(d_runs, n, parity, e->side), "batched plan");
     if (r == SIPF_OK) r = cuda(cudaEventRecord(e->ev_join, e->side), "cudaEventRecord");
-    // runs grouped by grid size, in member order within a size
-    std::vector<int> sizes;
-    for (const sipf_ctx* c : e->members)
-        if (std::find(sizes.begin(), sizes.end(), c->H) == sizes.end()) sizes.push_back(c->H);
-    std::sort(sizes.begin(), sizes.end());
+    // runs grouped by (grid size, radix plan), in member order within a
+    // group, so that every member runs the passes of its own plan
+    std::vector<std::pair<int, int>> groups;
+    for (const sipf_ctx* c : e->members) {
+        const std::pair<int, int> g(c->H, c->radix_plan);
+        if (std::find(groups.begin(), groups.end(), g) == groups.end()) groups.push_back(g);
+    }
+    std::sort(groups.begin(), groups.end());
     const int device = e->members[0]->device;
-    for (int H : sizes) {
+    for (const auto& g : groups) {
+        const int H = g.first, plan = g.second;
         std::vector<SpecRun> runs;
-        int plan = 0;   // the radix plan of the size's first member serves the batch
         for (int i = 0; i < n; ++i)
-            if (e->members[i]->H == H) {
-                if (runs.empty()) plan = e->members[i]->radix_plan;
+            if (e->members[i]->H == H && e->members[i]->radix_plan == plan)
                 runs.push_back(spec_run(e->members[i], spectral_args(e->members[i], dt[i], 1)));
-            }
         for (size_t b0 = 0; b0 < runs.size() && r == SIPF_OK; b0 += kMaxBatch) {
             const int nb = static_cast<int>(std::min<size_t>(kMaxBatch, runs.size() - b0));
             for (int pass = 0; pass < 3 && r == SIPF_OK; ++pass)

@@ -151,3 +151,46 @@ def test_a_member_outside_the_batched_form_falls_back_to_streams():
         f0, s0, l0 = snapshot(solo)
     for k in f0:
         np.testing.assert_array_equal(f[k], f0[k], err_msg=k)
+
+
+def test_members_on_the_lane_group_pipeline_equal_their_solo_runs():
+    """Members whose tuning selects radix plan 2 (the lane-group spectral
+    pipeline) run its passes member by member inside the batched step, and
+    members of one grid size on different plans are batched apart: here three
+    of the four H = 64 members take plan 2, the fourth keeps its table plan,
+    and every member ends bit for bit where its solo run with the same plan
+    ends."""
+    runs = ensemble_workloads(12, seed=3, max_log2_N=15)
+    h64 = [i for i, w in enumerate(runs) if w.H == 64]
+    assert len(h64) >= 4 and len({w.H for w in runs}) > 2
+    on_plan2 = set(h64[:3])
+
+    def tune(sim, i):
+        if i in on_plan2:
+            t = sipf.sipf_get_tuning(sim.ctx)
+            t["radix_plan"] = 2
+            sipf.sipf_set_tuning(sim.ctx, **t)
+            assert sipf.sipf_get_tuning(sim.ctx)["radix_plan"] == 2
+
+    steps = 12
+    dts = np.array([w.dt for w in runs])
+    with sipf.Ensemble([(w.H, w.L, w.origin, w.N, w.params) for w in runs],
+                       mode=sipf.SIPF_ENSEMBLE_BATCHED) as ens:
+        for i, (sim, w) in enumerate(zip(ens.members, runs)):
+            tune(sim, i)
+            sim.set_state(w.x, w.mass, w.ids, w.v, w.m, w.w)
+        assert sipf.sipf_get_tuning(ens.members[h64[3]].ctx)["radix_plan"] != 2
+        ens.step(dts, steps)
+        ens.sync()
+        assert ens.last_path() == sipf.SIPF_ENSEMBLE_BATCHED
+        got = [snapshot(sim) for sim in ens.members]
+    for i, (w, dt, (f, s, l)) in enumerate(zip(runs, dts, got)):
+        with sipf.Simulation(w.H, w.L, w.origin, w.N, w.params) as solo:
+            tune(solo, i)
+            solo.set_state(w.x, w.mass, w.ids, w.v, w.m, w.w)
+            solo.step(dt, steps)
+            f0, s0, l0 = snapshot(solo)
+        for k in f0:
+            np.testing.assert_array_equal(f[k], f0[k], err_msg=f"{w.name} {k}")
+        np.testing.assert_array_equal(s, s0)
+        np.testing.assert_array_equal(l, l0)
