@@ -893,8 +893,8 @@ __global__ void __launch_bounds__(kSxNT)
 // inverse: M, W, B in place, and V (or its filtered copy) -> i k_x V, i k_y V).
 template <int H, int SIGN, int V>
 __global__ void __launch_bounds__(kSxNT)
-    k_sx_columns(SpectralArgs a, float2* __restrict__ f0, float2* __restrict__ f1,
-                 float2* __restrict__ f2, float2* __restrict__ dx, float2* __restrict__ dy,
+    k_sx_columns(SpectralArgs a, float2* f0, float2* f1, float2* f2, float2* __restrict__ dx,
+                 float2* __restrict__ dy,
                  const float2* __restrict__ twg, int plain) {
     constexpr int NT = kSxNT, KXP = kxp<H>(), KB = kSxCols, CP = KB + 1;
     extern __shared__ float2 sm[];
