@@ -268,7 +268,8 @@ int sipf_resample(sipf_ctx* ctx, double ratio, int32_t* resampled);
  * a step of the whole ensemble is one persistent particle-step launch over
  * the concatenated (run, tile-item) work list of all members, one launch
  * planning every member's next step, and each of the three spectral passes
- * once per grid size (the members of one size batched, 64 per launch); pairs
+ * once per (grid size, radix plan) group (the members of a group batched, 64
+ * per launch; members on radix plan 2 run its passes one after another); pairs
  * of steps are captured once per (dt vector, parity) as a CUDA graph (at most
  * four kept) and replayed.  Otherwise, or in mode SIPF_ENSEMBLE_STREAMS, each
  * member advances on its own stream with its own two-step graph.  Either way
