@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(Cfg<H>::NT3)
 }
 
 // ---------------------------------------------------------------- warp per-axis pipeline
-// For the grid sizes with a LaneShape shape the whole spectral step can run as
+// For the grid sizes with a LaneShape the whole spectral step can run as
 // five passes over lines held in registers by groups of P lanes (WarpFFT),
 // with the half spectra in global memory (L2) between them and no block
 // barrier inside a transform:
