@@ -112,13 +112,15 @@ __global__ void __launch_bounds__(Cfg<H>::NT1)
     const StepScalars* __restrict__ sc = R.sc;
     const float* __restrict__ us = R.us;
     constexpr int NT = Cfg<H>::NT1, KXP = kxp<H>(), HK = H / 2 + 1, RP = rowp<H>();
-    const float u_scale = sc->u_scale;   // u_bar per accumulator unit
+    pdl_trigger();
     extern __shared__ float2 sm[];
     float2* Z = sm;               // [H][RP]: m* + i w*
     float2* Vb = Z + H * RP;      // v^n: [H/2][RP] row pairs, then [H][KXP] half rows
     float2* tw = Vb + H * KXP;    // [H]
     const int z = blockIdx.x;
     for (int i = threadIdx.x; i < H; i += NT) tw[i] = twg[i];
+    pdl_wait();   // the deposit, fields and step scalars of the kernels before
+    const float u_scale = sc->u_scale;   // u_bar per accumulator unit
     const size_t plane = static_cast<size_t>(z) * H * H;
     const float c0 = *voff;   // the v spectrum only feeds derivatives: remove a constant
     {
@@ -264,11 +266,13 @@ __global__ void __launch_bounds__(Cfg<H>::NT2)
     float2* tw = buf + H * KB;
     const int ky = blockIdx.x, field = blockIdx.y;   // 0 m, 1 w, 2 v -> i k_z V, 3 v -> filtered V
     const int k0 = NB == 1 ? blockIdx.z * KB : 0;
+    pdl_trigger();
     if (field < 2 && !a.do_mw) return;
     if (field == 3 && !a.filter) return;
     const float2* src = field == 0 ? gM : field == 1 ? gW : gV;
     float2* dst = field == 0 ? gM : field == 1 ? gW : field == 2 ? gB : gA;
     for (int i = threadIdx.x; i < H; i += NT) tw[i] = twg[i];
+    pdl_wait();   // the forward pass's spectra
     constexpr int R1 = Radix<H, V>::R1;
     // element (column t, z) of the block's tile in a [z][ky][KXP] half spectrum
     auto at = [ky, k0](int t, int zz) -> size_t {
@@ -408,9 +412,11 @@ __global__ void __launch_bounds__(Cfg<H>::NT3)
     // of the gather array's nodes (x, y, z components, then w) follow each
     // other closely, while the lines are still in L2
     const int z = blockIdx.x >> 1, group = 1 - static_cast<int>(blockIdx.x & 1);
+    pdl_trigger();
     if (group == 0 && !a.do_mw) return;
     for (int i = threadIdx.x; i < H; i += NT) tw[i] = twg[i];
     __syncthreads();
+    pdl_wait();   // the z pass's spectra
     const size_t pbase = static_cast<size_t>(z) * H * KXP;
     // inverse y: first stage from global, second in shared memory
     if (group == 0) {
@@ -1063,15 +1069,16 @@ cudaError_t fused_pass(const SpecBatch<NB>& batch, int nb, int pass, int device,
     configure_fused<H, NB, V>(device);
     constexpr int KXP = kxp<H>();
     if (pass == 0) {
-        k_forward_xy<H, NB, V><<<dim3(H, nb), Cfg<H>::NT1, FusedSmem<H>::fwd, s>>>(batch);
+        return launch_pdl(k_forward_xy<H, NB, V>, dim3(H, nb), dim3(Cfg<H>::NT1),
+                          FusedSmem<H>::fwd, s, batch);
     } else if (pass == 1) {
         const int kt = (KXP + zcols<H>() - 1) / zcols<H>();
-        k_z_multiply<H, NB, V><<<dim3(H, 4, NB == 1 ? kt : nb), Cfg<H>::NT2, FusedSmem<H>::z, s>>>(
-            batch);
+        return launch_pdl(k_z_multiply<H, NB, V>, dim3(H, 4, NB == 1 ? kt : nb),
+                          dim3(Cfg<H>::NT2), FusedSmem<H>::z, s, batch);
     } else {
-        k_inverse_xy<H, NB, V><<<dim3(2 * H, 1, nb), Cfg<H>::NT3, FusedSmem<H>::inv, s>>>(batch);
+        return launch_pdl(k_inverse_xy<H, NB, V>, dim3(2 * H, 1, nb), dim3(Cfg<H>::NT3),
+                          FusedSmem<H>::inv, s, batch);
     }
-    return cudaGetLastError();
 }
 
 // One fused pass over n runs (n = 1: the batch-of-one instantiation).

@@ -709,10 +709,12 @@ __global__ void __launch_bounds__(kNT, DepBlock<ORDER>::MIN_BLOCKS)
            unsigned long long* __restrict__ acc, int do_deposit, int do_move,
            int* __restrict__ status) {
     __shared__ StepShared<ORDER> sh;
+    pdl_trigger();
     for (int i = threadIdx.x; i < DepBlock<ORDER>::N; i += kNT) {
         sh.dep[i] = 0;
         sh.dep64[i] = 0;
     }
+    pdl_wait();   // the gather array of the spectral passes before
     // block b takes a contiguous run of items; consecutive items of one tile
     // share the node block of the gather array and the deposit sums, which
     // go to the grid accumulator once, when the tile changes
@@ -1302,11 +1304,13 @@ cudaError_t launch_step_kernel(sipf_ctx* c, const PushArgs& a, int do_deposit, i
     const bool sparse = c->N < static_cast<int64_t>(kSparsePerTile) * c->ntiles;
     auto kernel = c->p.p2g_order == 4 ? (sparse ? k_step<4, true> : k_step<4, false>)
                                       : (sparse ? k_step<2, true> : k_step<2, false>);
-    kernel<<<c->step_blocks, kNT, 0, c->stream>>>(
-        a, c->dsc + b, reinterpret_cast<const float4*>(c->G), buf_of(c, b), buf_of(c, b ^ 1),
-        layout_of(c, b ^ 1), c->items, c->n_items,
-        reinterpret_cast<unsigned long long*>(c->acc), do_deposit, do_move, c->status);
-    return cudaGetLastError();
+    return launch_pdl(kernel, dim3(c->step_blocks), dim3(kNT), 0, c->stream, a,
+                      static_cast<const StepScalars*>(c->dsc + b),
+                      static_cast<const float4*>(reinterpret_cast<float4*>(c->G)), buf_of(c, b),
+                      buf_of(c, b ^ 1), layout_of(c, b ^ 1), static_cast<const Item*>(c->items),
+                      static_cast<const int*>(c->n_items),
+                      reinterpret_cast<unsigned long long*>(c->acc), do_deposit, do_move,
+                      c->status);
 }
 
 // Items of buffer `b` and, with next_layout, the layout of b ^ 1.

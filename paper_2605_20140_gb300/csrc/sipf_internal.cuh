@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/sipf.h"
@@ -34,6 +35,34 @@ __device__ __forceinline__ uint4 philox_round(uint4 c, uint32_t k0, uint32_t k1)
     const uint64_t p1 = static_cast<uint64_t>(0xCD9E8D57u) * c.z;
     return make_uint4(static_cast<uint32_t>(p1 >> 32) ^ c.y ^ k0, static_cast<uint32_t>(p1),
                       static_cast<uint32_t>(p0 >> 32) ^ c.w ^ k1, static_cast<uint32_t>(p0));
+}
+
+// Programmatic dependent launch.  A kernel launched with launch_pdl may
+// begin while the kernel before it in the stream runs its last blocks:
+// pdl_wait() returns once that kernel has completed and its writes are
+// visible (a kernel reads nothing its predecessor writes before it), and
+// pdl_trigger() lets the next kernel's blocks start launching.  Both are
+// no-ops in kernels launched the ordinary way.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <class... Exp, class... Act>
+cudaError_t launch_pdl(void (*kernel)(Exp...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Act&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    // the legacy default stream keeps ordinary launches
+    cfg.numAttrs = s ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Act>(args)...);
 }
 
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
