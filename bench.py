@@ -161,8 +161,8 @@ _STEP_SOURCES = ("paper_2605_20140_gb300/csrc/particles.cu",
                  "paper_2605_20140_gb300/csrc/sipf_internal.cuh")
 # (kernel group, H, N) -> (sources, their digest, DRAM bytes per launch from
 # the ncu captures summarised under profiles/)
-NCU_TRAFFIC = {("particle_step", 128, 1 << 22): (_STEP_SOURCES, "975cc82290c3ac8f", 151.4e6),
-               ("particle_step", 256, 1 << 25): (_STEP_SOURCES, "975cc82290c3ac8f", 1650.8e6)}
+NCU_TRAFFIC = {("particle_step", 128, 1 << 22): (_STEP_SOURCES, "9fe946df0af00a12", 151.4e6),
+               ("particle_step", 256, 1 << 25): (_STEP_SOURCES, "9fe946df0af00a12", 1650.8e6)}
 
 
 def _ncu_traffic(group, H, N):

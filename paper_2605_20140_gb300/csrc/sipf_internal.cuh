@@ -60,8 +60,8 @@ cudaError_t launch_pdl(void (*kernel)(Exp...), dim3 grid, dim3 block, size_t sme
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    // the legacy default stream keeps ordinary launches
-    cfg.numAttrs = s ? 1 : 0;
+    // the legacy default stream (NULL or its explicit handle) keeps ordinary launches
+    cfg.numAttrs = (s == nullptr || s == cudaStreamLegacy) ? 0 : 1;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Act>(args)...);
 }
 
